@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the photon-package transport on GB300: packages/s.
+
+A step is one pass of the whole path over one batch: zero the counts, transport
+the batch of packages (Bjorkman-Wood re-emission, persistent packet-pool kernel,
+FP32), invert the counts into per-cell temperatures (FP64) and gather the escaped
+spectrum. The workload is the flared proto-planetary disk (128^3 base cubes, two
+levels of 2x2x2 refinement at the inner rim and midplane, 200 frequency bins,
+midplane V-band optical depth 1e3, 1e8 packages per GPU).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. With several ranks (torchrun) every rank follows its own
+package-id range (weak scaling), the integer counts are summed over ranks, and the
+step time is the maximum over ranks. ``--impl reference`` times the CPU oracle
+on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "photon packages/sec on 1 GB300 (chosen form vs plain) at stated T/count tolerance"
+UNIT = "packages/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--packages", type=float, default=1e8, help="packages per GPU per step")
+    p.add_argument("--workload", choices=["disk", "sphere"], default="disk")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--plain-packages", type=float, default=1e7)
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def build_model(name):
+    from paper_1201_3588_gb300 import workloads as w
+    if name == "sphere":
+        return w.sphere_model(), "dust sphere 16^3, 64 bins, 2 species, tau_V=1"
+    return (w.disk_model(),
+            "flared disk 128^3 base + 2 levels of 2x2x2 refinement, 200 bins, 2 species, "
+            "midplane tau_V=1e3, r 0.1-100 AU")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(model, n_total, seconds, mode=0):
+    """Oracle packages/s on the host (one thread): packages 0, 1, 2 ... of the same
+    workload, in chunks, until `seconds` of CPU work have been spent."""
+    import oracle
+    om = oracle.OracleModel(model)
+    tally = oracle.new_tally(om)
+    done, chunk = 0, 4
+    t0 = time.perf_counter()
+    while True:
+        oracle.transport(om, chunk, seed=1000, first_id=done, n_total=n_total, mode=mode,
+                         tally=tally)
+        done += chunk
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+        chunk = max(1, min(chunk * 2, int(done / el * (seconds - el)) + 1))
+    return done / el, done, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    model, desc = build_model(args.workload)
+    n_total = int(args.packages)
+    per_step = max(1.0, args.cpu_seconds / 3.0)
+    times, counts = [], []
+    for i in range(args.warmup + args.steps):
+        rate, n, el = cpu_oracle_rate(model, n_total, per_step)
+        if i >= args.warmup:
+            times.append(el)
+            counts.append(n)
+    value = sum(counts) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "packages_per_step": sum(counts) // len(counts),
+                       "sample": "oracle prefix of the same workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sum(counts)} packages over {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def walk_bytes(c, S):
+    """Algorithmic bytes of one transport launch (per unit of work):
+    every cell entered reads one base-cube id (4 B), one child id per refinement
+    level (4 B each) and S densities (4 B each); every absorption is one 8-byte
+    read-modify-write of a count (16 B)."""
+    entered = c["crossings"] + c["absorptions"] + c["scatters"] + c["capped"]
+    return entered * (4 + 4 * S) + 4 * c["levels"] + 16 * c["absorptions"]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1201_3588_gb300 import rt
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    model, desc = build_model(args.workload)
+    n = int(args.packages)
+    S, N, B = model.n_species, model.tree.n_leaves, model.n_bins
+    stream = torch.cuda.Stream(device=dev)
+    g = rt.Grid(model)
+    g.emit_star(n * world)
+    T_dev = torch.empty((S, N), dtype=torch.float32, device=dev)
+    sed_dev = torch.empty((2, model.n_sed_dirs, B), dtype=torch.int64, device=dev)
+    cnt_dev = torch.empty((S, N), dtype=torch.int64, device=dev) if world > 1 else None
+    first = rank * n
+
+    def step(k, ev=None):
+        g.reset(stream)
+        if ev:
+            ev[0].record(stream)
+        g.transport(n, seed=1000 + k, first_id=first, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        if world > 1:  # sum the integer counts over ranks (package ranges are disjoint)
+            g.counts(out=cnt_dev, stream=stream)
+            with torch.cuda.stream(stream):
+                dist.all_reduce(cnt_dev)
+            g.set_counts(cnt_dev, stream=stream)
+        g.temperatures(out=T_dev, stream=stream)
+        g.sed(out=sed_dev, stream=stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    counters_warm = g.counters()
+
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(args.warmup + k, kev[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    clocks = clk.summary()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    kern_s = [a.elapsed_time(b) / 1e3 for a, b in kev]
+    c = g.counters()  # last step's counters (each step starts from zero)
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = n * world * args.steps / elapsed
+
+    # roofline of the dominant kernel (the transport launch)
+    hbm, src = peaks()
+    kmean = sum(kern_s) / len(kern_s)
+    bytes_launch = walk_bytes(c, S)
+    achieved = bytes_launch / kmean / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "kernel": "k_transport_pool", "kernel_ms": 1e3 * kmean,
+            "algorithmic_bytes_per_launch": bytes_launch}
+
+    extra = {}
+    if rank == 0 and not args.no_plain:
+        extra["plain"] = plain_rates(g, model, int(args.plain_packages), stream, c, n)
+    e2e = e2e_rate(model, n, world, first, args.e2e_steps) if args.e2e_steps > 0 else None
+    if rank == 0:
+        cpu_rate, cpu_n, cpu_s = cpu_oracle_rate(model, n * world, args.cpu_seconds)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "packages_per_gpu_per_step": n, "leaves": N,
+                       "bins": B, "species": S, "reemission": "bjorkman-wood",
+                       "kernel": "persistent packet pool",
+                       "l2": f"inputs larger than L2: grid + counts "
+                             f"{(4 * N * S + N + 8 * N * S) / 2**20:.0f} MiB > 129 MiB"},
+            "roofline": roof,
+            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {cpu_n} packages of the same workload "
+                                       f"(BW mode, one thread, {cpu_s:.1f} s)"},
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "per_step": {"crossings": c["crossings"], "absorptions": c["absorptions"],
+                         "scatters": c["scatters"], "capped": c["capped"],
+                         "errors": c["errors"], "crossings_per_s": c["crossings"] / kmean,
+                         "warmup_crossings": counters_warm["crossings"]},
+            **extra,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def plain_rates(g, model, n_prefix, stream, c_pool, n_full):
+    """The plain forms (one thread per package, global tables, per-lane atomics) on a
+    package prefix of the same workload, FP32 and FP64, against the pool on the same
+    prefix."""
+    import torch
+    from paper_1201_3588_gb300 import rt
+    out = {"packages": n_prefix}
+    for name, kern in (("pool_f32", rt.KERNEL_POOL), ("plain_f32", rt.KERNEL_PLAIN_F32),
+                       ("plain_f64", rt.KERNEL_PLAIN_F64)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        g.reset(stream)
+        a.record(stream)
+        g.transport(n_prefix, seed=77, kernel=kern, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        s = a.elapsed_time(b) / 1e3
+        out[name] = n_prefix / s
+    out["pool_over_plain_f32"] = out["pool_f32"] / out["plain_f32"]
+    out["pool_over_plain_f64"] = out["pool_f32"] / out["plain_f64"]
+    return out
+
+
+def e2e_rate(model, n, world, first, steps):
+    """Same metric through the public API with host buffers: create the grid from
+    host arrays, set dust and source, transport, temperatures and spectrum back to
+    host, destroy -- all inside the timed region."""
+    import numpy as np
+    import torch
+    from paper_1201_3588_gb300 import rt
+    S, N, B = model.n_species, model.tree.n_leaves, model.n_bins
+    T_host = np.zeros((S, N), dtype=np.float32)
+    times = []
+    for k in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with rt.Grid(model) as g:
+            g.emit_star(n * world)
+            g.transport(n, seed=5000 + k, first_id=first)
+            g.temperatures(out=T_host)
+            sed, eps = g.sed()
+        torch.cuda.synchronize()
+        if k > 0:  # the first pass warms the process
+            times.append(time.perf_counter() - t0)
+    t = model.tree
+    h2d = 4 * t.n_base ** 3 + 32 * t.n_blocks + 4 * S * N + N + 8 * (B + 1) + 24 * S * B
+    d2h = 4 * S * N + 16 * model.n_sed_dirs * B + 8 * S * 1024 + 8
+    return {"value": n * world / (sum(times) / len(times)), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": 1e3 * sum(times) / len(times)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * rt.h -- C ABI of librt_gb300: Monte Carlo dust radiative transfer with photon
+ * packages of constant energy through a grid of cubes and subcubes, on one GB300
+ * (sm_103a), after Siebenmorgen, Heymann & Kruegel, "PAH in vectorized three
+ * dimensional Monte Carlo dust radiative transfer models", Sec. 2.
+ *
+ * Conventions shared by every entry point:
+ *  - Units are cgs (cm, g, s, erg, Hz, K). The domain is the cube
+ *    [-half_size_cm, half_size_cm]^3 cut into n_base^3 base cubes.
+ *  - Every call returns an rt_status; nothing aborts and no C++ exception crosses
+ *    the ABI. rt_status_string() names a status.
+ *  - Input arrays are read during the call and copied; the caller keeps
+ *    ownership. Output arrays are caller-owned; `mem` says whether a pointer is
+ *    host (RT_MEM_HOST) or device (RT_MEM_DEVICE) memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls that
+ *    launch work are asynchronous on that stream, except where a host output is
+ *    requested, in which case the call waits for its own copy.
+ *  - Device-side faults of the method (a malformed tree reached by a package, a
+ *    time budget exceeded) are recorded in a status word on the device; the next
+ *    call that synchronises (rt_get_counters, rt_sed, a host-memory output)
+ *    returns them as RT_ERR_DEVICE or RT_ERR_TIMEOUT.
+ *  - A handle is used by one host thread at a time.
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_grid rt_grid;
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_ARG = 1,      /* invalid argument or inconsistent sizes */
+    RT_ERR_OOM = 2,      /* device or host allocation failed */
+    RT_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    RT_ERR_TIMEOUT = 4,  /* a kernel stopped at its time budget; results partial */
+    RT_ERR_STATE = 5,    /* call out of order (e.g. transport before rt_emit_star) */
+    RT_ERR_RANGE = 6,    /* package ids beyond the planned total */
+    RT_ERR_DEVICE = 7    /* a package met a malformed tree; results invalid */
+} rt_status;
+
+/* Re-emission rule after an absorption (Sec. 2, the correction of Bjorkman &
+ * Wood 2001 and its omission in the vectorised code). */
+enum {
+    RT_REEMIT_BW = 0,     /* difference spectrum kappa_abs [B(T(n+1)) - B(T(n))] */
+    RT_REEMIT_NOCORR = 1, /* kappa_abs B(T(n)), T(0) floored at t_min */
+    RT_REEMIT_FROZEN = 2  /* kappa_abs B(T_frozen), per-cell temperatures given */
+};
+
+enum { RT_SOURCE_POINT = 0, RT_SOURCE_BEAM = 1 };
+
+/* Transport kernel forms. POOL is the persistent packet pool (FP32); the PLAIN
+ * forms run one thread per package with per-lane global atomics, in FP32 or FP64. */
+enum { RT_KERNEL_POOL = 0, RT_KERNEL_PLAIN_F32 = 1, RT_KERNEL_PLAIN_F64 = 2 };
+
+enum { RT_MEM_HOST = 0, RT_MEM_DEVICE = 1 };
+
+/* Grid of cubes and subcubes (Sec. 2: space is cut into cubes, and cubes that
+ * need finer resolution are split again into subcubes, the cells).
+ * base[ix + n*(iy + n*iz)] and child[8*block + (ox | oy<<1 | oz<<2)] hold a leaf id
+ * (>= 0) or -(block+1) for a cube split into 2x2x2 children. Every leaf id in
+ * [0, n_leaves) must appear exactly once and no path may exceed max_level. */
+typedef struct rt_grid_desc {
+    double half_size_cm;
+    int32_t n_base;         /* base cubes per axis, 1 .. 2048 */
+    int32_t max_level;      /* refinement levels, 0 .. 7 */
+    int64_t n_blocks;       /* number of 2x2x2 child blocks */
+    int64_t n_leaves;       /* cells (leaves) */
+    const int32_t *base;    /* host, [n_base^3] */
+    const int32_t *child;   /* host, [n_blocks*8]; may be NULL when n_blocks == 0 */
+    int32_t n_species;      /* dust species, 1 .. 8 */
+    int32_t n_bins;         /* frequency bins, 1 .. 1024 */
+    const double *rho;      /* host, [n_species][n_leaves] density, g cm^-3 */
+    const double *nu_edges; /* host, [n_bins+1] bin edges in Hz, ascending */
+    int32_t n_sed_dirs;     /* escape direction bins in cos(theta) w.r.t. +z, >= 1 */
+    int32_t n_temp;         /* temperature-table rows incl. T = 0; 0 selects 1024 */
+    double t_min, t_max;    /* table range in K; 0 selects 1 K and 3000 K */
+} rt_grid_desc;
+
+typedef struct rt_run_opts {
+    int32_t mode;           /* RT_REEMIT_* */
+    int32_t kernel;         /* RT_KERNEL_* */
+    uint64_t max_events;    /* interactions per package before it is capped; 0: 1e7 */
+    int32_t blocks_per_sm;  /* pool: resident blocks per SM; 0: from occupancy */
+    int32_t threads;        /* threads per block, multiple of 32; 0: 256 */
+    int32_t refill_period;  /* pool: steps between refills of dead lanes; 0: 8 */
+    int32_t reserved;
+    double budget_s;        /* device time budget per launch in s; 0: 120 */
+} rt_run_opts;
+
+typedef struct rt_counters {
+    uint64_t emitted, escaped, capped, absorptions, scatters, crossings, errors;
+    uint64_t clamped;       /* absorptions whose energy lay beyond the table's t_max */
+    uint64_t levels;        /* sum over cells entered (crossed or interacted in) of the
+                               cell's refinement level: child-table reads of the walk */
+} rt_counters;
+
+/* Create a grid handle; copies the tree and densities to the device. */
+rt_status rt_grid_create(const rt_grid_desc *d, rt_grid **out);
+
+/* Release every resource of the handle. NULL is accepted. */
+rt_status rt_grid_destroy(rt_grid *g);
+
+/* Dust species `species` (0-based): absorption and scattering opacities per bin
+ * (cm^2 per gram of that species) and the Henyey-Greenstein asymmetry per bin
+ * (Sec. 1-2). is_pah / n_carbon tag PAH species. Host arrays of n_bins. */
+rt_status rt_set_dust(rt_grid *g, int species, const double *kabs, const double *ksca,
+                      const double *g_hg, int n_bins, int is_pah, int n_carbon);
+
+/* The source (Sec. 2: the star sends out packages that all carry the same energy
+ * eps but differ in frequency):
+ * a blackbody of temperature T_star (K) and luminosity L_star (erg/s) at pos_cm,
+ * emitting isotropically (RT_SOURCE_POINT) or along beam_dir (RT_SOURCE_BEAM).
+ * Every package carries eps = L_in / n_packages_total, L_in the part of L_star
+ * inside the frequency grid. */
+rt_status rt_emit_star(rt_grid *g, double T_star, double L_star, const double pos_cm[3],
+                       int source_kind, const double beam_dir[3], uint64_t n_packages_total);
+
+/* Per-cell temperatures [n_species][n_leaves] (K) for RT_REEMIT_FROZEN. */
+rt_status rt_set_frozen_temperatures(rt_grid *g, const float *T, int mem, void *stream);
+
+/* Follow packages first_package_id .. first_package_id + n_packages - 1 (Sec. 2:
+ * optical-depth sampling cell by cell, Henyey-Greenstein scattering, absorption
+ * with isotropic re-emission at nu_new, each absorption adding eps to its cell).
+ * Package k draws its random numbers from Philox4x32-10 with key = seed and
+ * counter (k, event, block), so ranges may be run in any order or split across
+ * calls. Absorption counts and the escaped spectrum accumulate across calls
+ * until rt_reset. o may be NULL (defaults). Asynchronous on `stream`. */
+rt_status rt_transport(rt_grid *g, uint64_t n_packages, uint64_t seed,
+                       uint64_t first_package_id, const rt_run_opts *o, void *stream);
+
+/* Zero the counts, the escaped spectrum and the counters. */
+rt_status rt_reset(rt_grid *g, void *stream);
+
+/* Cell temperatures [n_species][n_leaves] (K) from the counts (Sec. 2: every
+ * absorption adds eps to the cell's energy, which sets its temperature):
+ * n eps = rho V 4 pi sum_b kappa_abs(b) P_b(T), inverted in FP64. Cells without
+ * absorptions (or without the species) get 0. */
+rt_status rt_cell_temperatures(rt_grid *g, float *T_out, int mem, void *stream);
+
+/* Escaped packages per direction and frequency bin, [2][n_sed_dirs][n_bins]:
+ * index 0 counts all escaped packages, index 1 those that never interacted.
+ * eps_out (may be NULL) receives the package energy in erg/s. The spectrum's
+ * luminosity per bin is count * eps. */
+rt_status rt_sed(rt_grid *g, uint64_t *counts_out, int mem, double *eps_out, void *stream);
+
+/* Raw absorption counts [n_species][n_leaves]. */
+rt_status rt_counts(rt_grid *g, uint64_t *out, int mem, void *stream);
+
+/* Replace the absorption counts [n_species][n_leaves] (resuming from a checkpoint,
+ * or loading counts summed over several package ranges, e.g. over ranks). */
+rt_status rt_set_counts(rt_grid *g, const uint64_t *in, int mem, void *stream);
+
+/* Package totals accumulated since the last reset; synchronises the handle's
+ * last stream and reports device-side faults. */
+rt_status rt_get_counters(rt_grid *g, rt_counters *out);
+
+/* Replay: the histories of the listed packages (host ids) in the frozen mode,
+ * one thread per package with the FP32 transport code. Each record holds
+ * {events, absorptions, scatters, crossings, escaped, capped, final_bin,
+ * dir_bin, last_leaf} as int64; out is host memory [n][9]. */
+rt_status rt_trace(rt_grid *g, const uint64_t *ids, int64_t n, uint64_t seed,
+                   uint64_t max_events, int64_t *out);
+
+/* Philox4x32-10 blocks for counters {id_lo, id_hi, event, block} = (ids[i], event,
+ * block) under key = seed, written to out[4*i..4*i+3] (host). Diagnostic. */
+rt_status rt_philox(const uint64_t *ids, int64_t n, uint32_t event, uint32_t block,
+                    uint64_t seed, uint32_t *out);
+
+const char *rt_status_string(rt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT_GB300_H */

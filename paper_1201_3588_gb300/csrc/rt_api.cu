@@ -1,0 +1,667 @@
+// rt_api.cu -- host side of librt_gb300: the C ABI declared in include/rt.h.
+// Validates inputs, owns the device memory of a grid handle, builds the FP64
+// tables on the device and launches the transport and temperature kernels.
+
+#include "../../include/rt.h"
+#include "rt_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace rt;
+
+struct rt_grid {
+  int dev = 0;
+  rt_grid_desc desc{};
+  double d0 = 0;  // base-cube edge, cm
+  DevGrid g{};
+  // device memory owned by the handle
+  int32_t* d_base = nullptr;
+  int32_t* d_child = nullptr;
+  float* d_rho = nullptr;
+  int8_t* d_level = nullptr;
+  unsigned long long* d_count = nullptr;
+  unsigned long long* d_sed = nullptr;
+  unsigned long long* d_counters = nullptr;
+  unsigned long long* d_next = nullptr;
+  unsigned int* d_status = nullptr;
+  // tables
+  double* d_nu = nullptr;
+  double* d_kabs = nullptr;
+  double* d_ksca = nullptr;
+  double* d_ghg = nullptr;
+  double* d_Tgrid = nullptr;
+  double* d_P = nullptr;
+  double* d_S64 = nullptr;
+  float* d_S32 = nullptr;
+  float* d_dcdf = nullptr;
+  Kappa* d_kap = nullptr;
+  float* d_star_cdf = nullptr;
+  double* d_star_frac = nullptr;
+  float* d_Tfrozen = nullptr;
+  float* d_ufrozen = nullptr;
+  float* d_Tscratch = nullptr;
+  // host state
+  std::vector<double> nu, kabs, ksca, ghg;   // [S][B]
+  std::vector<char> dust_set;
+  std::vector<int> is_pah, n_carbon;
+  bool star_set = false;
+  double T_star = 0, L_star = 0, pos[3] = {0, 0, 0}, beam[3] = {0, 0, 1};
+  int source_kind = 0;
+  unsigned long long n_total = 0;
+  bool tables_ready = false;
+  bool frozen_ready = false;
+  double eps = 0, star_frac = 0;
+  DevTables tab{};
+  int n_levels_used = 0;
+};
+
+namespace {
+
+rt_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RT_OK : RT_ERR_CUDA; }
+
+#define RT_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return RT_ERR_CUDA;         \
+  } while (0)
+
+template <typename T>
+rt_status dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return RT_ERR_OOM;
+  }
+  return cuda_status(e);
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_tables(rt_grid* g) {
+  dfree(g->d_nu);
+  dfree(g->d_kabs);
+  dfree(g->d_ksca);
+  dfree(g->d_ghg);
+  dfree(g->d_Tgrid);
+  dfree(g->d_P);
+  dfree(g->d_S64);
+  dfree(g->d_S32);
+  dfree(g->d_dcdf);
+  dfree(g->d_kap);
+  dfree(g->d_star_cdf);
+  dfree(g->d_star_frac);
+  g->tables_ready = false;
+}
+
+void free_all(rt_grid* g) {
+  free_tables(g);
+  dfree(g->d_base);
+  dfree(g->d_child);
+  dfree(g->d_rho);
+  dfree(g->d_level);
+  dfree(g->d_count);
+  dfree(g->d_sed);
+  dfree(g->d_counters);
+  dfree(g->d_next);
+  dfree(g->d_status);
+  dfree(g->d_Tfrozen);
+  dfree(g->d_ufrozen);
+  dfree(g->d_Tscratch);
+}
+
+// Walk the tree from every base cube: every leaf id must appear exactly once,
+// every block be referenced exactly once, and no path exceed max_level.
+rt_status check_tree(const rt_grid_desc* d, std::vector<int8_t>& level, int* max_seen) {
+  const long long n = d->n_base;
+  const long long nb = n * n * n;
+  level.assign((size_t)d->n_leaves, (int8_t)-1);
+  std::vector<char> seen_blk((size_t)d->n_blocks, 0);
+  std::vector<std::pair<int32_t, int>> stk;
+  stk.reserve(64);
+  *max_seen = 0;
+  for (long long i = 0; i < nb; ++i) {
+    stk.clear();
+    stk.push_back({d->base[i], 0});
+    while (!stk.empty()) {
+      auto [node, lev] = stk.back();
+      stk.pop_back();
+      if (lev > d->max_level) return RT_ERR_ARG;
+      if (node >= 0) {
+        if ((long long)node >= d->n_leaves || level[(size_t)node] >= 0) return RT_ERR_ARG;
+        level[(size_t)node] = (int8_t)lev;
+        if (lev > *max_seen) *max_seen = lev;
+      } else {
+        long long blk = -(long long)node - 1;
+        if (blk >= d->n_blocks || seen_blk[(size_t)blk]) return RT_ERR_ARG;
+        seen_blk[(size_t)blk] = 1;
+        for (int o = 0; o < 8; ++o) stk.push_back({d->child[blk * 8 + o], lev + 1});
+      }
+    }
+  }
+  for (long long i = 0; i < d->n_leaves; ++i)
+    if (level[(size_t)i] < 0) return RT_ERR_ARG;
+  for (long long b = 0; b < d->n_blocks; ++b)
+    if (!seen_blk[(size_t)b]) return RT_ERR_ARG;
+  return RT_OK;
+}
+
+rt_status sync_status(rt_grid* g, cudaStream_t s) {
+  RT_CUDA(cudaStreamSynchronize(s));
+  unsigned st = 0;
+  RT_CUDA(cudaMemcpy(&st, g->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st & kStatusTree) return RT_ERR_DEVICE;
+  if (st & kStatusTimeout) return RT_ERR_TIMEOUT;
+  return RT_OK;
+}
+
+rt_status build_tables(rt_grid* g, cudaStream_t s) {
+  if (g->tables_ready) return RT_OK;
+  const int S = g->desc.n_species, B = g->desc.n_bins, nT = g->desc.n_temp;
+  for (int i = 0; i < S; ++i)
+    if (!g->dust_set[i]) return RT_ERR_STATE;
+  if (!g->star_set) return RT_ERR_STATE;
+  free_tables(g);
+  rt_status st;
+#define ALLOC(p, n) if ((st = dalloc(&(p), (n))) != RT_OK) { free_tables(g); return st; }
+  ALLOC(g->d_nu, (size_t)B + 1);
+  ALLOC(g->d_kabs, (size_t)S * B);
+  ALLOC(g->d_ksca, (size_t)S * B);
+  ALLOC(g->d_ghg, (size_t)S * B);
+  ALLOC(g->d_Tgrid, (size_t)nT);
+  ALLOC(g->d_P, (size_t)nT * B);
+  ALLOC(g->d_S64, (size_t)S * nT);
+  ALLOC(g->d_S32, (size_t)S * nT);
+  ALLOC(g->d_dcdf, (size_t)S * (nT - 1) * B);
+  ALLOC(g->d_kap, (size_t)S * B);
+  ALLOC(g->d_star_cdf, (size_t)B);
+  ALLOC(g->d_star_frac, 1);
+#undef ALLOC
+  RT_CUDA(cudaMemcpyAsync(g->d_nu, g->nu.data(), sizeof(double) * (B + 1),
+                          cudaMemcpyHostToDevice, s));
+  RT_CUDA(cudaMemcpyAsync(g->d_kabs, g->kabs.data(), sizeof(double) * S * B,
+                          cudaMemcpyHostToDevice, s));
+  RT_CUDA(cudaMemcpyAsync(g->d_ksca, g->ksca.data(), sizeof(double) * S * B,
+                          cudaMemcpyHostToDevice, s));
+  RT_CUDA(cudaMemcpyAsync(g->d_ghg, g->ghg.data(), sizeof(double) * S * B,
+                          cudaMemcpyHostToDevice, s));
+  TableBuild tb{};
+  tb.S = S;
+  tb.B = B;
+  tb.n_T = nT;
+  tb.nu = g->d_nu;
+  tb.kabs = g->d_kabs;
+  tb.ksca = g->d_ksca;
+  tb.ghg = g->d_ghg;
+  tb.T_star = g->T_star;
+  tb.t_min = g->desc.t_min;
+  tb.t_max = g->desc.t_max;
+  tb.Tgrid = g->d_Tgrid;
+  tb.P = g->d_P;
+  tb.S64 = g->d_S64;
+  tb.S32 = g->d_S32;
+  tb.dcdf = g->d_dcdf;
+  tb.kap = g->d_kap;
+  tb.star_cdf = g->d_star_cdf;
+  tb.star_frac = g->d_star_frac;
+  RT_CUDA(launch_build_tables(tb, s));
+  // S(t_min) per species: table row 1 is exactly t_min
+  std::vector<double> S64((size_t)S * nT);
+  RT_CUDA(cudaMemcpyAsync(S64.data(), g->d_S64, sizeof(double) * S * nT,
+                          cudaMemcpyDeviceToHost, s));
+  RT_CUDA(cudaMemcpyAsync(&g->star_frac, g->d_star_frac, sizeof(double),
+                          cudaMemcpyDeviceToHost, s));
+  RT_CUDA(cudaStreamSynchronize(s));
+  dfree(g->d_P);
+  g->eps = g->L_star * g->star_frac / (double)g->n_total;
+  DevTables& t = g->tab;
+  t = DevTables{};
+  t.kap = g->d_kap;
+  t.star_cdf = g->d_star_cdf;
+  t.S32 = g->d_S32;
+  t.S64 = g->d_S64;
+  t.Tgrid = g->d_Tgrid;
+  t.dcdf = g->d_dcdf;
+  t.u_frozen = nullptr;
+  for (int i = 0; i < S; ++i) t.u_tmin[i] = (float)S64[(size_t)i * nT + 1];
+  for (int l = 0; l < kMaxLevels; ++l) {
+    double V = std::pow(g->d0 * std::ldexp(1.0, -l), 3.0);
+    t.eps_over_V[l] = g->eps / V;
+    t.eps_d0_over_V[l] = (float)(g->eps * g->d0 / V);
+  }
+  t.d0 = g->d0;
+  g->tables_ready = true;
+  g->frozen_ready = false;
+  return RT_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool finite3(const double* v) {
+  return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rt_status_string(rt_status s) {
+  switch (s) {
+    case RT_OK: return "ok";
+    case RT_ERR_ARG: return "invalid argument";
+    case RT_ERR_OOM: return "out of memory";
+    case RT_ERR_CUDA: return "CUDA runtime error";
+    case RT_ERR_TIMEOUT: return "kernel stopped at its time budget";
+    case RT_ERR_STATE: return "call out of order";
+    case RT_ERR_RANGE: return "package ids beyond the planned total";
+    case RT_ERR_DEVICE: return "malformed grid met on the device";
+  }
+  return "unknown status";
+}
+
+rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
+  if (!d || !out) return RT_ERR_ARG;
+  *out = nullptr;
+  if (!(d->half_size_cm > 0) || !std::isfinite(d->half_size_cm)) return RT_ERR_ARG;
+  if (d->n_base < 1 || d->n_base > 2048 || d->max_level < 0 || d->max_level >= kMaxLevels)
+    return RT_ERR_ARG;
+  if ((long long)d->n_base << d->max_level > (1ll << 24)) return RT_ERR_ARG;
+  if (d->n_species < 1 || d->n_species > kMaxSpecies) return RT_ERR_ARG;
+  if (d->n_bins < 1 || d->n_bins > kMaxBins || d->n_sed_dirs < 1 || d->n_sed_dirs > 1024)
+    return RT_ERR_ARG;
+  if (d->n_leaves < 1 || d->n_leaves > 0x7fffffffll || d->n_blocks < 0 ||
+      d->n_blocks > 0x7fffffffll)
+    return RT_ERR_ARG;
+  if (!d->base || !d->rho || !d->nu_edges || (d->n_blocks > 0 && !d->child))
+    return RT_ERR_ARG;
+  for (int b = 0; b <= d->n_bins; ++b)
+    if (!(d->nu_edges[b] > 0) || !std::isfinite(d->nu_edges[b]) ||
+        (b > 0 && !(d->nu_edges[b] > d->nu_edges[b - 1])))
+      return RT_ERR_ARG;
+  const long long S = d->n_species, N = d->n_leaves;
+  for (long long i = 0; i < S * N; ++i)
+    if (!(d->rho[i] >= 0) || !std::isfinite(d->rho[i])) return RT_ERR_ARG;
+
+  rt_grid* g = new (std::nothrow) rt_grid();
+  if (!g) return RT_ERR_OOM;
+  g->desc = *d;
+  g->desc.base = nullptr;
+  g->desc.child = nullptr;
+  g->desc.rho = nullptr;
+  g->desc.nu_edges = nullptr;
+  if (g->desc.n_temp == 0) g->desc.n_temp = 1024;
+  if (g->desc.t_min == 0) g->desc.t_min = 1.0;
+  if (g->desc.t_max == 0) g->desc.t_max = 3000.0;
+  if (g->desc.n_temp < 3 || g->desc.n_temp > 65536 || !(g->desc.t_min > 0) ||
+      !(g->desc.t_max > g->desc.t_min)) {
+    delete g;
+    return RT_ERR_ARG;
+  }
+  std::vector<int8_t> level;
+  int max_seen = 0;
+  rt_status st = check_tree(d, level, &max_seen);
+  if (st != RT_OK) {
+    delete g;
+    return st;
+  }
+  g->n_levels_used = max_seen + 1;
+  g->d0 = 2.0 * d->half_size_cm / d->n_base;
+  g->nu.assign(d->nu_edges, d->nu_edges + d->n_bins + 1);
+  g->kabs.assign((size_t)S * d->n_bins, 0.0);
+  g->ksca.assign((size_t)S * d->n_bins, 0.0);
+  g->ghg.assign((size_t)S * d->n_bins, 0.0);
+  g->dust_set.assign((size_t)S, 0);
+  g->is_pah.assign((size_t)S, 0);
+  g->n_carbon.assign((size_t)S, 0);
+  if (cudaGetDevice(&g->dev) != cudaSuccess) {
+    delete g;
+    return RT_ERR_CUDA;
+  }
+  // densities to [N][S] floats times the base-cube edge
+  std::vector<float> rho((size_t)S * N);
+  for (long long c = 0; c < N; ++c)
+    for (long long s = 0; s < S; ++s)
+      rho[(size_t)(c * S + s)] = (float)(d->rho[(size_t)(s * N + c)] * g->d0);
+  const long long nb = (long long)d->n_base * d->n_base * d->n_base;
+  const int B = d->n_bins;
+#define ALLOC(p, n) if ((st = dalloc(&(p), (n))) != RT_OK) { free_all(g); delete g; return st; }
+  ALLOC(g->d_base, (size_t)nb);
+  ALLOC(g->d_child, (size_t)d->n_blocks * 8);
+  ALLOC(g->d_rho, (size_t)S * N);
+  ALLOC(g->d_level, (size_t)N);
+  ALLOC(g->d_count, (size_t)S * N);
+  ALLOC(g->d_sed, (size_t)2 * d->n_sed_dirs * B);
+  ALLOC(g->d_counters, (size_t)kNumCounters);
+  ALLOC(g->d_next, 1);
+  ALLOC(g->d_status, 1);
+#undef ALLOC
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_base, d->base, sizeof(int32_t) * nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && d->n_blocks > 0)
+    e = cudaMemcpy(g->d_child, d->child, sizeof(int32_t) * 8 * d->n_blocks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_rho, rho.data(), sizeof(float) * S * N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_level, level.data(), (size_t)N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(g->d_count, 0, sizeof(unsigned long long) * S * N);
+  if (e == cudaSuccess) e = cudaMemset(g->d_sed, 0, sizeof(unsigned long long) * 2 * d->n_sed_dirs * B);
+  if (e == cudaSuccess) e = cudaMemset(g->d_counters, 0, sizeof(unsigned long long) * kNumCounters);
+  if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    free_all(g);
+    delete g;
+    return RT_ERR_CUDA;
+  }
+  g->g.base = g->d_base;
+  g->g.child = g->d_child;
+  g->g.rho = g->d_rho;
+  g->g.level = g->d_level;
+  g->g.n_leaves = N;
+  g->g.n_blocks = d->n_blocks;
+  g->g.n_base = d->n_base;
+  g->g.max_level = d->max_level;
+  g->g.S = (int)S;
+  g->g.B = B;
+  g->g.n_dir = d->n_sed_dirs;
+  g->g.n_T = g->desc.n_temp;
+  *out = g;
+  return RT_OK;
+}
+
+rt_status rt_grid_destroy(rt_grid* g) {
+  if (!g) return RT_OK;
+  cudaSetDevice(g->dev);
+  free_all(g);
+  delete g;
+  return RT_OK;
+}
+
+rt_status rt_set_dust(rt_grid* g, int species, const double* kabs, const double* ksca,
+                      const double* g_hg, int n_bins, int is_pah, int n_carbon) {
+  if (!g || !kabs || !ksca || !g_hg) return RT_ERR_ARG;
+  if (species < 0 || species >= g->desc.n_species || n_bins != g->desc.n_bins)
+    return RT_ERR_ARG;
+  double tot_abs = 0;
+  for (int b = 0; b < n_bins; ++b) {
+    if (!(kabs[b] >= 0) || !(ksca[b] >= 0) || !std::isfinite(kabs[b]) ||
+        !std::isfinite(ksca[b]) || !(g_hg[b] > -1) || !(g_hg[b] < 1))
+      return RT_ERR_ARG;
+    tot_abs += kabs[b];
+  }
+  if (!(tot_abs > 0)) return RT_ERR_ARG;  // a species must be able to emit
+  size_t o = (size_t)species * n_bins;
+  std::memcpy(&g->kabs[o], kabs, sizeof(double) * n_bins);
+  std::memcpy(&g->ksca[o], ksca, sizeof(double) * n_bins);
+  std::memcpy(&g->ghg[o], g_hg, sizeof(double) * n_bins);
+  g->dust_set[(size_t)species] = 1;
+  g->is_pah[(size_t)species] = is_pah;
+  g->n_carbon[(size_t)species] = n_carbon;
+  g->tables_ready = false;
+  return RT_OK;
+}
+
+rt_status rt_emit_star(rt_grid* g, double T_star, double L_star, const double pos_cm[3],
+                       int source_kind, const double beam_dir[3],
+                       uint64_t n_packages_total) {
+  if (!g || !pos_cm) return RT_ERR_ARG;
+  if (!(T_star > 0) || !(L_star > 0) || !std::isfinite(T_star) || !std::isfinite(L_star))
+    return RT_ERR_ARG;
+  if (n_packages_total == 0 || !finite3(pos_cm)) return RT_ERR_ARG;
+  double H = g->desc.half_size_cm;
+  for (int a = 0; a < 3; ++a)
+    if (pos_cm[a] < -H || pos_cm[a] > H) return RT_ERR_ARG;
+  if (source_kind != RT_SOURCE_POINT && source_kind != RT_SOURCE_BEAM) return RT_ERR_ARG;
+  double bd[3] = {0, 0, 1};
+  if (source_kind == RT_SOURCE_BEAM) {
+    if (!beam_dir || !finite3(beam_dir)) return RT_ERR_ARG;
+    double nrm = std::sqrt(beam_dir[0] * beam_dir[0] + beam_dir[1] * beam_dir[1] +
+                           beam_dir[2] * beam_dir[2]);
+    if (!(nrm > 0)) return RT_ERR_ARG;
+    for (int a = 0; a < 3; ++a) bd[a] = beam_dir[a] / nrm;
+  }
+  g->T_star = T_star;
+  g->L_star = L_star;
+  for (int a = 0; a < 3; ++a) {
+    g->pos[a] = pos_cm[a];
+    g->beam[a] = bd[a];
+  }
+  g->source_kind = source_kind;
+  g->n_total = n_packages_total;
+  g->star_set = true;
+  g->tables_ready = false;
+  return RT_OK;
+}
+
+rt_status rt_set_frozen_temperatures(rt_grid* g, const float* T, int mem, void* stream) {
+  if (!g || !T) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  const size_t n = (size_t)g->desc.n_species * g->desc.n_leaves;
+  if (!g->d_Tfrozen && (st = dalloc(&g->d_Tfrozen, n)) != RT_OK) return st;
+  if (!g->d_ufrozen && (st = dalloc(&g->d_ufrozen, n)) != RT_OK) return st;
+  RT_CUDA(cudaMemcpyAsync(g->d_Tfrozen, T, sizeof(float) * n,
+                          mem == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                               : cudaMemcpyHostToDevice,
+                          s));
+  RT_CUDA(launch_frozen_u(g->g, g->tab, g->d_Tfrozen, g->d_ufrozen, (float)g->desc.t_min, s));
+  if (mem != RT_MEM_DEVICE) RT_CUDA(cudaStreamSynchronize(s));
+  g->frozen_ready = true;
+  return RT_OK;
+}
+
+rt_status rt_reset(rt_grid* g, void* stream) {
+  if (!g) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  const size_t S = g->desc.n_species, N = g->desc.n_leaves;
+  RT_CUDA(cudaMemsetAsync(g->d_count, 0, sizeof(unsigned long long) * S * N, s));
+  RT_CUDA(cudaMemsetAsync(g->d_sed, 0,
+                          sizeof(unsigned long long) * 2 * g->desc.n_sed_dirs * g->desc.n_bins,
+                          s));
+  RT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s));
+  RT_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), s));
+  return RT_OK;
+}
+
+static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64_t first,
+                          const rt_run_opts* o, DevRun* r) {
+  int mode = o ? o->mode : RT_REEMIT_BW;
+  if (mode < 0 || mode > 2) return RT_ERR_ARG;
+  if (mode == RT_REEMIT_FROZEN && !g->frozen_ready) return RT_ERR_STATE;
+  *r = DevRun{};
+  r->seed = seed;
+  r->first_id = first;
+  r->n_packages = n_packages;
+  r->max_events = (o && o->max_events) ? o->max_events : 10000000ull;
+  if (r->max_events > 0xffffffffull - 1) r->max_events = 0xffffffffull - 1;
+  r->next = g->d_next;
+  r->count = g->d_count;
+  r->sed = g->d_sed;
+  r->counters = g->d_counters;
+  r->status = g->d_status;
+  for (int a = 0; a < 3; ++a) {
+    double p = (g->pos[a] + g->desc.half_size_cm) / g->d0;
+    r->src64[a] = p;
+    r->src[a] = (float)p;
+    r->beam64[a] = g->beam[a];
+    r->beam[a] = (float)g->beam[a];
+  }
+  r->source_kind = g->source_kind;
+  r->mode = mode;
+  r->refill_period = (o && o->refill_period > 0) ? o->refill_period : 8;
+  double budget = (o && o->budget_s > 0) ? o->budget_s : 120.0;
+  r->budget_ns = (unsigned long long)(budget * 1e9);
+  return RT_OK;
+}
+
+rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
+                       uint64_t first_package_id, const rt_run_opts* o, void* stream) {
+  if (!g) return RT_ERR_ARG;
+  int kernel = o ? o->kernel : RT_KERNEL_POOL;
+  int threads = (o && o->threads > 0) ? o->threads : 256;
+  if (kernel < 0 || kernel > 2 || threads % 32 != 0 || threads > 256) return RT_ERR_ARG;
+  if (o && (o->blocks_per_sm < 0 || o->blocks_per_sm > 32 || o->refill_period < 0))
+    return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  if (first_package_id > g->n_total || n_packages > g->n_total - first_package_id)
+    return RT_ERR_RANGE;
+  if (n_packages == 0) return RT_OK;
+  DevRun r;
+  if ((st = fill_run(g, n_packages, seed, first_package_id, o, &r)) != RT_OK) return st;
+  DevTables t = g->tab;
+  t.u_frozen = g->d_ufrozen;
+  if (kernel == RT_KERNEL_POOL) {
+    RT_CUDA(cudaMemsetAsync(g->d_next, 0, sizeof(unsigned long long), s));
+    RT_CUDA(launch_transport_pool(g->g, t, r, o ? o->blocks_per_sm : 0, threads, s));
+  } else {
+    RT_CUDA(launch_transport_plain(g->g, t, r, kernel == RT_KERNEL_PLAIN_F64, threads, s));
+  }
+  return RT_OK;
+}
+
+rt_status rt_cell_temperatures(rt_grid* g, float* T_out, int mem, void* stream) {
+  if (!g || !T_out) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  const size_t n = (size_t)g->desc.n_species * g->desc.n_leaves;
+  float* dst = T_out;
+  if (mem != RT_MEM_DEVICE) {
+    if (!g->d_Tscratch && (st = dalloc(&g->d_Tscratch, n)) != RT_OK) return st;
+    dst = g->d_Tscratch;
+  }
+  RT_CUDA(launch_temperatures(g->g, g->tab, g->d_count, dst, g->d_counters, s));
+  if (mem != RT_MEM_DEVICE) {
+    RT_CUDA(cudaMemcpyAsync(T_out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    return sync_status(g, s);
+  }
+  return RT_OK;
+}
+
+rt_status rt_sed(rt_grid* g, uint64_t* counts_out, int mem, double* eps_out, void* stream) {
+  if (!g || !counts_out) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  const size_t n = (size_t)2 * g->desc.n_sed_dirs * g->desc.n_bins;
+  RT_CUDA(cudaMemcpyAsync(counts_out, g->d_sed, sizeof(unsigned long long) * n,
+                          mem == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                               : cudaMemcpyDeviceToHost,
+                          s));
+  if (eps_out) *eps_out = g->eps;
+  if (mem != RT_MEM_DEVICE) return sync_status(g, s);
+  return RT_OK;
+}
+
+rt_status rt_counts(rt_grid* g, uint64_t* out, int mem, void* stream) {
+  if (!g || !out) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  const size_t n = (size_t)g->desc.n_species * g->desc.n_leaves;
+  RT_CUDA(cudaMemcpyAsync(out, g->d_count, sizeof(unsigned long long) * n,
+                          mem == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                               : cudaMemcpyDeviceToHost,
+                          s));
+  if (mem != RT_MEM_DEVICE) return sync_status(g, s);
+  return RT_OK;
+}
+
+rt_status rt_set_counts(rt_grid* g, const uint64_t* in, int mem, void* stream) {
+  if (!g || !in) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  const size_t n = (size_t)g->desc.n_species * g->desc.n_leaves;
+  RT_CUDA(cudaMemcpyAsync(g->d_count, in, sizeof(unsigned long long) * n,
+                          mem == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                               : cudaMemcpyHostToDevice,
+                          s));
+  if (mem != RT_MEM_DEVICE) RT_CUDA(cudaStreamSynchronize(s));
+  return RT_OK;
+}
+
+rt_status rt_get_counters(rt_grid* g, rt_counters* out) {
+  if (!g || !out) return RT_ERR_ARG;
+  RT_CUDA(cudaSetDevice(g->dev));
+  RT_CUDA(cudaDeviceSynchronize());
+  unsigned long long c[kNumCounters];
+  RT_CUDA(cudaMemcpy(c, g->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+  out->emitted = c[kCEmitted];
+  out->escaped = c[kCEscaped];
+  out->capped = c[kCCapped];
+  out->absorptions = c[kCAbsorptions];
+  out->scatters = c[kCScatters];
+  out->crossings = c[kCCrossings];
+  out->errors = c[kCErrors];
+  out->clamped = c[kCClamped];
+  out->levels = c[kCLevels];
+  return sync_status(g, nullptr);
+}
+
+rt_status rt_trace(rt_grid* g, const uint64_t* ids, int64_t n, uint64_t seed,
+                   uint64_t max_events, int64_t* out) {
+  if (!g || (n > 0 && (!ids || !out)) || n < 0) return RT_ERR_ARG;
+  if (n == 0) return RT_OK;
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, nullptr);
+  if (st != RT_OK) return st;
+  if (!g->frozen_ready) return RT_ERR_STATE;
+  rt_run_opts o{};
+  o.mode = RT_REEMIT_FROZEN;
+  o.max_events = max_events;
+  DevRun r;
+  if ((st = fill_run(g, 0, seed, 0, &o, &r)) != RT_OK) return st;
+  DevTables t = g->tab;
+  t.u_frozen = g->d_ufrozen;
+  unsigned long long* d_ids = nullptr;
+  long long* d_out = nullptr;
+  if ((st = dalloc(&d_ids, (size_t)n)) != RT_OK) return st;
+  if ((st = dalloc(&d_out, (size_t)n * 9)) != RT_OK) {
+    dfree(d_ids);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(d_ids, ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_trace(g->g, t, r, d_ids, n, d_out, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(int64_t) * 9 * n, cudaMemcpyDeviceToHost);
+  dfree(d_ids);
+  dfree(d_out);
+  if (e != cudaSuccess) return RT_ERR_CUDA;
+  return sync_status(g, nullptr);
+}
+
+rt_status rt_philox(const uint64_t* ids, int64_t n, uint32_t event, uint32_t block,
+                    uint64_t seed, uint32_t* out) {
+  if (n < 0 || (n > 0 && (!ids || !out))) return RT_ERR_ARG;
+  if (n == 0) return RT_OK;
+  unsigned long long* d_ids = nullptr;
+  unsigned* d_out = nullptr;
+  rt_status st;
+  if ((st = dalloc(&d_ids, (size_t)n)) != RT_OK) return st;
+  if ((st = dalloc(&d_out, (size_t)n * 4)) != RT_OK) {
+    dfree(d_ids);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(d_ids, ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_philox(d_ids, n, event, block, seed, d_out, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+  dfree(d_ids);
+  dfree(d_out);
+  return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// rt_internal.h -- structures shared by the host side and the kernels of
+// librt_gb300. Not part of the public ABI (include/rt.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rt {
+
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxLevels = 8;     // levels 0 .. 7
+constexpr int kMaxBins = 1024;
+
+// Device status bits.
+constexpr unsigned kStatusTree = 1u;     // a package met a malformed tree
+constexpr unsigned kStatusTimeout = 2u;  // a launch ran past its time budget
+
+// Indices into the device counter array.
+enum Counter {
+  kCEmitted = 0, kCEscaped, kCCapped, kCAbsorptions, kCScatters, kCCrossings,
+  kCErrors, kCClamped, kCLevels, kNumCounters
+};
+
+// Geometry and densities (device pointers), passed by value.
+struct DevGrid {
+  const int32_t* base;     // [n^3]
+  const int32_t* child;    // [n_blocks*8]
+  const float* rho;        // [n_leaves][S]: density times the base-cube edge, g cm^-2
+  const int8_t* level;     // [n_leaves] refinement level of every leaf
+  long long n_leaves, n_blocks;
+  int n_base, max_level, S, B, n_dir, n_T;
+};
+
+// Per-bin opacity record for one species, kept in shared memory during transport.
+struct Kappa {
+  float kext, ksca, kabs, g;  // cm^2 g^-1, cm^2 g^-1, cm^2 g^-1, HG asymmetry
+};
+
+// Tables built in FP64 on the device and stored for transport.
+struct DevTables {
+  const Kappa* kap;           // [B][S]
+  const float* star_cdf;      // [B] normalised cumulative stellar spectrum
+  const float* S32;           // [S][n_T] emitted power per gram at the table rows
+  const double* S64;          // [S][n_T]
+  const double* Tgrid;        // [n_T], Tgrid[0] = 0
+  const float* dcdf;          // [S][n_T-1][B] normalised cumulative of row differences
+  const float* u_frozen;      // [S][n_leaves] (frozen mode) or null
+  float u_tmin[kMaxSpecies];  // S_s(t_min)
+  float eps_d0_over_V[kMaxLevels];   // eps * d0 / V(level), erg s^-1 cm^-2 (FP32)
+  double eps_over_V[kMaxLevels];     // eps / V(level) (FP64, temperatures)
+  double d0;                  // base-cube edge, cm
+};
+
+// One transport launch.
+struct DevRun {
+  unsigned long long seed, first_id, n_packages, max_events;
+  unsigned long long* next;       // pool: packages handed out so far
+  unsigned long long* count;      // [S][n_leaves]
+  unsigned long long* sed;        // [2][n_dir][B]
+  unsigned long long* counters;   // [kNumCounters]
+  unsigned int* status;
+  float src[3];                   // source position, base-cube units
+  float beam[3];
+  double src64[3];
+  double beam64[3];
+  int source_kind, mode, refill_period;
+  int sed_in_smem;                // pool: escaped-spectrum histogram in shared memory
+  unsigned long long budget_ns;
+};
+
+// Kernel launchers (rt_transport.cu, rt_tables.cu).
+cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
+                                  int blocks_per_sm, int threads, cudaStream_t s);
+cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const DevRun& r,
+                                   bool fp64, int threads, cudaStream_t s);
+cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
+                         const unsigned long long* ids, long long n, long long* out,
+                         cudaStream_t s);
+cudaError_t launch_philox(const unsigned long long* ids, long long n, unsigned event,
+                          unsigned block, unsigned long long seed, unsigned* out,
+                          cudaStream_t s);
+
+struct TableBuild {
+  int S, B, n_T;
+  const double* nu;          // [B+1]
+  const double* kabs;        // [S][B]
+  const double* ksca;        // [S][B]
+  const double* ghg;         // [S][B]
+  double T_star, t_min, t_max;
+  // outputs
+  double* Tgrid;             // [n_T]
+  double* P;                 // scratch [n_T][B]
+  double* S64;               // [S][n_T]
+  float* S32;                // [S][n_T]
+  float* dcdf;               // [S][n_T-1][B]
+  Kappa* kap;                // [B][S]
+  float* star_cdf;           // [B]
+  double* star_frac;         // [1] in-range fraction of the stellar blackbody
+};
+cudaError_t launch_build_tables(const TableBuild& tb, cudaStream_t s);
+
+cudaError_t launch_frozen_u(const DevGrid& g, const DevTables& t, const float* T_frozen,
+                            float* u_frozen, float t_min, cudaStream_t s);
+cudaError_t launch_temperatures(const DevGrid& g, const DevTables& t,
+                                const unsigned long long* count, float* T_out,
+                                unsigned long long* counters, cudaStream_t s);
+
+}  // namespace rt

@@ -1,0 +1,265 @@
+// rt_tables.cu -- FP64 table builders, frozen-temperature energies and the
+// per-cell temperature update of librt_gb300.
+//
+// The Planck function integrated over a frequency bin is evaluated in closed
+// form: with x = h nu / k T, the integral of B_nu over [nu0, nu1] equals
+// (2 k^4 T^4 / h^3 c^2) [G(x0) - G(x1)], G(x) the integral of t^3/(e^t - 1) from x
+// to infinity, summed as sum_k e^{-kx} (x^3/k + 3x^2/k^2 + 6x/k^3 + 6/k^4) for
+// x >= 1/2 and as pi^4/15 minus the Bernoulli series of the integral from 0 to x
+// below that.
+
+#include "rt_internal.h"
+
+#include <math.h>
+
+namespace rt {
+namespace {
+
+constexpr double kH = 6.62607015e-27;
+constexpr double kK = 1.380649e-16;
+constexpr double kC = 2.99792458e10;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kPi4Over15 = 6.4939394022668291491;  // pi^4 / 15
+
+// integral_0^x t^3/(e^t-1) dt for 0 <= x < 1/2: sum_n (B_n/n!) x^(n+3)/(n+3)
+__device__ double planck_head(double x) {
+  // B_n / n! for n = 0, 1, 2, 4, ..., 20 (odd n > 1 vanish)
+  const double c0 = 1.0, c1 = -0.5;
+  const double ce[10] = {1.0 / 12.0,
+                         -1.0 / 720.0,
+                         1.0 / 30240.0,
+                         -1.0 / 1209600.0,
+                         1.0 / 47900160.0,
+                         -691.0 / 1307674368000.0,
+                         1.0 / 74724249600.0,
+                         -3617.0 / 10670622842880000.0,
+                         43867.0 / 5109094217170944000.0,
+                         -174611.0 / 802857662698291200000.0};
+  double x2 = x * x, x3 = x2 * x;
+  double s = c0 * x3 / 3.0 + c1 * x3 * x / 4.0;
+  double xp = x3 * x2;  // x^(n+3) for n = 2
+  for (int k = 0; k < 10; ++k) {
+    int n = 2 * k + 2;
+    s += ce[k] * xp / (double)(n + 3);
+    xp *= x2;
+  }
+  return s;
+}
+
+// integral_x^inf t^3/(e^t-1) dt for x >= 1/2
+__device__ double planck_tail(double x) {
+  double s = 0.0;
+  double x2 = x * x, x3 = x2 * x;
+  for (int k = 1; k <= 400; ++k) {
+    double kk = (double)k;
+    double e = exp(-kk * x);
+    double term = e * (x3 / kk + 3.0 * x2 / (kk * kk) + 6.0 * x / (kk * kk * kk) +
+                       6.0 / (kk * kk * kk * kk));
+    s += term;
+    if (term <= 1e-18 * s) break;
+  }
+  return s;
+}
+
+// integral over [nu0, nu1] of B_nu(T) d nu, erg s^-1 cm^-2 sr^-1
+__device__ double planck_bin(double nu0, double nu1, double T) {
+  if (!(T > 0.0)) return 0.0;
+  double a = kH / (kK * T);
+  double x0 = a * nu0, x1 = a * nu1;
+  double d;
+  if (x1 < 0.5) {
+    d = planck_head(x1) - planck_head(x0);
+  } else if (x0 < 0.5) {
+    d = (kPi4Over15 - planck_head(x0)) - planck_tail(x1);
+  } else {
+    d = planck_tail(x0) - planck_tail(x1);
+  }
+  double kT = kK * T;
+  double pref = 2.0 * kT * kT * kT * kT / (kH * kH * kH * kC * kC);
+  return pref * (d > 0.0 ? d : 0.0);
+}
+
+__device__ double table_T(int i, int n_T, double t_min, double t_max) {
+  if (i == 0) return 0.0;
+  if (i == n_T - 1) return t_max;
+  return t_min * pow(t_max / t_min, (double)(i - 1) / (double)(n_T - 2));
+}
+
+__global__ void k_planck_rows(TableBuild tb) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long tot = (long long)tb.n_T * tb.B;
+  if (idx >= tot) return;
+  int i = (int)(idx / tb.B), b = (int)(idx % tb.B);
+  double T = table_T(i, tb.n_T, tb.t_min, tb.t_max);
+  if (b == 0) tb.Tgrid[i] = T;
+  tb.P[idx] = planck_bin(tb.nu[b], tb.nu[b + 1], T);
+}
+
+// one thread per (species, row): S(T_i) = 4 pi sum_b kappa_abs P_b(T_i)
+__global__ void k_emission_rows(TableBuild tb) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= tb.S * tb.n_T) return;
+  int s = idx / tb.n_T, i = idx % tb.n_T;
+  const double* ka = tb.kabs + (size_t)s * tb.B;
+  const double* P = tb.P + (size_t)i * tb.B;
+  double acc = 0.0;
+  for (int b = 0; b < tb.B; ++b) acc += ka[b] * P[b];
+  acc *= 4.0 * kPi;
+  tb.S64[idx] = acc;
+  tb.S32[idx] = (float)acc;
+}
+
+// one thread per (species, interval): normalised cumulative of
+// kappa_abs(b) [P_b(T_{i+1}) - P_b(T_i)] over the bins
+__global__ void k_difference_cdfs(TableBuild tb) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int nI = tb.n_T - 1;
+  if (idx >= tb.S * nI) return;
+  int s = idx / nI, i = idx % nI;
+  const double* ka = tb.kabs + (size_t)s * tb.B;
+  const double* P0 = tb.P + (size_t)i * tb.B;
+  const double* P1 = P0 + tb.B;
+  float* out = tb.dcdf + (size_t)idx * tb.B;
+  double tot = 0.0;
+  for (int b = 0; b < tb.B; ++b) {
+    double d = ka[b] * (P1[b] - P0[b]);
+    tot += d > 0.0 ? d : 0.0;
+  }
+  double cum = 0.0;
+  for (int b = 0; b < tb.B; ++b) {
+    double d = ka[b] * (P1[b] - P0[b]);
+    cum += d > 0.0 ? d : 0.0;
+    out[b] = tot > 0.0 ? (float)(cum / tot) : 1.0f;
+  }
+  out[tb.B - 1] = 1.0f;
+}
+
+__global__ void k_opacity_and_star(TableBuild tb) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < tb.B) {
+    for (int s = 0; s < tb.S; ++s) {
+      size_t j = (size_t)s * tb.B + b;
+      Kappa k;
+      k.kabs = (float)tb.kabs[j];
+      k.ksca = (float)tb.ksca[j];
+      k.kext = (float)(tb.kabs[j] + tb.ksca[j]);
+      k.g = (float)tb.ghg[j];
+      tb.kap[(size_t)b * tb.S + s] = k;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < tb.B; ++i) tot += planck_bin(tb.nu[i], tb.nu[i + 1], tb.T_star);
+    double cum = 0.0;
+    for (int i = 0; i < tb.B; ++i) {
+      cum += planck_bin(tb.nu[i], tb.nu[i + 1], tb.T_star);
+      tb.star_cdf[i] = tot > 0.0 ? (float)(cum / tot) : 1.0f;
+    }
+    tb.star_cdf[tb.B - 1] = 1.0f;
+    // sigma = 2 pi^5 k^4 / (15 c^2 h^3)
+    double sigma = 2.0 * pow(kPi, 5.0) * pow(kK, 4.0) / (15.0 * kC * kC * pow(kH, 3.0));
+    double T4 = pow(tb.T_star, 4.0);
+    tb.star_frac[0] = kPi * tot / (sigma * T4);
+  }
+}
+
+// S at temperature T by linear interpolation in T between table rows (the same
+// piecewise-linear model the transport samples from).
+__global__ void k_frozen_u(DevGrid g, DevTables t, const float* T_frozen, float* u_frozen,
+                           float t_min) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long tot = (long long)g.S * g.n_leaves;
+  if (idx >= tot) return;
+  int s = (int)(idx / g.n_leaves);
+  double T = fmax((double)T_frozen[idx], (double)t_min);
+  const double* Tg = t.Tgrid;
+  const double* S = t.S64 + (size_t)s * g.n_T;
+  int n_T = g.n_T;
+  double u;
+  if (T >= Tg[n_T - 1]) {
+    u = S[n_T - 1];
+  } else {
+    int lo = 0, hi = n_T - 1;  // Tg[lo] <= T < Tg[hi]
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (Tg[mid] <= T) lo = mid; else hi = mid;
+    }
+    double w = (T - Tg[lo]) / (Tg[hi] - Tg[lo]);
+    u = S[lo] + w * (S[hi] - S[lo]);
+  }
+  u_frozen[idx] = (float)u;
+}
+
+// T from n eps = M S(T): binary search in the FP64 S table, then power-law
+// (log-log) interpolation between rows; linear from T = 0 in the first interval.
+__global__ void k_temperatures(DevGrid g, DevTables t, const unsigned long long* count,
+                               float* T_out, unsigned long long* counters) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long tot = (long long)g.S * g.n_leaves;
+  bool clamped = false;
+  if (idx < tot) {
+    int s = (int)(idx / g.n_leaves);
+    long long c = idx - (long long)s * g.n_leaves;
+    unsigned long long n = count[idx];
+    float rho_d0 = g.rho[c * g.S + s];
+    float Tv = 0.0f;
+    if (n > 0 && rho_d0 > 0.0f) {
+      int lev = g.level[c];
+      double rho = (double)rho_d0 / t.d0;
+      double u = (double)n * t.eps_over_V[lev] / rho;
+      const double* S = t.S64 + (size_t)s * g.n_T;
+      const double* Tg = t.Tgrid;
+      int n_T = g.n_T;
+      if (u >= S[n_T - 1]) {
+        Tv = (float)Tg[n_T - 1];
+        clamped = true;
+      } else {
+        int lo = 0, hi = n_T - 1;  // S[lo] <= u < S[hi]
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (S[mid] <= u) lo = mid; else hi = mid;
+        }
+        double T;
+        if (lo == 0 || !(S[lo] > 0.0)) {
+          T = Tg[hi] * u / S[hi];
+        } else {
+          double a = log(u / S[lo]) / log(S[hi] / S[lo]);
+          T = Tg[lo] * exp(a * log(Tg[hi] / Tg[lo]));
+        }
+        Tv = (float)T;
+      }
+    }
+    T_out[idx] = Tv;
+  }
+  unsigned m = __ballot_sync(0xffffffffu, clamped);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(&counters[kCClamped], (unsigned long long)__popc(m));
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_build_tables(const TableBuild& tb, cudaStream_t s) {
+  k_planck_rows<<<nblk((long long)tb.n_T * tb.B, 256), 256, 0, s>>>(tb);
+  k_emission_rows<<<nblk((long long)tb.S * tb.n_T, 128), 128, 0, s>>>(tb);
+  k_difference_cdfs<<<nblk((long long)tb.S * (tb.n_T - 1), 128), 128, 0, s>>>(tb);
+  k_opacity_and_star<<<nblk(tb.B, 128), 128, 0, s>>>(tb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frozen_u(const DevGrid& g, const DevTables& t, const float* T_frozen,
+                            float* u_frozen, float t_min, cudaStream_t s) {
+  long long n = (long long)g.S * g.n_leaves;
+  k_frozen_u<<<nblk(n, 256), 256, 0, s>>>(g, t, T_frozen, u_frozen, t_min);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_temperatures(const DevGrid& g, const DevTables& t,
+                                const unsigned long long* count, float* T_out,
+                                unsigned long long* counters, cudaStream_t s) {
+  long long n = (long long)g.S * g.n_leaves;
+  k_temperatures<<<nblk(n, 256), 256, 0, s>>>(g, t, count, T_out, counters);
+  return cudaGetLastError();
+}
+
+}  // namespace rt

@@ -1,0 +1,643 @@
+// rt_transport.cu -- photon-package transport kernels of librt_gb300.
+//
+// A package (Sec. 2) leaves the star with constant energy eps at a frequency bin
+// drawn from the stellar spectrum, samples an optical depth tau = -ln(xi), and
+// walks the grid of cubes and subcubes cell by cell, spending
+// rho * kappa_ext * path of its tau in each cell. Where tau runs out it
+// interacts: with probability kappa_sca / kappa_ext it scatters by the
+// Henyey-Greenstein phase function, otherwise it is absorbed -- the cell's count
+// of absorptions rises by one (an exact integer; eps is constant) and a package
+// of the same energy leaves the absorption spot isotropically at a frequency
+// drawn from the re-emission spectrum. A package that leaves the domain is binned
+// into the escaped spectrum.
+//
+// Random numbers: Philox4x32-10 (Salmon et al. 2011), key = seed, counter =
+// (package id lo, id hi, event index, block). Event 0 is the emission and uses
+// one block: {bin, mu, phi, tau}. Interaction k uses block 0 = {albedo test,
+// species, mu, phi} and block 1 = {tau, energy position, bin, -}. Each 32-bit word
+// maps to the midpoint of one of 2^23 equal sub-intervals of (0,1).
+//
+// Re-emission bin: the three rules of Sec. 2 (the Bjorkman & Wood difference
+// spectrum, its omission, a frozen temperature) are all mixtures over the
+// temperature-table intervals: an energy per gram u is drawn uniformly in
+// [u_lo, u_hi] (BW: [n, n+1] eps/M; no correction: [0, max(n eps/M, S(t_min))];
+// frozen: [0, S(T_frozen)]), the table interval holding u is found in S(T), and
+// the bin is drawn from that interval's normalised cumulative difference
+// kappa_abs [P_b(T_{i+1}) - P_b(T_i)].
+//
+// Geometry: positions are in base-cube units. A point on a face belongs to the
+// cell ahead of the direction of motion. After a face crossing the position is
+// set exactly onto the face (exactly representable) and the other coordinates are
+// clamped into the cell, so every crossing advances the cell index.
+
+#include "rt_internal.h"
+
+#include <math.h>
+
+namespace rt {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------- Philox
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 draw(unsigned long long seed, unsigned long long id,
+                                      unsigned event, unsigned block) {
+  return philox10(make_uint4((unsigned)id, (unsigned)(id >> 32), event, block),
+                  make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+}
+
+template <typename R>
+__device__ __forceinline__ R unit(unsigned x) {
+  return ((R)(x >> 9) + (R)0.5) * (R)(1.0 / 8388608.0);
+}
+
+// ---------------------------------------------------------------- math helpers
+template <typename R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+
+template <typename R>
+__device__ __forceinline__ void sincos2pi(R xi, R* s, R* c);
+template <> __device__ __forceinline__ void sincos2pi(float xi, float* s, float* c) {
+  sincospif(2.0f * xi, s, c);
+}
+template <> __device__ __forceinline__ void sincos2pi(double xi, double* s, double* c) {
+  sincospi(2.0 * xi, s, c);
+}
+
+template <typename R> __device__ __forceinline__ R log_(R x);
+template <> __device__ __forceinline__ float log_(float x) { return logf(x); }
+template <> __device__ __forceinline__ double log_(double x) { return log(x); }
+
+// isotropic direction from two deviates
+template <typename R>
+__device__ __forceinline__ void isotropic(R xmu, R xphi, R d[3]) {
+  R mu = (R)2 * xmu - (R)1;
+  R s = sqrt(fmax((R)0, (R)1 - mu * mu));
+  R sp, cp;
+  sincos2pi(xphi, &sp, &cp);
+  d[0] = s * cp;
+  d[1] = s * sp;
+  d[2] = mu;
+}
+
+// Henyey-Greenstein cos(theta) by inversion of its cumulative distribution
+template <typename R>
+__device__ __forceinline__ R hg_mu(R g, R xi) {
+  if (fabs(g) < (R)1e-6) return (R)2 * xi - (R)1;
+  R f = ((R)1 - g * g) / ((R)1 - g + (R)2 * g * xi);
+  R mu = ((R)1 + g * g - f * f) / ((R)2 * g);
+  return fmin((R)1, fmax((R)-1, mu));
+}
+
+// turn d by polar cosine mu and azimuth 2 pi xphi, azimuth counted from
+// (dx dz, dy dz, -(1-dz^2))/sqrt(1-dz^2) towards (-dy, dx, 0)/sqrt(1-dz^2)
+template <typename R>
+__device__ __forceinline__ void turn(R d[3], R mu, R xphi) {
+  R s = sqrt(fmax((R)0, (R)1 - mu * mu));
+  R sp, cp;
+  sincos2pi(xphi, &sp, &cp);
+  R ux = d[0], uy = d[1], uz = d[2], nx, ny, nz;
+  if (fabs(uz) > (R)0.99999) {
+    nx = s * cp;
+    ny = s * sp;
+    nz = (uz > (R)0 ? mu : -mu);
+  } else {
+    R r2 = (R)1 - uz * uz;
+    R ir = rsqrt_(r2);
+    R r = r2 * ir;
+    nx = mu * ux + s * (ux * uz * cp - uy * sp) * ir;
+    ny = mu * uy + s * (uy * uz * cp + ux * sp) * ir;
+    nz = mu * uz - s * r * cp;
+  }
+  R in = rsqrt_(nx * nx + ny * ny + nz * nz);
+  d[0] = nx * in;
+  d[1] = ny * in;
+  d[2] = nz * in;
+}
+
+// first index whose normalised cumulative value exceeds xi (cdf[n-1] == 1)
+__device__ __forceinline__ int search_cdf(const float* cdf, int n, float xi) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (cdf[mid] > xi) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- grid
+template <typename R>
+__device__ __forceinline__ int cell_index(R q, R d) {
+  R f = floor(q);
+  int i = (int)f;
+  if (d < (R)0 && f == q) --i;
+  return i;
+}
+
+// Leaf holding p when moving along d. Returns 0 inside, 1 outside, -1 malformed.
+template <typename R>
+__device__ __forceinline__ int locate(const DevGrid& g, const R p[3], const R d[3],
+                                      int& leaf, int& level, int I[3]) {
+  const int n = g.n_base;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    I[a] = cell_index(p[a], d[a]);
+    if (I[a] < 0 || I[a] >= n) return 1;
+  }
+  int node = __ldg(&g.base[I[0] + n * (I[1] + n * I[2])]);
+  int lev = 0;
+  while (node < 0) {
+    long long blk = -(long long)node - 1;
+    if (blk >= g.n_blocks || lev >= g.max_level) return -1;
+    ++lev;
+    R sc = (R)(1 << lev);
+    int oct = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int j = cell_index(p[a] * sc, d[a]);
+      int o = j - 2 * I[a];
+      if ((unsigned)o > 1u) return -1;
+      oct |= o << a;
+      I[a] = j;
+    }
+    node = __ldg(&g.child[blk * 8 + oct]);
+  }
+  if ((long long)node >= g.n_leaves) return -1;
+  leaf = node;
+  level = lev;
+  return 0;
+}
+
+// ---------------------------------------------------------------- package
+template <typename R>
+struct Pkg {
+  R p[3], d[3];
+  R tau;
+  int bin;
+  unsigned event;
+  unsigned long long id;
+  bool touched;  // interacted at least once
+};
+
+struct Tally {  // per-thread counters
+  unsigned long long emitted, escaped, capped, absorptions, scatters, crossings, errors,
+      clamped;
+  unsigned long long levels;  // sum of the refinement levels of the cells entered
+};
+
+enum Adv { kCrossed = 0, kInteract = 1, kEscaped = 2, kError = 3 };
+
+template <typename R>
+__device__ __forceinline__ void emit(Pkg<R>& k, unsigned long long id, const DevRun& r,
+                                     const float* star_cdf, int B) {
+  uint4 w = draw(r.seed, id, 0u, 0u);
+  k.id = id;
+  k.event = 0;
+  k.touched = false;
+  k.bin = search_cdf(star_cdf, B, unit<float>(w.x));
+  if (r.source_kind == 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) k.d[a] = sizeof(R) == 8 ? (R)r.beam64[a] : (R)r.beam[a];
+  } else {
+    isotropic<R>(unit<R>(w.y), unit<R>(w.z), k.d);
+  }
+  k.tau = -log_(unit<R>(w.w));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) k.p[a] = sizeof(R) == 8 ? (R)r.src64[a] : (R)r.src[a];
+}
+
+// One cell: cross it, or move to the interaction point inside it.
+template <typename R>
+__device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa* kap,
+                                       int& leaf, int& level) {
+  int I[3];
+  int rc = locate(g, k.p, k.d, leaf, level, I);
+  if (rc == 1) return kEscaped;
+  if (rc < 0) return kError;
+  R sz = (R)1 / (R)(1 << level);
+  R lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = (R)I[a] * sz;
+    hi[a] = lo[a] + sz;
+  }
+  R tex = (R)INFINITY;
+  int ax = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R t;
+    if (k.d[a] > (R)0) t = (hi[a] - k.p[a]) / k.d[a];
+    else if (k.d[a] < (R)0) t = (lo[a] - k.p[a]) / k.d[a];
+    else continue;
+    if (t < tex) { tex = t; ax = a; }
+  }
+  tex = fmax(tex, (R)0);
+  // extinction per base-cube unit of path: sum_s (rho_s d0) kappa_ext,s(bin)
+  const float* rho = g.rho + (size_t)leaf * g.S;
+  const Kappa* kb = kap + k.bin * g.S;
+  R kx = (R)0;
+  for (int s = 0; s < g.S; ++s) kx += (R)__ldg(&rho[s]) * (R)kb[s].kext;
+  R dtau = kx * tex;
+  if (kx > (R)0 && dtau > k.tau) {
+    R sd = k.tau / kx;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) k.p[a] = fmin(hi[a], fmax(lo[a], k.p[a] + sd * k.d[a]));
+    return kInteract;
+  }
+  k.tau -= dtau;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) k.p[a] = fmin(hi[a], fmax(lo[a], k.p[a] + tex * k.d[a]));
+  k.p[ax] = k.d[ax] > (R)0 ? hi[ax] : lo[ax];
+  return kCrossed;
+}
+
+// Interaction part 1: draw the event's numbers; scatter completely, or pick the
+// absorbing species. Returns the species (>= 0) for an absorption, -1 for a scatter.
+template <typename R>
+__device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa* kap,
+                                        int leaf, const DevRun& r, uint4& w1) {
+  uint4 w0 = draw(r.seed, k.id, k.event, 0u);
+  w1 = draw(r.seed, k.id, k.event, 1u);
+  const float* rho = g.rho + (size_t)leaf * g.S;
+  const Kappa* kb = kap + k.bin * g.S;
+  float rs[kMaxSpecies];
+  float ksca = 0.f, kext = 0.f, kabs = 0.f;
+  for (int s = 0; s < g.S; ++s) {
+    rs[s] = __ldg(&rho[s]);
+    ksca += rs[s] * kb[s].ksca;
+    kext += rs[s] * kb[s].kext;
+    kabs += rs[s] * kb[s].kabs;
+  }
+  k.touched = true;
+  float xs = unit<float>(w0.y);
+  int sp = g.S - 1;
+  if (unit<float>(w0.x) * kext < ksca) {
+    float target = xs * ksca, cum = 0.f;
+    for (int s = 0; s < g.S; ++s) {
+      cum += rs[s] * kb[s].ksca;
+      if (cum > target) { sp = s; break; }
+    }
+    R mu = hg_mu<R>((R)kb[sp].g, unit<R>(w0.z));
+    turn<R>(k.d, mu, unit<R>(w0.w));
+    k.tau = -log_(unit<R>(w1.x));
+    return -1;
+  }
+  float target = xs * kabs, cum = 0.f;
+  for (int s = 0; s < g.S; ++s) {
+    cum += rs[s] * kb[s].kabs;
+    if (cum > target) { sp = s; break; }
+  }
+  isotropic<R>(unit<R>(w0.z), unit<R>(w0.w), k.d);
+  k.tau = -log_(unit<R>(w1.x));
+  return sp;
+}
+
+// Interaction part 2 (absorption): n is this package's place in the cell's
+// absorption count (the count before it); draw the new bin.
+template <typename R>
+__device__ __forceinline__ void reemit(Pkg<R>& k, const DevGrid& g, const DevTables& t,
+                                       const DevRun& r, int s, int leaf, int level,
+                                       unsigned long long n, const uint4& w1,
+                                       Tally& tl) {
+  float xu = unit<float>(w1.y), xb = unit<float>(w1.z);
+  float rho = __ldg(&g.rho[(size_t)leaf * g.S + s]);
+  float u;
+  if (r.mode == 0) {
+    float e = t.eps_d0_over_V[level] / rho;
+    u = ((float)n + xu) * e;
+  } else if (r.mode == 1) {
+    float e = t.eps_d0_over_V[level] / rho;
+    u = xu * fmaxf((float)n * e, t.u_tmin[s]);
+  } else {
+    u = xu * __ldg(&t.u_frozen[(size_t)s * g.n_leaves + leaf]);
+  }
+  const float* S = t.S32 + (size_t)s * g.n_T;
+  int nI = g.n_T - 1;
+  int i;
+  if (u >= __ldg(&S[nI])) {
+    i = nI - 1;
+    ++tl.clamped;
+  } else {
+    int lo = 0, hi = nI;  // S[lo] <= u < S[hi]
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (__ldg(&S[mid]) <= u) lo = mid; else hi = mid;
+    }
+    i = lo;
+  }
+  const float* cdf = t.dcdf + ((size_t)s * nI + i) * g.B;
+  int lo = 0, hi = g.B - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(&cdf[mid]) > xb) hi = mid; else lo = mid + 1;
+  }
+  k.bin = lo;
+}
+
+__device__ __forceinline__ int dir_bin(float dz, int n_dir) {
+  int b = (int)floorf(0.5f * (dz + 1.0f) * (float)n_dir);
+  return min(max(b, 0), n_dir - 1);
+}
+
+__device__ __forceinline__ void flush_tally(const Tally& tl, unsigned long long* c) {
+  unsigned long long v[kNumCounters] = {tl.emitted,   tl.escaped, tl.capped,
+                                        tl.absorptions, tl.scatters, tl.crossings,
+                                        tl.errors,    tl.clamped, tl.levels};
+#pragma unroll
+  for (int i = 0; i < kNumCounters; ++i) {
+    unsigned long long x = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&c[i], x);
+  }
+}
+
+// ---------------------------------------------------------------- plain kernel
+// One thread per package, tables read from global memory, one global atomic per
+// absorption and per escape.
+template <typename R>
+__global__ void __launch_bounds__(256) k_transport_plain(DevGrid g, DevTables t, DevRun r) {
+  Tally tl = {};
+  unsigned long long idx = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  const unsigned long long t0 = global_ns();
+  if (idx < r.n_packages) {
+    Pkg<R> k;
+    emit<R>(k, r.first_id + idx, r, t.star_cdf, g.B);
+    ++tl.emitted;
+    unsigned steps = 0;
+    for (;;) {
+      if ((++steps & 1023u) == 0 && global_ns() - t0 > r.budget_ns) {
+        atomicOr(r.status, kStatusTimeout);
+        break;
+      }
+      int leaf, level;
+      int a = advance<R>(k, g, t.kap, leaf, level);
+      if (a <= kInteract) tl.levels += level;
+      if (a == kCrossed) { ++tl.crossings; continue; }
+      if (a == kEscaped) {
+        ++tl.escaped;
+        int db = dir_bin((float)k.d[2], g.n_dir);
+        atomicAdd(&r.sed[(size_t)db * g.B + k.bin], 1ull);
+        if (!k.touched) atomicAdd(&r.sed[(size_t)(g.n_dir + db) * g.B + k.bin], 1ull);
+        break;
+      }
+      if (a == kError) {
+        ++tl.errors;
+        atomicOr(r.status, kStatusTree);
+        break;
+      }
+      if (++k.event > r.max_events) { ++tl.capped; break; }
+      uint4 w1;
+      int s = interact<R>(k, g, t.kap, leaf, r, w1);
+      if (s < 0) { ++tl.scatters; continue; }
+      unsigned long long n = atomicAdd(&r.count[(size_t)s * g.n_leaves + leaf], 1ull);
+      reemit<R>(k, g, t, r, s, leaf, level, n, w1, tl);
+      ++tl.absorptions;
+    }
+  }
+  flush_tally(tl, r.counters);
+}
+
+// ---------------------------------------------------------------- pool kernel
+// Persistent packet pool: each lane owns a package slot; dead lanes are refilled
+// from a global package counter every `refill_period` steps (one atomic per warp);
+// the opacity table, the stellar CDF and the escaped-spectrum histogram live in
+// shared memory; absorptions of lanes hitting the same (species, cell) in the
+// same step are merged into one atomic.
+__global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, DevRun r) {
+  extern __shared__ unsigned long long smem_u64[];
+  const int S = g.S, B = g.B;
+  const int n_sed = 2 * g.n_dir * B;
+  // escaped-spectrum histogram in shared memory when it fits, else in global memory
+  const bool sed_local = r.sed_in_smem != 0;
+  unsigned long long* s_sed = sed_local ? smem_u64 : r.sed;   // [2][n_dir][B]
+  Kappa* s_kap = reinterpret_cast<Kappa*>(smem_u64 + (sed_local ? n_sed : 0));  // [B][S]
+  float* s_cdf = reinterpret_cast<float*>(s_kap + B * S);     // [B]
+  if (sed_local)
+    for (int i = threadIdx.x; i < n_sed; i += blockDim.x) s_sed[i] = 0ull;
+  for (int i = threadIdx.x; i < B * S; i += blockDim.x) s_kap[i] = t.kap[i];
+  for (int i = threadIdx.x; i < B; i += blockDim.x) s_cdf[i] = t.star_cdf[i];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  Tally tl = {};
+  Pkg<float> k;
+  k.id = 0;
+  bool alive = false;
+  bool stop = false;
+  const unsigned long long t0 = global_ns();
+  const int K = r.refill_period > 0 ? r.refill_period : 8;
+
+  while (!stop) {
+    unsigned dead = __ballot_sync(kFull, !alive);
+    if (dead) {
+      int nd = __popc(dead);
+      int leader = __ffs(dead) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(r.next, (unsigned long long)nd);
+      base = __shfl_sync(kFull, base, leader);
+      if (!alive) {
+        unsigned long long j = base + __popc(dead & lt_mask);
+        if (j < r.n_packages) {
+          emit<float>(k, r.first_id + j, r, s_cdf, B);
+          alive = true;
+          ++tl.emitted;
+        }
+      }
+    }
+    if (!__any_sync(kFull, alive)) break;
+    if (lane == 0) stop = global_ns() - t0 > r.budget_ns;
+    stop = __shfl_sync(kFull, stop, 0);
+    if (stop) {
+      if (lane == 0) atomicOr(r.status, kStatusTimeout);
+      break;
+    }
+    for (int step = 0; step < K; ++step) {
+      int leaf = 0, level = 0, sp = -1;
+      uint4 w1 = make_uint4(0, 0, 0, 0);
+      bool absorbing = false;
+      if (alive) {
+        int a = advance<float>(k, g, s_kap, leaf, level);
+        if (a <= kInteract) tl.levels += level;
+        if (a == kCrossed) {
+          ++tl.crossings;
+        } else if (a == kEscaped) {
+          ++tl.escaped;
+          int db = dir_bin(k.d[2], g.n_dir);
+          atomicAdd(&s_sed[db * B + k.bin], 1ull);
+          if (!k.touched) atomicAdd(&s_sed[(g.n_dir + db) * B + k.bin], 1ull);
+          alive = false;
+        } else if (a == kError) {
+          ++tl.errors;
+          atomicOr(r.status, kStatusTree);
+          alive = false;
+        } else if (++k.event > r.max_events) {
+          ++tl.capped;
+          alive = false;
+        } else {
+          sp = interact<float>(k, g, s_kap, leaf, r, w1);
+          if (sp < 0) ++tl.scatters; else absorbing = true;
+        }
+      }
+      unsigned am = __ballot_sync(kFull, absorbing);
+      if (absorbing) {
+        unsigned long long key = ((unsigned long long)sp << 48) | (unsigned long long)leaf;
+        unsigned peers = __match_any_sync(am, key);
+        int leader = __ffs(peers) - 1;
+        unsigned long long old = 0;
+        if (lane == leader)
+          old = atomicAdd(&r.count[(size_t)sp * g.n_leaves + leaf],
+                          (unsigned long long)__popc(peers));
+        old = __shfl_sync(peers, old, leader);
+        reemit<float>(k, g, t, r, sp, leaf, level, old + __popc(peers & lt_mask), w1, tl);
+        ++tl.absorptions;
+      }
+    }
+  }
+  flush_tally(tl, r.counters);
+  if (sed_local) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_sed; i += blockDim.x)
+      if (s_sed[i]) atomicAdd(&r.sed[i], s_sed[i]);
+  }
+}
+
+// ---------------------------------------------------------------- replay
+// Frozen mode only: counts do not steer the path, so each listed package is
+// followed alone and its history recorded.
+__global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long long* ids,
+                        long long n, long long* out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Tally tl = {};
+  Pkg<float> k;
+  emit<float>(k, ids[i], r, t.star_cdf, g.B);
+  long long rec[9] = {0, 0, 0, 0, 0, 0, 0, 0, -1};
+  const unsigned long long t0 = global_ns();
+  unsigned steps = 0;
+  int leaf = -1, level = 0;
+  for (;;) {
+    if ((++steps & 1023u) == 0 && global_ns() - t0 > r.budget_ns) {
+      atomicOr(r.status, kStatusTimeout);
+      break;
+    }
+    int lf, lv;
+    int a = advance<float>(k, g, t.kap, lf, lv);
+    if (a == kCrossed) { ++rec[3]; leaf = lf; continue; }
+    if (a == kEscaped) { rec[4] = 1; break; }
+    if (a == kError) { atomicOr(r.status, kStatusTree); break; }
+    leaf = lf;
+    level = lv;
+    if (++k.event > r.max_events) { rec[5] = 1; break; }
+    uint4 w1;
+    int s = interact<float>(k, g, t.kap, lf, r, w1);
+    if (s < 0) { ++rec[2]; continue; }
+    reemit<float>(k, g, t, r, s, lf, level, 0ull, w1, tl);
+    ++rec[1];
+  }
+  rec[0] = k.event;
+  rec[6] = k.bin;
+  rec[7] = dir_bin(k.d[2], g.n_dir);
+  rec[8] = leaf;
+  for (int j = 0; j < 9; ++j) out[i * 9 + j] = rec[j];
+}
+
+__global__ void k_philox(const unsigned long long* ids, long long n, unsigned event,
+                         unsigned block, unsigned long long seed, unsigned* out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint4 w = draw(seed, ids[i], event, block);
+  out[4 * i] = w.x;
+  out[4 * i + 1] = w.y;
+  out[4 * i + 2] = w.z;
+  out[4 * i + 3] = w.w;
+}
+
+}  // namespace
+
+constexpr size_t kSmemBudget = 200 * 1024;
+
+static size_t table_smem(const DevGrid& g) {
+  return sizeof(Kappa) * g.B * g.S + sizeof(float) * g.B;
+}
+
+static size_t sed_smem(const DevGrid& g) {
+  return sizeof(unsigned long long) * 2 * g.n_dir * g.B;
+}
+
+cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
+                                  int blocks_per_sm, int threads, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  DevRun rr = r;
+  rr.sed_in_smem = table_smem(g) + sed_smem(g) <= kSmemBudget ? 1 : 0;
+  size_t sm = table_smem(g) + (rr.sed_in_smem ? sed_smem(g) : 0);
+  if (sm > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_transport_pool, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  if (blocks_per_sm <= 0) {
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_pool, threads, sm);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = occ > 0 ? occ : 1;
+  }
+  k_transport_pool<<<sms * blocks_per_sm, threads, sm, s>>>(g, t, rr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const DevRun& r,
+                                   bool fp64, int threads, cudaStream_t s) {
+  unsigned long long nb = (r.n_packages + threads - 1) / threads;
+  if (nb == 0) return cudaSuccess;
+  if (nb > 0x7fffffffull) return cudaErrorInvalidValue;
+  if (fp64)
+    k_transport_plain<double><<<(unsigned)nb, threads, 0, s>>>(g, t, r);
+  else
+    k_transport_plain<float><<<(unsigned)nb, threads, 0, s>>>(g, t, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
+                         const unsigned long long* ids, long long n, long long* out,
+                         cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_trace<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, t, r, ids, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const unsigned long long* ids, long long n, unsigned event,
+                          unsigned block, unsigned long long seed, unsigned* out,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_philox<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(ids, n, event, block, seed, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rt

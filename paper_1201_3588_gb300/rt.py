@@ -1,0 +1,252 @@
+"""Python binding of librt_gb300 (include/rt.h) through ctypes.
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels. Importing this module loads the library and raises if it cannot be
+found or built; there is no fallback. PyTorch, when used, only supplies device
+buffers (``tensor.data_ptr()``) and streams (``stream.cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+REEMIT_BW, REEMIT_NOCORR, REEMIT_FROZEN = 0, 1, 2
+KERNEL_POOL, KERNEL_PLAIN_F32, KERNEL_PLAIN_F64 = 0, 1, 2
+MEM_HOST, MEM_DEVICE = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
+          4: "kernel stopped at its time budget", 5: "call out of order",
+          6: "package ids beyond the planned total", 7: "malformed grid met on the device"}
+
+TRACE_FIELDS = ("events", "absorptions", "scatters", "crossings", "escaped", "capped",
+                "final_bin", "dir_bin", "last_leaf")
+
+
+class RTError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class _Desc(C.Structure):
+    _fields_ = [("half_size_cm", C.c_double), ("n_base", C.c_int32), ("max_level", C.c_int32),
+                ("n_blocks", C.c_int64), ("n_leaves", C.c_int64), ("base", C.c_void_p),
+                ("child", C.c_void_p), ("n_species", C.c_int32), ("n_bins", C.c_int32),
+                ("rho", C.c_void_p), ("nu_edges", C.c_void_p), ("n_sed_dirs", C.c_int32),
+                ("n_temp", C.c_int32), ("t_min", C.c_double), ("t_max", C.c_double)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("kernel", C.c_int32), ("max_events", C.c_uint64),
+                ("blocks_per_sm", C.c_int32), ("threads", C.c_int32),
+                ("refill_period", C.c_int32), ("reserved", C.c_int32),
+                ("budget_s", C.c_double)]
+
+
+class _Counters(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("emitted", "escaped", "capped", "absorptions",
+                                          "scatters", "crossings", "errors", "clamped",
+                                          "levels")]
+
+
+_lib = None
+
+# exported symbols with their argument types; every name declared in include/rt.h
+SIGNATURES = {
+    "rt_grid_create": [C.POINTER(_Desc), C.POINTER(C.c_void_p)],
+    "rt_grid_destroy": [C.c_void_p],
+    "rt_set_dust": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                    C.c_int],
+    "rt_emit_star": [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_int, C.c_void_p,
+                     C.c_uint64],
+    "rt_set_frozen_temperatures": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_transport": [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(_Opts),
+                     C.c_void_p],
+    "rt_reset": [C.c_void_p, C.c_void_p],
+    "rt_cell_temperatures": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_sed": [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p],
+    "rt_counts": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_set_counts": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_get_counters": [C.c_void_p, C.POINTER(_Counters)],
+    "rt_trace": [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p],
+    "rt_philox": [C.c_void_p, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p],
+    "rt_status_string": [C.c_int],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librt_gb300.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"librt_gb300.so not found at {path}; run __graft_entry__.build()")
+    L = C.CDLL(path)
+    for name, args in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name == "rt_status_string" else C.c_int
+    _lib = L
+    return L
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise RTError(code, where)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr_mem(x):
+    """(pointer, mem kind) of a numpy array or a torch tensor."""
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr(), (MEM_DEVICE if x.is_cuda else MEM_HOST)
+    return x.ctypes.data, MEM_HOST
+
+
+class Grid:
+    """One model on the device (handle to ``rt_grid``)."""
+
+    def __init__(self, model, n_temp: int = 0, t_min: float = 0.0, t_max: float = 0.0):
+        L = load()
+        t = model.tree
+        self.model = model
+        self.S, self.N, self.B = model.n_species, t.n_leaves, model.n_bins
+        self.n_dir = model.n_sed_dirs
+        base = np.ascontiguousarray(t.base, dtype=np.int32)
+        child = np.ascontiguousarray(t.child, dtype=np.int32)
+        rho = np.ascontiguousarray(model.rho, dtype=np.float64)
+        nu = np.ascontiguousarray(model.nu_edges, dtype=np.float64)
+        d = _Desc(half_size_cm=model.half_size, n_base=t.n_base, max_level=t.max_level,
+                  n_blocks=t.n_blocks, n_leaves=t.n_leaves, base=base.ctypes.data,
+                  child=child.ctypes.data if child.size else None, n_species=self.S,
+                  n_bins=self.B, rho=rho.ctypes.data, nu_edges=nu.ctypes.data,
+                  n_sed_dirs=self.n_dir, n_temp=n_temp, t_min=t_min, t_max=t_max)
+        h = C.c_void_p()
+        _check(L.rt_grid_create(C.byref(d), C.byref(h)), "rt_grid_create")
+        self._h = h
+        kabs, ksca, g = model.opacity_arrays()
+        for s, sp in enumerate(model.species):
+            ka = np.ascontiguousarray(kabs[s])
+            ks = np.ascontiguousarray(ksca[s])
+            gg = np.ascontiguousarray(g[s])
+            _check(L.rt_set_dust(h, s, ka.ctypes.data, ks.ctypes.data, gg.ctypes.data,
+                                 self.B, int(sp.is_pah), int(sp.n_carbon)), "rt_set_dust")
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rt_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- set-up
+    def emit_star(self, n_total: int, star=None):
+        st = star if star is not None else self.model.star
+        pos = (C.c_double * 3)(*st.pos_cm)
+        beam = (C.c_double * 3)(*st.beam_dir)
+        _check(load().rt_emit_star(self._h, st.T, st.L, pos, int(st.kind), beam, int(n_total)),
+               "rt_emit_star")
+
+    def set_frozen_temperatures(self, T, stream=None):
+        if not hasattr(T, "data_ptr"):
+            T = np.ascontiguousarray(T, dtype=np.float32).reshape(self.S, self.N)
+        p, mem = _ptr_mem(T)
+        _check(load().rt_set_frozen_temperatures(self._h, p, mem, _stream(stream)),
+               "rt_set_frozen_temperatures")
+
+    # -- work
+    def transport(self, n_packages: int, seed: int = 0, first_id: int = 0,
+                  mode: int = REEMIT_BW, kernel: int = KERNEL_POOL, max_events: int = 0,
+                  blocks_per_sm: int = 0, threads: int = 0, refill_period: int = 0,
+                  budget_s: float = 0.0, stream=None):
+        o = _Opts(mode=mode, kernel=kernel, max_events=max_events, blocks_per_sm=blocks_per_sm,
+                  threads=threads, refill_period=refill_period, reserved=0, budget_s=budget_s)
+        _check(load().rt_transport(self._h, int(n_packages), int(seed), int(first_id),
+                                   C.byref(o), _stream(stream)), "rt_transport")
+
+    def reset(self, stream=None):
+        _check(load().rt_reset(self._h, _stream(stream)), "rt_reset")
+
+    def temperatures(self, out=None, stream=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros((self.S, self.N), dtype=np.float32)
+        p, mem = _ptr_mem(out)
+        _check(load().rt_cell_temperatures(self._h, p, mem, _stream(stream)),
+               "rt_cell_temperatures")
+        return out
+
+    def sed(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros((2, self.n_dir, self.B), dtype=np.uint64)
+        p, mem = _ptr_mem(out)
+        eps = C.c_double()
+        _check(load().rt_sed(self._h, p, mem, C.byref(eps), _stream(stream)), "rt_sed")
+        return out, eps.value
+
+    def counts(self, out=None, stream=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros((self.S, self.N), dtype=np.uint64)
+        p, mem = _ptr_mem(out)
+        _check(load().rt_counts(self._h, p, mem, _stream(stream)), "rt_counts")
+        return out
+
+    def set_counts(self, counts, stream=None):
+        if not hasattr(counts, "data_ptr"):
+            counts = np.ascontiguousarray(counts, dtype=np.uint64).reshape(self.S, self.N)
+        p, mem = _ptr_mem(counts)
+        _check(load().rt_set_counts(self._h, p, mem, _stream(stream)), "rt_set_counts")
+
+    def counters(self) -> dict:
+        c = _Counters()
+        code = load().rt_get_counters(self._h, C.byref(c))
+        out = {n: int(getattr(c, n)) for n, _ in _Counters._fields_}
+        _check(code, "rt_get_counters")
+        return out
+
+    def trace(self, ids, seed: int = 0, max_events: int = 0) -> np.ndarray:
+        idv = np.ascontiguousarray(ids, dtype=np.uint64)
+        out = np.zeros((idv.shape[0], 9), dtype=np.int64)
+        _check(load().rt_trace(self._h, idv.ctypes.data, idv.shape[0], int(seed),
+                               int(max_events), out.ctypes.data), "rt_trace")
+        return out
+
+
+def philox(ids, event: int, block: int, seed: int) -> np.ndarray:
+    idv = np.ascontiguousarray(ids, dtype=np.uint64)
+    out = np.zeros((idv.shape[0], 4), dtype=np.uint32)
+    _check(load().rt_philox(idv.ctypes.data, idv.shape[0], event, block, int(seed),
+                            out.ctypes.data), "rt_philox")
+    return out
+
+
+def status_string(code: int) -> str:
+    return load().rt_status_string(code).decode()
