@@ -40,7 +40,8 @@ typedef enum {
     RT_ERR_TIMEOUT = 4,  /* a kernel stopped at its time budget; results partial */
     RT_ERR_STATE = 5,    /* call out of order (e.g. transport before rt_emit_star) */
     RT_ERR_RANGE = 6,    /* package ids beyond the planned total */
-    RT_ERR_DEVICE = 7    /* a package met a malformed tree; results invalid */
+    RT_ERR_DEVICE = 7,   /* a package met a malformed tree; results invalid */
+    RT_ERR_TOO_LARGE = 8 /* request exceeds a fixed maximum (see the no-alloc entry) */
 } rt_status;
 
 /* Re-emission rule after an absorption (Sec. 2, the correction of Bjorkman &
@@ -172,6 +173,48 @@ rt_status rt_philox(const uint64_t *ids, int64_t n, uint32_t event, uint32_t blo
                     uint64_t seed, uint32_t *out);
 
 const char *rt_status_string(rt_status s);
+
+/* Cell temperatures for callers that cannot allocate device memory. The paper has
+ * no counterpart; this is a service of the library.
+ *
+ * Who needs it: code that owns all of its device memory and may not call
+ * cudaMalloc at the point where temperatures are wanted -- a framework that hands
+ * out memory only from its own pool (a stray cudaMalloc would synchronise the
+ * device and fragment the pool), or a pipeline being recorded by stream capture,
+ * during which allocation is not allowed. Such a caller passes every input and the
+ * output as its own device buffers; this entry point then allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ * It computes what rt_cell_temperatures computes: T from
+ * n eps = rho V 4 pi sum_b kappa_abs(b) P_b(T), inverted in FP64, 0 where n = 0 or
+ * rho = 0, t_max (counted in *n_clamped) where the energy lies beyond the table.
+ * The FP64 emission table it needs lives in one fixed array in device memory that
+ * the library reserves statically: 147,712 bytes, held on every GPU that loads the
+ * library until the process exits. Hence the limits: n_species <= 8,
+ * n_temp <= 2048 table rows, n_bins <= 1024; larger requests return
+ * RT_ERR_TOO_LARGE.
+ *
+ * count   device, [n_species][n_cells] absorption counts
+ * rho     device, [n_species][n_cells] densities, g cm^-3
+ * volume  device, [n_cells] cell volumes, cm^3
+ * kabs    device, [n_species][n_bins] absorption opacities, cm^2 g^-1
+ * nu_edges device, [n_bins+1] bin edges, Hz, ascending
+ * eps     package energy, erg/s; t_min, t_max, n_temp as in rt_grid_desc (0: defaults)
+ * T_out   device, [n_species][n_cells], K
+ * n_clamped device, one uint64 (may be NULL): cells set to t_max
+ * stream  cudaStream_t; the call is asynchronous on it.
+ *
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current) and may load the library's device code; make that
+ * first call before any stream capture. Every call reuses the same array and finds
+ * there whatever the previous call left, so calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the caller. */
+rt_status rt_cell_temperatures_noalloc(const uint64_t *count, const double *rho,
+                                       const double *volume, const double *kabs,
+                                       const double *nu_edges, int n_species,
+                                       int64_t n_cells, int n_bins, double eps,
+                                       double t_min, double t_max, int n_temp,
+                                       float *T_out, uint64_t *n_clamped, void *stream);
 
 #ifdef __cplusplus
 }

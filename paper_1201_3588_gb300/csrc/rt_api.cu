@@ -266,6 +266,7 @@ const char* rt_status_string(rt_status s) {
     case RT_ERR_STATE: return "call out of order";
     case RT_ERR_RANGE: return "package ids beyond the planned total";
     case RT_ERR_DEVICE: return "malformed grid met on the device";
+    case RT_ERR_TOO_LARGE: return "request exceeds a fixed maximum";
   }
   return "unknown status";
 }

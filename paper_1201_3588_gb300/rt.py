@@ -20,7 +20,8 @@ KERNEL_POOL, KERNEL_PLAIN_F32, KERNEL_PLAIN_F64 = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
           4: "kernel stopped at its time budget", 5: "call out of order",
-          6: "package ids beyond the planned total", 7: "malformed grid met on the device"}
+          6: "package ids beyond the planned total", 7: "malformed grid met on the device",
+          8: "request exceeds a fixed maximum"}
 
 TRACE_FIELDS = ("events", "absorptions", "scatters", "crossings", "escaped", "capped",
                 "final_bin", "dir_bin", "last_leaf")
@@ -75,6 +76,10 @@ SIGNATURES = {
     "rt_trace": [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p],
     "rt_philox": [C.c_void_p, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p],
     "rt_status_string": [C.c_int],
+    "rt_cell_temperatures_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_double,
+                                     C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                     C.c_void_p],
 }
 
 
@@ -246,6 +251,27 @@ def philox(ids, event: int, block: int, seed: int) -> np.ndarray:
     _check(load().rt_philox(idv.ctypes.data, idv.shape[0], event, block, int(seed),
                             out.ctypes.data), "rt_philox")
     return out
+
+
+def cell_temperatures_noalloc(count, rho, volume, kabs, nu_edges, eps: float, T_out,
+                              n_clamped=None, t_min: float = 0.0, t_max: float = 0.0,
+                              n_temp: int = 0, stream=None):
+    """Temperatures from caller-owned device tensors (counts uint64/int64 [S][N], rho
+    float64 [S][N], volume float64 [N], kabs float64 [S][B], nu_edges float64 [B+1],
+    T_out float32 [S][N], n_clamped int64 [1] or None); the library allocates
+    nothing for this call (its table lives in a fixed device array)."""
+    S, N = int(count.shape[0]), int(count.shape[1])
+    B = int(kabs.shape[1])
+    for name, t in (("count", count), ("rho", rho), ("volume", volume), ("kabs", kabs),
+                    ("nu_edges", nu_edges), ("T_out", T_out)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    _check(load().rt_cell_temperatures_noalloc(
+        count.data_ptr(), rho.data_ptr(), volume.data_ptr(), kabs.data_ptr(),
+        nu_edges.data_ptr(), S, N, B, float(eps), float(t_min), float(t_max), int(n_temp),
+        T_out.data_ptr(), n_clamped.data_ptr() if n_clamped is not None else None,
+        _stream(stream)), "rt_cell_temperatures_noalloc")
+    return T_out
 
 
 def status_string(code: int) -> str:
