@@ -25,6 +25,7 @@ struct rt_grid {
   int32_t* d_child = nullptr;
   float* d_rho = nullptr;
   int8_t* d_level = nullptr;
+  int32_t* d_links = nullptr;
   unsigned long long* d_count = nullptr;
   unsigned long long* d_sed = nullptr;
   unsigned long long* d_counters = nullptr;
@@ -40,6 +41,8 @@ struct rt_grid {
   double* d_S64 = nullptr;
   float* d_S32 = nullptr;
   float* d_dcdf = nullptr;
+  unsigned short* d_cdf_guide = nullptr;
+  int* d_u_guide = nullptr;
   Kappa* d_kap = nullptr;
   float* d_star_cdf = nullptr;
   double* d_star_frac = nullptr;
@@ -99,6 +102,8 @@ void free_tables(rt_grid* g) {
   dfree(g->d_S64);
   dfree(g->d_S32);
   dfree(g->d_dcdf);
+  dfree(g->d_cdf_guide);
+  dfree(g->d_u_guide);
   dfree(g->d_kap);
   dfree(g->d_star_cdf);
   dfree(g->d_star_frac);
@@ -111,6 +116,7 @@ void free_all(rt_grid* g) {
   dfree(g->d_child);
   dfree(g->d_rho);
   dfree(g->d_level);
+  dfree(g->d_links);
   dfree(g->d_count);
   dfree(g->d_sed);
   dfree(g->d_counters);
@@ -122,31 +128,40 @@ void free_all(rt_grid* g) {
 }
 
 // Walk the tree from every base cube: every leaf id must appear exactly once,
-// every block be referenced exactly once, and no path exceed max_level.
-rt_status check_tree(const rt_grid_desc* d, std::vector<int8_t>& level, int* max_seen) {
+// every block be referenced exactly once, and no path exceed max_level. Records
+// each leaf's level and integer corner (at its level).
+rt_status check_tree(const rt_grid_desc* d, std::vector<int8_t>& level,
+                     std::vector<int32_t>& ijk, int* max_seen) {
   const long long n = d->n_base;
   const long long nb = n * n * n;
   level.assign((size_t)d->n_leaves, (int8_t)-1);
+  ijk.assign((size_t)d->n_leaves * 3, 0);
   std::vector<char> seen_blk((size_t)d->n_blocks, 0);
-  std::vector<std::pair<int32_t, int>> stk;
+  struct Item { int32_t node; int lev; int32_t i, j, k; };
+  std::vector<Item> stk;
   stk.reserve(64);
   *max_seen = 0;
-  for (long long i = 0; i < nb; ++i) {
+  for (long long b = 0; b < nb; ++b) {
     stk.clear();
-    stk.push_back({d->base[i], 0});
+    stk.push_back({d->base[b], 0, (int32_t)(b % n), (int32_t)((b / n) % n), (int32_t)(b / (n * n))});
     while (!stk.empty()) {
-      auto [node, lev] = stk.back();
+      Item it = stk.back();
       stk.pop_back();
-      if (lev > d->max_level) return RT_ERR_ARG;
-      if (node >= 0) {
-        if ((long long)node >= d->n_leaves || level[(size_t)node] >= 0) return RT_ERR_ARG;
-        level[(size_t)node] = (int8_t)lev;
-        if (lev > *max_seen) *max_seen = lev;
+      if (it.lev > d->max_level) return RT_ERR_ARG;
+      if (it.node >= 0) {
+        if ((long long)it.node >= d->n_leaves || level[(size_t)it.node] >= 0) return RT_ERR_ARG;
+        level[(size_t)it.node] = (int8_t)it.lev;
+        ijk[(size_t)it.node * 3 + 0] = it.i;
+        ijk[(size_t)it.node * 3 + 1] = it.j;
+        ijk[(size_t)it.node * 3 + 2] = it.k;
+        if (it.lev > *max_seen) *max_seen = it.lev;
       } else {
-        long long blk = -(long long)node - 1;
+        long long blk = -(long long)it.node - 1;
         if (blk >= d->n_blocks || seen_blk[(size_t)blk]) return RT_ERR_ARG;
         seen_blk[(size_t)blk] = 1;
-        for (int o = 0; o < 8; ++o) stk.push_back({d->child[blk * 8 + o], lev + 1});
+        for (int o = 0; o < 8; ++o)
+          stk.push_back({d->child[blk * 8 + o], it.lev + 1, 2 * it.i + (o & 1),
+                         2 * it.j + ((o >> 1) & 1), 2 * it.k + ((o >> 2) & 1)});
       }
     }
   }
@@ -184,6 +199,8 @@ rt_status build_tables(rt_grid* g, cudaStream_t s) {
   ALLOC(g->d_S64, (size_t)S * nT);
   ALLOC(g->d_S32, (size_t)S * nT);
   ALLOC(g->d_dcdf, (size_t)S * (nT - 1) * B);
+  ALLOC(g->d_cdf_guide, (size_t)S * (nT - 1) * B);
+  ALLOC(g->d_u_guide, (size_t)S * nT);
   ALLOC(g->d_kap, (size_t)S * B);
   ALLOC(g->d_star_cdf, (size_t)B);
   ALLOC(g->d_star_frac, 1);
@@ -212,6 +229,8 @@ rt_status build_tables(rt_grid* g, cudaStream_t s) {
   tb.S64 = g->d_S64;
   tb.S32 = g->d_S32;
   tb.dcdf = g->d_dcdf;
+  tb.cdf_guide = g->d_cdf_guide;
+  tb.u_guide = g->d_u_guide;
   tb.kap = g->d_kap;
   tb.star_cdf = g->d_star_cdf;
   tb.star_frac = g->d_star_frac;
@@ -233,8 +252,15 @@ rt_status build_tables(rt_grid* g, cudaStream_t s) {
   t.S64 = g->d_S64;
   t.Tgrid = g->d_Tgrid;
   t.dcdf = g->d_dcdf;
+  t.cdf_guide = g->d_cdf_guide;
+  t.u_guide = g->d_u_guide;
   t.u_frozen = nullptr;
-  for (int i = 0; i < S; ++i) t.u_tmin[i] = (float)S64[(size_t)i * nT + 1];
+  for (int i = 0; i < S; ++i) {
+    t.u_tmin[i] = (float)S64[(size_t)i * nT + 1];
+    double l0 = std::log(S64[(size_t)i * nT + 1]), l1 = std::log(S64[(size_t)i * nT + nT - 1]);
+    t.u_ln0[i] = (float)l0;
+    t.u_inv[i] = (float)((nT - 1) / (l1 - l0));
+  }
   for (int l = 0; l < kMaxLevels; ++l) {
     double V = std::pow(g->d0 * std::ldexp(1.0, -l), 3.0);
     t.eps_over_V[l] = g->eps / V;
@@ -310,8 +336,13 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
     return RT_ERR_ARG;
   }
   std::vector<int8_t> level;
+  std::vector<int32_t> ijk;
   int max_seen = 0;
-  rt_status st = check_tree(d, level, &max_seen);
+  if (d->n_leaves >= kMaxLinkedLeaves) {
+    delete g;
+    return RT_ERR_ARG;
+  }
+  rt_status st = check_tree(d, level, ijk, &max_seen);
   if (st != RT_OK) {
     delete g;
     return st;
@@ -341,6 +372,7 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   ALLOC(g->d_child, (size_t)d->n_blocks * 8);
   ALLOC(g->d_rho, (size_t)S * N);
   ALLOC(g->d_level, (size_t)N);
+  ALLOC(g->d_links, (size_t)N * 8);
   ALLOC(g->d_count, (size_t)S * N);
   ALLOC(g->d_sed, (size_t)2 * d->n_sed_dirs * B);
   ALLOC(g->d_counters, (size_t)kNumCounters);
@@ -366,6 +398,7 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   g->g.child = g->d_child;
   g->g.rho = g->d_rho;
   g->g.level = g->d_level;
+  g->g.links = g->d_links;
   g->g.n_leaves = N;
   g->g.n_blocks = d->n_blocks;
   g->g.n_base = d->n_base;
@@ -374,6 +407,24 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   g->g.B = B;
   g->g.n_dir = d->n_sed_dirs;
   g->g.n_T = g->desc.n_temp;
+  // face links of every leaf, built on the device from the leaf corners
+  {
+    int32_t* d_ijk = nullptr;
+    if ((st = dalloc(&d_ijk, (size_t)N * 3)) != RT_OK) {
+      free_all(g);
+      delete g;
+      return st;
+    }
+    e = cudaMemcpy(d_ijk, ijk.data(), sizeof(int32_t) * 3 * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_build_links(g->g, d_ijk, g->d_links, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    dfree(d_ijk);
+    if (e != cudaSuccess) {
+      free_all(g);
+      delete g;
+      return RT_ERR_CUDA;
+    }
+  }
   *out = g;
   return RT_OK;
 }
@@ -501,6 +552,7 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
   r->source_kind = g->source_kind;
   r->mode = mode;
   r->refill_period = (o && o->refill_period > 0) ? o->refill_period : 8;
+  r->interaction_batch = (o && o->interaction_batch > 0) ? o->interaction_batch : 8;
   double budget = (o && o->budget_s > 0) ? o->budget_s : 120.0;
   r->budget_ns = (unsigned long long)(budget * 1e9);
   return RT_OK;
@@ -512,7 +564,8 @@ rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
   int kernel = o ? o->kernel : RT_KERNEL_POOL;
   int threads = (o && o->threads > 0) ? o->threads : 256;
   if (kernel < 0 || kernel > 2 || threads % 32 != 0 || threads > 256) return RT_ERR_ARG;
-  if (o && (o->blocks_per_sm < 0 || o->blocks_per_sm > 32 || o->refill_period < 0))
+  if (o && (o->blocks_per_sm < 0 || o->blocks_per_sm > 32 || o->refill_period < 0 ||
+            o->interaction_batch < 0 || o->interaction_batch > 32))
     return RT_ERR_ARG;
   cudaStream_t s = as_stream(stream);
   RT_CUDA(cudaSetDevice(g->dev));

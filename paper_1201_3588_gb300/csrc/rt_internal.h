@@ -21,12 +21,22 @@ enum Counter {
   kCErrors, kCClamped, kCLevels, kNumCounters
 };
 
+// Face links of a leaf (record of 8 int32 per leaf: faces -x,+x,-y,+y,-z,+z, then
+// the densities of species 0 and 1 as float bits when S <= 2). A link is
+//   kLinkEscape                the face is the domain boundary;
+//   id | (level << 28)         the neighbouring leaf (same size or coarser);
+//   -(block + 1)               the same-size neighbour is split: descend into block.
+constexpr int32_t kLinkEscape = (int32_t)0x80000000;
+constexpr int32_t kLinkLeafMask = 0x0FFFFFFF;
+constexpr long long kMaxLinkedLeaves = 1ll << 28;
+
 // Geometry and densities (device pointers), passed by value.
 struct DevGrid {
   const int32_t* base;     // [n^3]
   const int32_t* child;    // [n_blocks*8]
   const float* rho;        // [n_leaves][S]: density times the base-cube edge, g cm^-2
   const int8_t* level;     // [n_leaves] refinement level of every leaf
+  const int32_t* links;    // [n_leaves][8] face links (+ densities when S <= 2)
   long long n_leaves, n_blocks;
   int n_base, max_level, S, B, n_dir, n_T;
 };
@@ -44,6 +54,10 @@ struct DevTables {
   const double* S64;          // [S][n_T]
   const double* Tgrid;        // [n_T], Tgrid[0] = 0
   const float* dcdf;          // [S][n_T-1][B] normalised cumulative of row differences
+  const unsigned short* cdf_guide;  // [S][n_T-1][B]: first bin whose cdf exceeds k/B
+  const int* u_guide;         // [S][n_T]: interval holding exp(u_ln0 + k / u_inv)
+  float u_ln0[kMaxSpecies];   // ln S_s(T_1)
+  float u_inv[kMaxSpecies];   // (n_T - 1) / (ln S_s(T_last) - ln S_s(T_1))
   const float* u_frozen;      // [S][n_leaves] (frozen mode) or null
   float u_tmin[kMaxSpecies];  // S_s(t_min)
   float eps_d0_over_V[kMaxLevels];   // eps * d0 / V(level), erg s^-1 cm^-2 (FP32)
@@ -64,6 +78,7 @@ struct DevRun {
   double src64[3];
   double beam64[3];
   int source_kind, mode, refill_period;
+  int interaction_batch;          // pool: waiting lanes that trigger an interaction phase
   int sed_in_smem;                // pool: escaped-spectrum histogram in shared memory
   unsigned long long budget_ns;
 };
@@ -76,6 +91,8 @@ cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const D
 cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
                          const unsigned long long* ids, long long n, long long* out,
                          cudaStream_t s);
+cudaError_t launch_build_links(const DevGrid& g, const int32_t* leaf_ijk, int32_t* links,
+                               cudaStream_t s);
 cudaError_t launch_philox(const unsigned long long* ids, long long n, unsigned event,
                           unsigned block, unsigned long long seed, unsigned* out,
                           cudaStream_t s);
@@ -93,6 +110,8 @@ struct TableBuild {
   double* S64;               // [S][n_T]
   float* S32;                // [S][n_T]
   float* dcdf;               // [S][n_T-1][B]
+  unsigned short* cdf_guide; // [S][n_T-1][B]
+  int* u_guide;              // [S][n_T]
   Kappa* kap;                // [B][S]
   float* star_cdf;           // [B]
   double* star_frac;         // [1] in-range fraction of the stellar blackbody

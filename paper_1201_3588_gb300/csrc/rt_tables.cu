@@ -60,6 +60,41 @@ __global__ void k_difference_cdfs(TableBuild tb) {
   out[tb.B - 1] = 1.0f;
 }
 
+// Search accelerators (results identical to a binary search; they only give the
+// search a starting point). Per difference-CDF row: the first bin whose cumulative
+// value exceeds k/B, k = 0..B-1. One thread per row.
+__global__ void k_cdf_guides(TableBuild tb) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int nI = tb.n_T - 1;
+  if (idx >= tb.S * nI) return;
+  const float* cdf = tb.dcdf + (size_t)idx * tb.B;
+  unsigned short* gd = tb.cdf_guide + (size_t)idx * tb.B;
+  int b = 0;
+  for (int k = 0; k < tb.B; ++k) {
+    float thr = (float)k / (float)tb.B;
+    while (b < tb.B - 1 && cdf[b] <= thr) ++b;
+    gd[k] = (unsigned short)b;
+  }
+}
+
+// Per species: for u_k = exp(ln S(T_1) + k (ln S(T_last) - ln S(T_1)) / (n_T - 1)),
+// the largest interval i <= n_T - 2 with S(T_i) <= u_k. One thread per (s, k).
+__global__ void k_u_guides(TableBuild tb) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= tb.S * tb.n_T) return;
+  int s = idx / tb.n_T, k = idx % tb.n_T;
+  const double* S = tb.S64 + (size_t)s * tb.n_T;
+  int nI = tb.n_T - 1;
+  double l0 = log(S[1]), l1 = log(S[nI]);
+  double u = exp(l0 + (l1 - l0) * (double)k / (double)nI);
+  int lo = 0, hi = nI;  // S[lo] <= u < S[hi] (clamped at the last interval)
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (S[mid] <= u) lo = mid; else hi = mid;
+  }
+  tb.u_guide[idx] = lo;
+}
+
 __global__ void k_opacity_and_star(TableBuild tb) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < tb.B) {
@@ -169,6 +204,8 @@ cudaError_t launch_build_tables(const TableBuild& tb, cudaStream_t s) {
   k_planck_rows<<<nblk((long long)tb.n_T * tb.B, 256), 256, 0, s>>>(tb);
   k_emission_rows<<<nblk((long long)tb.S * tb.n_T, 128), 128, 0, s>>>(tb);
   k_difference_cdfs<<<nblk((long long)tb.S * (tb.n_T - 1), 128), 128, 0, s>>>(tb);
+  k_cdf_guides<<<nblk((long long)tb.S * (tb.n_T - 1), 128), 128, 0, s>>>(tb);
+  k_u_guides<<<nblk((long long)tb.S * tb.n_T, 128), 128, 0, s>>>(tb);
   k_opacity_and_star<<<nblk(tb.B, 128), 128, 0, s>>>(tb);
   return cudaGetLastError();
 }

@@ -193,6 +193,7 @@ __device__ __forceinline__ int locate(const DevGrid& g, const R p[3], const R d[
 template <typename R>
 struct Pkg {
   R p[3], d[3];
+  R inv[3];  // 1/d (unused where d == 0)
   R tau;
   int bin;
   unsigned event;
@@ -207,6 +208,12 @@ struct Tally {  // per-thread counters
 };
 
 enum Adv { kCrossed = 0, kInteract = 1, kEscaped = 2, kError = 3 };
+
+template <typename R>
+__device__ __forceinline__ void set_inverse(Pkg<R>& k) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) k.inv[a] = (R)1 / k.d[a];
+}
 
 template <typename R>
 __device__ __forceinline__ void emit(Pkg<R>& k, unsigned long long id, const DevRun& r,
@@ -225,6 +232,7 @@ __device__ __forceinline__ void emit(Pkg<R>& k, unsigned long long id, const Dev
   k.tau = -log_(unit<R>(w.w));
 #pragma unroll
   for (int a = 0; a < 3; ++a) k.p[a] = sizeof(R) == 8 ? (R)r.src64[a] : (R)r.src[a];
+  set_inverse(k);
 }
 
 // One cell: cross it, or move to the interaction point inside it.
@@ -247,8 +255,8 @@ __device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa*
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     R t;
-    if (k.d[a] > (R)0) t = (hi[a] - k.p[a]) / k.d[a];
-    else if (k.d[a] < (R)0) t = (lo[a] - k.p[a]) / k.d[a];
+    if (k.d[a] > (R)0) t = (hi[a] - k.p[a]) * k.inv[a];
+    else if (k.d[a] < (R)0) t = (lo[a] - k.p[a]) * k.inv[a];
     else continue;
     if (t < tex) { tex = t; ax = a; }
   }
@@ -270,6 +278,111 @@ __device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa*
   for (int a = 0; a < 3; ++a) k.p[a] = fmin(hi[a], fmax(lo[a], k.p[a] + tex * k.d[a]));
   k.p[ax] = k.d[ax] > (R)0 ? hi[ax] : lo[ax];
   return kCrossed;
+}
+
+// ---------------------------------------------------------------- linked walk
+// The leaf a package is in, with its level and integer corner (at that level).
+struct Cell {
+  int leaf, level;
+  int I[3];
+};
+
+// Enter the grid at the package's position (full descent from the base cube).
+__device__ __forceinline__ int enter(const Pkg<float>& k, const DevGrid& g, Cell& c,
+                                     unsigned long long& child_reads) {
+  int rc = locate<float>(g, k.p, k.d, c.leaf, c.level, c.I);
+  if (rc == 0) child_reads += c.level;
+  return rc;
+}
+
+// One cell of the walk using the face links: the exit face follows from the
+// geometry alone, so the face link and the densities come from one record read;
+// the next leaf is the linked one (same size or coarser), or is found by a short
+// descent when the neighbouring region is finer.
+__device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevGrid& g,
+                                              const Kappa* kap,
+                                              unsigned long long& child_reads) {
+  const float sz = __int_as_float((127 - c.level) << 23);  // 2^-level
+  float lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = (float)c.I[a] * sz;
+    hi[a] = lo[a] + sz;
+  }
+  float tex = INFINITY;
+  int ax = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float t;
+    if (k.d[a] > 0.f) t = (hi[a] - k.p[a]) * k.inv[a];
+    else if (k.d[a] < 0.f) t = (lo[a] - k.p[a]) * k.inv[a];
+    else continue;
+    if (t < tex) { tex = t; ax = a; }
+  }
+  tex = fmaxf(tex, 0.f);
+  const bool up = k.d[ax] > 0.f;
+  const int* rec = g.links + (size_t)c.leaf * 8;
+  const int link = __ldg(rec + 2 * ax + (up ? 1 : 0));
+  const Kappa* kb = kap + k.bin * g.S;
+  float kx;
+  if (g.S <= 2) {
+    kx = __int_as_float(__ldg(rec + 6)) * kb[0].kext;
+    if (g.S == 2) kx += __int_as_float(__ldg(rec + 7)) * kb[1].kext;
+  } else {
+    const float* rho = g.rho + (size_t)c.leaf * g.S;
+    kx = 0.f;
+    for (int s = 0; s < g.S; ++s) kx += __ldg(&rho[s]) * kb[s].kext;
+  }
+  const float dtau = kx * tex;
+  if (kx > 0.f && dtau > k.tau) {
+    const float sd = k.tau / kx;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) k.p[a] = fminf(hi[a], fmaxf(lo[a], k.p[a] + sd * k.d[a]));
+    return kInteract;
+  }
+  k.tau -= dtau;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) k.p[a] = fminf(hi[a], fmaxf(lo[a], k.p[a] + tex * k.d[a]));
+  k.p[ax] = up ? hi[ax] : lo[ax];
+  if (link == kLinkEscape) return kEscaped;
+  int J[3] = {c.I[0], c.I[1], c.I[2]};
+  J[ax] += up ? 1 : -1;
+  if (link >= 0) {
+    const int nl = link >> 28;
+    const int sh = c.level - nl;
+    c.leaf = link & kLinkLeafMask;
+    c.level = nl;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c.I[a] = J[a] >> sh;
+    return kCrossed;
+  }
+  // the same-size neighbour is split: descend, staying inside that node
+  long long blk = -(long long)link - 1;
+  int lev = c.level;
+  for (;;) {
+    if (blk >= g.n_blocks || lev >= g.max_level) return kError;
+    ++lev;
+    ++child_reads;
+    const float sc = (float)(1 << lev);
+    int oct = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int j = cell_index(k.p[a] * sc, k.d[a]);
+      j = min(max(j, 2 * J[a]), 2 * J[a] + 1);
+      oct |= (j - 2 * J[a]) << a;
+      J[a] = j;
+    }
+    const int node = __ldg(&g.child[blk * 8 + oct]);
+    if (node >= 0) {
+      if ((long long)node >= g.n_leaves) return kError;
+      c.leaf = node;
+      c.level = lev;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) c.I[a] = J[a];
+      return kCrossed;
+    }
+    blk = -(long long)node - 1;
+  }
 }
 
 // Interaction part 1: draw the event's numbers; scatter completely, or pick the
@@ -300,6 +413,7 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
     }
     R mu = hg_mu<R>((R)kb[sp].g, unit<R>(w0.z));
     turn<R>(k.d, mu, unit<R>(w0.w));
+    set_inverse(k);
     k.tau = -log_(unit<R>(w1.x));
     return -1;
   }
@@ -309,6 +423,7 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
     if (cum > target) { sp = s; break; }
   }
   isotropic<R>(unit<R>(w0.z), unit<R>(w0.w), k.d);
+  set_inverse(k);
   k.tau = -log_(unit<R>(w1.x));
   return sp;
 }
@@ -339,20 +454,20 @@ __device__ __forceinline__ void reemit(Pkg<R>& k, const DevGrid& g, const DevTab
     i = nI - 1;
     ++tl.clamped;
   } else {
-    int lo = 0, hi = nI;  // S[lo] <= u < S[hi]
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (__ldg(&S[mid]) <= u) lo = mid; else hi = mid;
-    }
-    i = lo;
+    // interval i with S[i] <= u < S[i+1]: start from the guide, finish by scanning
+    float kf = (__logf(fmaxf(u, 1e-30f)) - t.u_ln0[s]) * t.u_inv[s];
+    int kk = (int)fminf(fmaxf(kf, 0.0f), (float)nI);
+    i = __ldg(&t.u_guide[s * g.n_T + kk]);
+    while (i > 0 && __ldg(&S[i]) > u) --i;
+    while (i + 1 < nI && __ldg(&S[i + 1]) <= u) ++i;
   }
-  const float* cdf = t.dcdf + ((size_t)s * nI + i) * g.B;
-  int lo = 0, hi = g.B - 1;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (__ldg(&cdf[mid]) > xb) hi = mid; else lo = mid + 1;
-  }
-  k.bin = lo;
+  // first bin whose cumulative value exceeds xb: guide start, then scan
+  const size_t row = ((size_t)s * nI + i) * g.B;
+  const float* cdf = t.dcdf + row;
+  int b = __ldg(&t.cdf_guide[row + min((int)(xb * (float)g.B), g.B - 1)]);
+  while (b > 0 && __ldg(&cdf[b - 1]) > xb) --b;
+  while (__ldg(&cdf[b]) <= xb) ++b;
+  k.bin = b;
 }
 
 __device__ __forceinline__ int dir_bin(float dz, int n_dir) {
@@ -423,8 +538,11 @@ __global__ void __launch_bounds__(256) k_transport_plain(DevGrid g, DevTables t,
 // Persistent packet pool: each lane owns a package slot; dead lanes are refilled
 // from a global package counter every `refill_period` steps (one atomic per warp);
 // the opacity table, the stellar CDF and the escaped-spectrum histogram live in
-// shared memory; absorptions of lanes hitting the same (species, cell) in the
-// same step are merged into one atomic.
+// shared memory. A lane that reaches its interaction point waits; the warp runs
+// the (long, divergent) interaction code only once `interaction_batch` lanes wait
+// or no lane is left walking, so both phases run with most lanes active. Each
+// package's history is unchanged by this schedule. Absorptions of lanes hitting
+// the same (species, cell) in one phase are merged into one atomic.
 __global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, DevRun r) {
   extern __shared__ unsigned long long smem_u64[];
   const int S = g.S, B = g.B;
@@ -446,9 +564,12 @@ __global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, 
   Pkg<float> k;
   k.id = 0;
   bool alive = false;
+  bool pending = false;  // reached an interaction point, waiting for the batch
+  Cell cell{0, 0, {0, 0, 0}};
   bool stop = false;
   const unsigned long long t0 = global_ns();
   const int K = r.refill_period > 0 ? r.refill_period : 8;
+  const int batch = r.interaction_batch > 0 ? r.interaction_batch : 8;
 
   while (!stop) {
     unsigned dead = __ballot_sync(kFull, !alive);
@@ -462,8 +583,19 @@ __global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, 
         unsigned long long j = base + __popc(dead & lt_mask);
         if (j < r.n_packages) {
           emit<float>(k, r.first_id + j, r, s_cdf, B);
-          alive = true;
           ++tl.emitted;
+          const int rc = enter(k, g, cell, tl.levels);
+          if (rc == 0) {
+            alive = true;
+          } else if (rc == 1) {  // source outside the grid, moving away
+            ++tl.escaped;
+            const int db = dir_bin(k.d[2], g.n_dir);
+            atomicAdd(&s_sed[db * B + k.bin], 1ull);
+            atomicAdd(&s_sed[(g.n_dir + db) * B + k.bin], 1ull);
+          } else {
+            ++tl.errors;
+            atomicOr(r.status, kStatusTree);
+          }
         }
       }
     }
@@ -475,15 +607,13 @@ __global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, 
       break;
     }
     for (int step = 0; step < K; ++step) {
-      int leaf = 0, level = 0, sp = -1;
-      uint4 w1 = make_uint4(0, 0, 0, 0);
-      bool absorbing = false;
-      if (alive) {
-        int a = advance<float>(k, g, s_kap, leaf, level);
-        if (a <= kInteract) tl.levels += level;
+      // walk phase: lanes not waiting for an interaction cross one cell
+      if (alive && !pending) {
+        const int a = advance_linked(k, cell, g, s_kap, tl.levels);
         if (a == kCrossed) {
           ++tl.crossings;
         } else if (a == kEscaped) {
+          ++tl.crossings;  // the boundary face it left through
           ++tl.escaped;
           int db = dir_bin(k.d[2], g.n_dir);
           atomicAdd(&s_sed[db * B + k.bin], 1ull);
@@ -493,25 +623,40 @@ __global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, 
           ++tl.errors;
           atomicOr(r.status, kStatusTree);
           alive = false;
-        } else if (++k.event > r.max_events) {
+        } else {
+          pending = true;  // at the interaction point inside cell.leaf
+        }
+      }
+      // interaction phase, warp-uniform: once `batch` lanes wait, or nobody walks
+      const unsigned pm = __ballot_sync(kFull, pending);
+      if (pm == 0u) continue;
+      const unsigned walking = __ballot_sync(kFull, alive && !pending);
+      if (__popc(pm) < batch && walking != 0u) continue;
+      int sp = -1;
+      uint4 w1 = make_uint4(0, 0, 0, 0);
+      bool absorbing = false;
+      if (pending) {
+        pending = false;
+        if (++k.event > r.max_events) {
           ++tl.capped;
           alive = false;
         } else {
-          sp = interact<float>(k, g, s_kap, leaf, r, w1);
+          sp = interact<float>(k, g, s_kap, cell.leaf, r, w1);
           if (sp < 0) ++tl.scatters; else absorbing = true;
         }
       }
-      unsigned am = __ballot_sync(kFull, absorbing);
+      const unsigned am = __ballot_sync(kFull, absorbing);
       if (absorbing) {
-        unsigned long long key = ((unsigned long long)sp << 48) | (unsigned long long)leaf;
+        unsigned long long key = ((unsigned long long)sp << 48) | (unsigned long long)cell.leaf;
         unsigned peers = __match_any_sync(am, key);
         int leader = __ffs(peers) - 1;
         unsigned long long old = 0;
         if (lane == leader)
-          old = atomicAdd(&r.count[(size_t)sp * g.n_leaves + leaf],
+          old = atomicAdd(&r.count[(size_t)sp * g.n_leaves + cell.leaf],
                           (unsigned long long)__popc(peers));
         old = __shfl_sync(peers, old, leader);
-        reemit<float>(k, g, t, r, sp, leaf, level, old + __popc(peers & lt_mask), w1, tl);
+        reemit<float>(k, g, t, r, sp, cell.leaf, cell.level, old + __popc(peers & lt_mask), w1,
+                      tl);
         ++tl.absorptions;
       }
     }
@@ -537,31 +682,66 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
   long long rec[9] = {0, 0, 0, 0, 0, 0, 0, 0, -1};
   const unsigned long long t0 = global_ns();
   unsigned steps = 0;
-  int leaf = -1, level = 0;
-  for (;;) {
+  Cell c{0, 0, {0, 0, 0}};
+  int rc = enter(k, g, c, tl.levels);
+  if (rc == 1) rec[4] = 1;
+  if (rc < 0) atomicOr(r.status, kStatusTree);
+  while (rc == 0) {
     if ((++steps & 1023u) == 0 && global_ns() - t0 > r.budget_ns) {
       atomicOr(r.status, kStatusTimeout);
       break;
     }
-    int lf, lv;
-    int a = advance<float>(k, g, t.kap, lf, lv);
-    if (a == kCrossed) { ++rec[3]; leaf = lf; continue; }
-    if (a == kEscaped) { rec[4] = 1; break; }
+    const int lf = c.leaf;
+    const int a = advance_linked(k, c, g, t.kap, tl.levels);
+    rec[8] = lf;
+    if (a == kCrossed) { ++rec[3]; continue; }
+    if (a == kEscaped) { ++rec[3]; rec[4] = 1; break; }
     if (a == kError) { atomicOr(r.status, kStatusTree); break; }
-    leaf = lf;
-    level = lv;
     if (++k.event > r.max_events) { rec[5] = 1; break; }
     uint4 w1;
-    int s = interact<float>(k, g, t.kap, lf, r, w1);
+    int s = interact<float>(k, g, t.kap, c.leaf, r, w1);
     if (s < 0) { ++rec[2]; continue; }
-    reemit<float>(k, g, t, r, s, lf, level, 0ull, w1, tl);
+    reemit<float>(k, g, t, r, s, c.leaf, c.level, 0ull, w1, tl);
     ++rec[1];
   }
   rec[0] = k.event;
   rec[6] = k.bin;
   rec[7] = dir_bin(k.d[2], g.n_dir);
-  rec[8] = leaf;
   for (int j = 0; j < 9; ++j) out[i * 9 + j] = rec[j];
+}
+
+// Face links: for each leaf and face, the neighbour across it at the leaf's level
+// (descending from the base cube with integer coordinates).
+__global__ void k_build_links(DevGrid g, const int32_t* ijk, int32_t* links) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= g.n_leaves * 6) return;
+  const long long leaf = idx / 6;
+  const int f = (int)(idx % 6), a = f >> 1;
+  const int lev = g.level[leaf];
+  int J[3] = {ijk[leaf * 3], ijk[leaf * 3 + 1], ijk[leaf * 3 + 2]};
+  J[a] += (f & 1) ? 1 : -1;
+  const long long nl = (long long)g.n_base << lev;
+  int32_t link;
+  if (J[a] < 0 || J[a] >= nl) {
+    link = kLinkEscape;
+  } else {
+    const int n = g.n_base;
+    int node = g.base[(J[0] >> lev) + n * ((J[1] >> lev) + n * (J[2] >> lev))];
+    int l = 0;
+    while (node < 0 && l < lev) {
+      const long long blk = -(long long)node - 1;
+      ++l;
+      const int sh = lev - l;
+      const int oct = ((J[0] >> sh) & 1) | (((J[1] >> sh) & 1) << 1) | (((J[2] >> sh) & 1) << 2);
+      node = g.child[blk * 8 + oct];
+    }
+    link = node >= 0 ? (node | (l << 28)) : node;
+  }
+  links[leaf * 8 + f] = link;
+  if (f == 0) {
+    links[leaf * 8 + 6] = g.S >= 1 ? __float_as_int(g.rho[leaf * g.S]) : 0;
+    links[leaf * 8 + 7] = g.S >= 2 ? __float_as_int(g.rho[leaf * g.S + 1]) : 0;
+  }
 }
 
 __global__ void k_philox(const unsigned long long* ids, long long n, unsigned event,
@@ -629,6 +809,13 @@ cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
                          cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_trace<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, t, r, ids, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_links(const DevGrid& g, const int32_t* leaf_ijk, int32_t* links,
+                               cudaStream_t s) {
+  long long n = g.n_leaves * 6;
+  k_build_links<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, leaf_ijk, links);
   return cudaGetLastError();
 }
 

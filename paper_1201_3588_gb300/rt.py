@@ -44,7 +44,7 @@ class _Desc(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("kernel", C.c_int32), ("max_events", C.c_uint64),
                 ("blocks_per_sm", C.c_int32), ("threads", C.c_int32),
-                ("refill_period", C.c_int32), ("reserved", C.c_int32),
+                ("refill_period", C.c_int32), ("interaction_batch", C.c_int32),
                 ("budget_s", C.c_double)]
 
 
@@ -192,9 +192,10 @@ class Grid:
     def transport(self, n_packages: int, seed: int = 0, first_id: int = 0,
                   mode: int = REEMIT_BW, kernel: int = KERNEL_POOL, max_events: int = 0,
                   blocks_per_sm: int = 0, threads: int = 0, refill_period: int = 0,
-                  budget_s: float = 0.0, stream=None):
+                  interaction_batch: int = 0, budget_s: float = 0.0, stream=None):
         o = _Opts(mode=mode, kernel=kernel, max_events=max_events, blocks_per_sm=blocks_per_sm,
-                  threads=threads, refill_period=refill_period, reserved=0, budget_s=budget_s)
+                  threads=threads, refill_period=refill_period,
+                  interaction_batch=interaction_batch, budget_s=budget_s)
         _check(load().rt_transport(self._h, int(n_packages), int(seed), int(first_id),
                                    C.byref(o), _stream(stream)), "rt_transport")
 
