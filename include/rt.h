@@ -60,6 +60,9 @@ enum { RT_KERNEL_POOL = 0, RT_KERNEL_PLAIN_F32 = 1, RT_KERNEL_PLAIN_F64 = 2 };
 
 enum { RT_MEM_HOST = 0, RT_MEM_DEVICE = 1 };
 
+/* How rt_pah_emission computes the emission of transiently heated PAHs. */
+enum { RT_PAH_EXACT = 0, RT_PAH_SURROGATE = 1, RT_PAH_AUTO = 2 };
+
 /* Grid of cubes and subcubes (Sec. 2: space is cut into cubes, and cubes that
  * need finer resolution are split again into subcubes, the cells).
  * base[ix + n*(iy + n*iz)] and child[8*block + (ox | oy<<1 | oz<<2)] hold a leaf id
@@ -172,6 +175,38 @@ rt_status rt_trace(rt_grid *g, const uint64_t *ids, int64_t n, uint64_t seed,
  * block) under key = seed, written to out[4*i..4*i+3] (host). Diagnostic. */
 rt_status rt_philox(const uint64_t *ids, int64_t n, uint32_t event, uint32_t block,
                     uint64_t seed, uint32_t *out);
+
+/* Molecular data of a PAH species (Sec. 1: PAHs of 30 and 200 C atoms; Sec. 3, Fig. 3:
+ * their temperature distribution after single-photon heating). `species` must have
+ * been declared with is_pah = 1 in rt_set_dust, whose kabs is then the PAH's
+ * absorption cross section per gram. modes = {count_0, theta_0, count_1, theta_1, ...}
+ * lists n_groups (1..4) groups of vibrational modes with their characteristic
+ * temperatures (K): the heat content is sum n k theta / (exp(theta/T) - 1).
+ * n_levels internal-energy levels (16..2048; 0: 400) span 0 .. E(t_top) plus the
+ * largest photon energy of the grid (t_top 0: 2500 K).
+ *
+ * In transport, a package absorbed by a PAH is counted in its cell's absorbed
+ * spectrum of 64 coarse bins (coarse bin of fine bin b: floor(64 b / n_bins); all
+ * bins when n_bins < 64) and leaves at a frequency drawn from the PAH's template
+ * spectrum: the exact steady-state emission in a bath of the source's blackbody at
+ * a bolometric flux of 1e4 erg s^-1 cm^-2. */
+rt_status rt_set_pah(rt_grid *g, int species, int n_carbon, int n_hydrogen, double mol_mass_g,
+                     const double *modes, int n_groups, int n_levels, double t_top);
+
+/* PAH absorbed spectra [n_pah][n_leaves][n_coarse] (uint32 counts; PAHs numbered in
+ * species order). */
+rt_status rt_pah_absorbed(rt_grid *g, uint32_t *out, int mem, void *stream);
+
+/* Emission of the transiently heated PAHs of cells first_cell .. first_cell+n_cells-1
+ * into j_out [n_cells][n_bins] (erg/s per bin, summed over PAH species): for each
+ * cell the thermal-discrete steady state of each PAH under the photon absorption
+ * rates its absorbed spectrum implies (count * eps / (h nu_k N_molecules)), then
+ * N_molecules sum_f P_f 4 pi sigma_b P_b(T_f). Emitted power equals absorbed power.
+ * mode RT_PAH_EXACT solves every cell (one warp per cell, FP64 populations);
+ * `surrogate`, `tol` and n_fallback_out serve the learned mode. */
+rt_status rt_pah_emission(rt_grid *g, int64_t first_cell, int64_t n_cells, int mode,
+                          const void *surrogate, float tol, float *j_out, int mem,
+                          uint64_t *n_fallback_out, void *stream);
 
 const char *rt_status_string(rt_status s);
 

@@ -50,7 +50,8 @@ class _Model(C.Structure):
                 ("g", C.c_void_p), ("nu_edges", C.c_void_p), ("star_T", C.c_double),
                 ("star_L", C.c_double), ("star_pos", C.c_double * 3),
                 ("source_kind", C.c_int32), ("n_sed_dirs", C.c_int32),
-                ("beam_dir", C.c_double * 3)]
+                ("beam_dir", C.c_double * 3), ("pah_index", C.c_void_p),
+                ("pah_template", C.c_void_p), ("n_coarse", C.c_int32), ("n_pah", C.c_int32)]
 
 
 class _Run(C.Structure):
@@ -61,7 +62,8 @@ class _Run(C.Structure):
 
 
 class _Tally(C.Structure):
-    _fields_ = [("count", C.c_void_p), ("sed", C.c_void_p), ("emitted", C.c_uint64),
+    _fields_ = [("count", C.c_void_p), ("sed", C.c_void_p), ("pahabs", C.c_void_p),
+                ("emitted", C.c_uint64),
                 ("escaped", C.c_uint64), ("capped", C.c_uint64),
                 ("absorptions", C.c_uint64), ("scatters", C.c_uint64),
                 ("crossings", C.c_uint64), ("errors", C.c_uint64)]
@@ -163,10 +165,14 @@ def rotate(d, mu, phi):
 
 # ------------------------------------------------------------------ models
 
-class OracleModel:
-    """ctypes view of a ``workloads.Model`` (arrays kept alive here)."""
+N_COARSE = 64
 
-    def __init__(self, model):
+
+class OracleModel:
+    """ctypes view of a ``workloads.Model`` (arrays kept alive here). For PAH species
+    the template re-emission spectra come from ``oracle.pah`` unless given."""
+
+    def __init__(self, model, pah_template=None):
         t = model.tree
         self.model = model
         self.base = np.ascontiguousarray(t.base, dtype=np.int32)
@@ -179,6 +185,18 @@ class OracleModel:
         self.g = np.ascontiguousarray(g)
         self.nu = np.ascontiguousarray(model.nu_edges, dtype=np.float64)
         st = model.star
+        self.pah_species = [i for i, sp in enumerate(model.species) if sp.is_pah]
+        self.n_pah = len(self.pah_species)
+        self.n_coarse = min(N_COARSE, model.n_bins)
+        self.pah_index = np.full(model.n_species, -1, dtype=np.int32)
+        for p, i in enumerate(self.pah_species):
+            self.pah_index[i] = p
+        if self.n_pah and pah_template is None:
+            from . import pah as _pah
+            pah_template = np.stack([_pah.template_spectrum(model.species[i], model.nu_edges,
+                                                            st.T) for i in self.pah_species])
+        self.pah_template = (np.ascontiguousarray(pah_template, dtype=np.float64)
+                             if self.n_pah else np.zeros(1))
         self.s = _Model(half_size=model.half_size, n_base=t.n_base, max_level=t.max_level,
                         base=_ptr(self.base), child=_ptr(self.child), n_blocks=t.n_blocks,
                         n_leaves=t.n_leaves, n_species=model.n_species,
@@ -186,7 +204,10 @@ class OracleModel:
                         ksca=_ptr(self.ksca), g=_ptr(self.g), nu_edges=_ptr(self.nu),
                         star_T=st.T, star_L=st.L, star_pos=(C.c_double * 3)(*st.pos_cm),
                         source_kind=st.kind, n_sed_dirs=model.n_sed_dirs,
-                        beam_dir=(C.c_double * 3)(*st.beam_dir))
+                        beam_dir=(C.c_double * 3)(*st.beam_dir),
+                        pah_index=_ptr(self.pah_index) if self.n_pah else None,
+                        pah_template=_ptr(self.pah_template), n_coarse=self.n_coarse,
+                        n_pah=self.n_pah)
 
     @property
     def S(self):
@@ -236,6 +257,7 @@ def package_energy(model, n_total: int) -> float:
 class Tally:
     count: np.ndarray     # uint64 [S][N]
     sed: np.ndarray       # uint64 [2][n_dir][B]
+    pahabs: np.ndarray    # uint64 [n_pah][N][n_coarse]
     emitted: int = 0
     escaped: int = 0
     capped: int = 0
@@ -248,7 +270,8 @@ class Tally:
 def new_tally(model) -> Tally:
     om = as_oracle(model)
     return Tally(np.zeros((om.S, om.N), dtype=np.uint64),
-                 np.zeros((2, om.model.n_sed_dirs, om.B), dtype=np.uint64))
+                 np.zeros((2, om.model.n_sed_dirs, om.B), dtype=np.uint64),
+                 np.zeros((max(om.n_pah, 1), om.N, om.n_coarse), dtype=np.uint64))
 
 
 def _run(n_packages, seed, first_id, n_total, mode, max_events, t_min, T_frozen):
@@ -271,7 +294,8 @@ def transport(model, n_packages: int, seed: int = 0, first_id: int = 0,
     tl = tally if tally is not None else new_tally(om)
     r, keep = _run(n_packages, seed, first_id, n_total or n_packages, mode, max_events,
                    t_min, T_frozen)
-    ct = _Tally(count=_ptr(tl.count), sed=_ptr(tl.sed), emitted=tl.emitted,
+    ct = _Tally(count=_ptr(tl.count), sed=_ptr(tl.sed), pahabs=_ptr(tl.pahabs),
+                emitted=tl.emitted,
                 escaped=tl.escaped, capped=tl.capped, absorptions=tl.absorptions,
                 scatters=tl.scatters, crossings=tl.crossings, errors=tl.errors)
     rc = lib().orc_transport(C.byref(om.s), C.byref(r), C.byref(ct))

@@ -561,6 +561,21 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
                 size_t ci = (size_t)s * N + leaf;
                 uint64_t n = 0;
                 if (count) n = count[ci]++;
+                int p = m->pah_index ? m->pah_index[s] : -1;
+                if (p >= 0) {
+                    /* PAH: the absorbed photon goes to the cell's coarse absorbed
+                     * spectrum; the package leaves at a frequency from the PAH's
+                     * template emission spectrum */
+                    if (t && t->pahabs) {
+                        int kc = (int)(((int64_t)bin * m->n_coarse) / B);
+                        t->pahabs[((size_t)p * N + leaf) * m->n_coarse + kc] += 1;
+                    }
+                    bin = sample_discrete(m->pah_template + (size_t)p * B, B, v[2]);
+                    isotropic(u[2], u[3], d);
+                    ++n_abs;
+                    tau = -log(v[0]);
+                    continue;
+                }
                 double mass = m->rho[ci] * pow(c->d0 * ldexp(1.0, -(int)cell[1]), 3);
                 double e = c->eps / mass;
                 double uf = 0.0;

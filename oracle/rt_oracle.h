@@ -39,6 +39,12 @@ typedef struct {
     double star_pos[3];        /* cm */
     int32_t source_kind, n_sed_dirs;
     double beam_dir[3];
+    /* PAH species (may be absent): pah_index[s] = PAH number of species s or -1;
+     * an absorption by a PAH is tallied in its cell's coarse absorbed spectrum and
+     * re-emitted from that PAH's template spectrum (weights per bin) */
+    const int32_t *pah_index;  /* [S] or NULL */
+    const double *pah_template;/* [n_pah][B] */
+    int32_t n_coarse, n_pah;
 } orc_model;
 
 typedef struct {
@@ -54,6 +60,7 @@ typedef struct {
 typedef struct {
     uint64_t *count;           /* [S][N] absorption counts, accumulated */
     uint64_t *sed;             /* [2][n_dir][B]: all escaped / escaped uncollided */
+    uint64_t *pahabs;          /* [n_pah][N][n_coarse] PAH absorptions, or NULL */
     uint64_t emitted, escaped, capped, absorptions, scatters, crossings, errors;
 } orc_tally;
 

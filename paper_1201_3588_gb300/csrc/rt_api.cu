@@ -49,10 +49,28 @@ struct rt_grid {
   float* d_Tfrozen = nullptr;
   float* d_ufrozen = nullptr;
   float* d_Tscratch = nullptr;
+  // PAH tables and tallies
+  double* d_pah_sigma = nullptr;
+  float* d_pah_s = nullptr;
+  double* d_pah_L = nullptr;
+  double* d_pah_ek = nullptr;
+  int* d_pah_qk = nullptr;
+  double* d_pah_wk = nullptr;
+  float* d_pah_cdf = nullptr;
+  unsigned* d_pahabs = nullptr;
+  float* d_jscratch = nullptr;
+  size_t jscratch_n = 0;
   // host state
   std::vector<double> nu, kabs, ksca, ghg;   // [S][B]
   std::vector<char> dust_set;
   std::vector<int> is_pah, n_carbon;
+  std::vector<char> pah_set;
+  std::vector<PahSpec> pah_spec;
+  std::vector<double> pah_mass;
+  int pah_levels = 400;
+  double pah_t_top = 2500.0;
+  int n_pah = 0;
+  PahTables ptab{};
   bool star_set = false;
   double T_star = 0, L_star = 0, pos[3] = {0, 0, 0}, beam[3] = {0, 0, 1};
   int source_kind = 0;
@@ -107,6 +125,13 @@ void free_tables(rt_grid* g) {
   dfree(g->d_kap);
   dfree(g->d_star_cdf);
   dfree(g->d_star_frac);
+  dfree(g->d_pah_sigma);
+  dfree(g->d_pah_s);
+  dfree(g->d_pah_L);
+  dfree(g->d_pah_ek);
+  dfree(g->d_pah_qk);
+  dfree(g->d_pah_wk);
+  dfree(g->d_pah_cdf);
   g->tables_ready = false;
 }
 
@@ -125,6 +150,8 @@ void free_all(rt_grid* g) {
   dfree(g->d_Tfrozen);
   dfree(g->d_ufrozen);
   dfree(g->d_Tscratch);
+  dfree(g->d_pahabs);
+  dfree(g->d_jscratch);
 }
 
 // Walk the tree from every base cube: every leaf id must appear exactly once,
@@ -178,6 +205,85 @@ rt_status sync_status(rt_grid* g, cudaStream_t s) {
   RT_CUDA(cudaMemcpy(&st, g->d_status, sizeof(st), cudaMemcpyDeviceToHost));
   if (st & kStatusTree) return RT_ERR_DEVICE;
   if (st & kStatusTimeout) return RT_ERR_TIMEOUT;
+  return RT_OK;
+}
+
+double heat_content_host(double T, const PahSpec& sp) {
+  const double kB = 1.380649e-16;
+  double e = 0.0;
+  for (int i = 0; i < sp.n_groups; ++i) {
+    double x = sp.theta[i] / T;
+    if (x < 700.0) e += sp.n_modes[i] * kB * sp.theta[i] / std::expm1(x);
+  }
+  return e;
+}
+
+// Level tables, coarse photon energies and template spectra of the PAH species.
+rt_status build_pah_tables(rt_grid* g, cudaStream_t s) {
+  const int S = g->desc.n_species, B = g->desc.n_bins, N = (int)0;
+  (void)N;
+  std::vector<int> pahs;
+  for (int i = 0; i < S; ++i)
+    if (g->is_pah[(size_t)i]) {
+      if (!g->pah_set[(size_t)i]) return RT_ERR_STATE;
+      pahs.push_back(i);
+    }
+  g->n_pah = (int)pahs.size();
+  if (g->n_pah == 0) return RT_OK;
+  if (g->n_pah > kMaxPah) return RT_ERR_ARG;
+  const int P = g->n_pah, M = g->pah_levels, K = g->tab.n_coarse;
+  rt_status st;
+  if ((st = dalloc(&g->d_pah_sigma, (size_t)P * B)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_pah_s, (size_t)P * M * B)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_pah_L, (size_t)P * M)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_pah_ek, (size_t)K)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_pah_qk, (size_t)P * K)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_pah_wk, (size_t)P * K)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_pah_cdf, (size_t)P * B)) != RT_OK) return st;
+  if (!g->d_pahabs) {
+    if ((st = dalloc(&g->d_pahabs, (size_t)P * g->desc.n_leaves * K)) != RT_OK) return st;
+    RT_CUDA(cudaMemsetAsync(g->d_pahabs, 0, sizeof(unsigned) * P * g->desc.n_leaves * K, s));
+  }
+  std::vector<double> sigma((size_t)P * B);
+  PahBuild pb{};
+  PahTables& pt = g->ptab;
+  pt = PahTables{};
+  pb.n_pah = pt.n_pah = P;
+  pb.M = pt.M = M;
+  pb.K = pt.K = K;
+  pb.B = B;
+  const double h = 6.62607015e-27;
+  for (int p = 0; p < P; ++p) {
+    int sp = pahs[(size_t)p];
+    for (int b = 0; b < B; ++b)
+      sigma[(size_t)p * B + b] = g->kabs[(size_t)sp * B + b] * g->pah_mass[(size_t)sp];
+    pb.spec[p] = g->pah_spec[(size_t)sp];
+    double e_max = heat_content_host(g->pah_t_top, pb.spec[p]) + h * g->nu[(size_t)B];
+    pb.dE[p] = pt.dE[p] = e_max / (M - 1);
+    pt.mol_mass[p] = g->pah_mass[(size_t)sp];
+    pt.species[p] = sp;
+    g->tab.pah_of[sp] = p;
+  }
+  RT_CUDA(cudaMemcpyAsync(g->d_pah_sigma, sigma.data(), sizeof(double) * P * B,
+                          cudaMemcpyHostToDevice, s));
+  pb.nu = g->d_nu;
+  pb.sigma = g->d_pah_sigma;
+  pb.T_star = g->T_star;
+  pb.f_ref = 1.0e4;  // erg s^-1 cm^-2, the heating bath of the paper's Fig. 3
+  pb.s = g->d_pah_s;
+  pb.L = g->d_pah_L;
+  pb.e_k = g->d_pah_ek;
+  pb.q_k = g->d_pah_qk;
+  pb.w_k = g->d_pah_wk;
+  pb.template_cdf = g->d_pah_cdf;
+  pt.s = g->d_pah_s;
+  pt.L = g->d_pah_L;
+  pt.e_k = g->d_pah_ek;
+  pt.q_k = g->d_pah_qk;
+  pt.w_k = g->d_pah_wk;
+  RT_CUDA(launch_pah_tables(pb, pt, s));
+  RT_CUDA(cudaStreamSynchronize(s));
+  g->tab.pah_cdf = g->d_pah_cdf;
   return RT_OK;
 }
 
@@ -267,6 +373,13 @@ rt_status build_tables(rt_grid* g, cudaStream_t s) {
     t.eps_d0_over_V[l] = (float)(g->eps * g->d0 / V);
   }
   t.d0 = g->d0;
+  for (int i = 0; i < kMaxSpecies; ++i) t.pah_of[i] = -1;
+  t.pah_cdf = nullptr;
+  t.n_coarse = B < 64 ? B : 64;
+  if ((st = build_pah_tables(g, s)) != RT_OK) {
+    free_tables(g);
+    return st;
+  }
   g->tables_ready = true;
   g->frozen_ready = false;
   return RT_OK;
@@ -356,6 +469,9 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   g->dust_set.assign((size_t)S, 0);
   g->is_pah.assign((size_t)S, 0);
   g->n_carbon.assign((size_t)S, 0);
+  g->pah_set.assign((size_t)S, 0);
+  g->pah_spec.assign((size_t)S, PahSpec{});
+  g->pah_mass.assign((size_t)S, 0.0);
   if (cudaGetDevice(&g->dev) != cudaSuccess) {
     delete g;
     return RT_ERR_CUDA;
@@ -523,6 +639,9 @@ rt_status rt_reset(rt_grid* g, void* stream) {
                           s));
   RT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s));
   RT_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), s));
+  if (g->d_pahabs)
+    RT_CUDA(cudaMemsetAsync(g->d_pahabs, 0,
+                            sizeof(unsigned) * g->n_pah * N * g->tab.n_coarse, s));
   return RT_OK;
 }
 
@@ -542,6 +661,7 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
   r->sed = g->d_sed;
   r->counters = g->d_counters;
   r->status = g->d_status;
+  r->pahabs = g->d_pahabs;
   for (int a = 0; a < 3; ++a) {
     double p = (g->pos[a] + g->desc.half_size_cm) / g->d0;
     r->src64[a] = p;
@@ -696,6 +816,88 @@ rt_status rt_trace(rt_grid* g, const uint64_t* ids, int64_t n, uint64_t seed,
   dfree(d_out);
   if (e != cudaSuccess) return RT_ERR_CUDA;
   return sync_status(g, nullptr);
+}
+
+rt_status rt_set_pah(rt_grid* g, int species, int n_carbon, int n_hydrogen, double mol_mass_g,
+                     const double* modes, int n_groups, int n_levels, double t_top) {
+  if (!g || !modes) return RT_ERR_ARG;
+  if (species < 0 || species >= g->desc.n_species || !g->is_pah[(size_t)species])
+    return RT_ERR_ARG;
+  if (n_carbon < 1 || n_hydrogen < 0 || !(mol_mass_g > 0) || n_groups < 1 ||
+      n_groups > kMaxModeGroups)
+    return RT_ERR_ARG;
+  if (n_levels == 0) n_levels = 400;
+  if (t_top == 0) t_top = 2500.0;
+  if (n_levels < 16 || n_levels > 2048 || !(t_top > 0) || !std::isfinite(t_top))
+    return RT_ERR_ARG;
+  PahSpec sp{};
+  sp.n_groups = n_groups;
+  for (int i = 0; i < n_groups; ++i) {
+    if (!(modes[2 * i] > 0) || !(modes[2 * i + 1] > 0)) return RT_ERR_ARG;
+    sp.n_modes[i] = modes[2 * i];
+    sp.theta[i] = modes[2 * i + 1];
+  }
+  g->pah_spec[(size_t)species] = sp;
+  g->pah_mass[(size_t)species] = mol_mass_g;
+  g->n_carbon[(size_t)species] = n_carbon;
+  g->pah_set[(size_t)species] = 1;
+  g->pah_levels = n_levels;
+  g->pah_t_top = t_top;
+  g->tables_ready = false;
+  (void)n_hydrogen;
+  return RT_OK;
+}
+
+rt_status rt_pah_absorbed(rt_grid* g, uint32_t* out, int mem, void* stream) {
+  if (!g || !out) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  if (g->n_pah == 0) return RT_ERR_STATE;
+  const size_t n = (size_t)g->n_pah * g->desc.n_leaves * g->tab.n_coarse;
+  RT_CUDA(cudaMemcpyAsync(out, g->d_pahabs, sizeof(unsigned) * n,
+                          mem == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                               : cudaMemcpyDeviceToHost,
+                          s));
+  if (mem != RT_MEM_DEVICE) return sync_status(g, s);
+  return RT_OK;
+}
+
+rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int mode,
+                          const void* surrogate, float tol, float* j_out, int mem,
+                          uint64_t* n_fallback_out, void* stream) {
+  if (!g || !j_out || first_cell < 0 || n_cells < 0) return RT_ERR_ARG;
+  if (first_cell > g->desc.n_leaves || n_cells > g->desc.n_leaves - first_cell)
+    return RT_ERR_ARG;
+  if (mode != RT_PAH_EXACT) return RT_ERR_ARG;
+  (void)surrogate;
+  (void)tol;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  if (g->n_pah == 0) return RT_ERR_STATE;
+  if (n_fallback_out) *n_fallback_out = 0;
+  if (n_cells == 0) return RT_OK;
+  const size_t n = (size_t)n_cells * g->desc.n_bins;
+  float* dst = j_out;
+  if (mem != RT_MEM_DEVICE) {
+    if (g->jscratch_n < n) {
+      dfree(g->d_jscratch);
+      g->jscratch_n = 0;
+      if ((st = dalloc(&g->d_jscratch, n)) != RT_OK) return st;
+      g->jscratch_n = n;
+    }
+    dst = g->d_jscratch;
+  }
+  RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, n_cells,
+                           dst, nullptr, s));
+  if (mem != RT_MEM_DEVICE) {
+    RT_CUDA(cudaMemcpyAsync(j_out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    return sync_status(g, s);
+  }
+  return RT_OK;
 }
 
 rt_status rt_philox(const uint64_t* ids, int64_t n, uint32_t event, uint32_t block,

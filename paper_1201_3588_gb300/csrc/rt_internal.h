@@ -10,6 +10,8 @@ namespace rt {
 constexpr int kMaxSpecies = 8;
 constexpr int kMaxLevels = 8;     // levels 0 .. 7
 constexpr int kMaxBins = 1024;
+constexpr int kMaxPah = 4;        // PAH species per grid
+constexpr int kMaxModeGroups = 4; // vibrational mode groups per PAH
 
 // Device status bits.
 constexpr unsigned kStatusTree = 1u;     // a package met a malformed tree
@@ -59,6 +61,9 @@ struct DevTables {
   float u_ln0[kMaxSpecies];   // ln S_s(T_1)
   float u_inv[kMaxSpecies];   // (n_T - 1) / (ln S_s(T_last) - ln S_s(T_1))
   const float* u_frozen;      // [S][n_leaves] (frozen mode) or null
+  const float* pah_cdf;       // [n_pah][B] template re-emission spectrum of each PAH
+  int pah_of[kMaxSpecies];    // PAH number of each species, -1 for grains
+  int n_coarse;               // coarse bins of the PAH absorbed spectrum
   float u_tmin[kMaxSpecies];  // S_s(t_min)
   float eps_d0_over_V[kMaxLevels];   // eps * d0 / V(level), erg s^-1 cm^-2 (FP32)
   double eps_over_V[kMaxLevels];     // eps / V(level) (FP64, temperatures)
@@ -73,6 +78,7 @@ struct DevRun {
   unsigned long long* sed;        // [2][n_dir][B]
   unsigned long long* counters;   // [kNumCounters]
   unsigned int* status;
+  unsigned* pahabs;               // [n_pah][n_leaves][n_coarse] PAH absorptions
   float src[3];                   // source position, base-cube units
   float beam[3];
   double src64[3];
@@ -117,6 +123,45 @@ struct TableBuild {
   double* star_frac;         // [1] in-range fraction of the stellar blackbody
 };
 cudaError_t launch_build_tables(const TableBuild& tb, cudaStream_t s);
+
+// PAH molecular data: vibrational mode groups (count, characteristic temperature)
+struct PahSpec {
+  int n_groups;
+  double n_modes[kMaxModeGroups];
+  double theta[kMaxModeGroups];
+};
+
+struct PahBuild {
+  int n_pah, M, K, B;
+  const double* nu;          // [B+1]
+  const double* sigma;       // [n_pah][B] cross section per molecule, cm^2
+  PahSpec spec[kMaxPah];
+  double dE[kMaxPah];        // level spacing, erg
+  double T_star, f_ref;      // template heating: source blackbody at bolometric flux f_ref
+  float* s;                  // [n_pah][M][B] emission per level and bin, erg/s
+  double* L;                 // [n_pah][M] cooling rate per level, erg/s
+  double* e_k;               // [K] photon energy of each coarse bin, erg
+  int* q_k;                  // [n_pah][K] floor(e_k / dE)
+  double* w_k;               // [n_pah][K] e_k / dE - q_k
+  float* template_cdf;       // [n_pah][B]
+};
+
+struct PahTables {
+  int n_pah, M, K;
+  const float* s;
+  const double* L;
+  const double* e_k;
+  const int* q_k;
+  const double* w_k;
+  double dE[kMaxPah];
+  double mol_mass[kMaxPah];  // g per molecule
+  int species[kMaxPah];      // species index of each PAH
+};
+
+cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream_t s);
+cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
+                             double eps, double d0, long long first, long long n,
+                             float* j_out, const unsigned char* want, cudaStream_t s);
 
 cudaError_t launch_frozen_u(const DevGrid& g, const DevTables& t, const float* T_frozen,
                             float* u_frozen, float t_min, cudaStream_t s);

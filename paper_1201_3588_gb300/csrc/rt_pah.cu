@@ -1,0 +1,282 @@
+// rt_pah.cu -- transiently heated PAH molecules on the device: FP64 level tables,
+// template re-emission spectra, and the exact steady-state emission per cell.
+//
+// Thermal-discrete steady state (Guhathakurta & Draine 1989): internal-energy
+// levels E_f = f dE, f = 0 .. M-1; absorbing a photon of energy e moves a molecule
+// from E_i up to E_i + e, split between the two levels around it so the energy is
+// kept (uniform levels: e/dE = q + w gives levels i+q and i+q+1 with weights 1-w and
+// w); cooling is continuous at L(E) = 4 pi sum_b sigma_b P_b(T(E)), a step to the
+// level below at rate C_f = L_f / dE. The upward probability flux across each level
+// boundary equals C_f P_f, so the populations follow level by level. The molecule
+// then emits sum_f P_f 4 pi sigma_b P_b(T_f) in bin b.
+
+#include "rt_internal.h"
+#include "rt_planck.cuh"
+
+#include <math.h>
+
+namespace rt {
+namespace {
+
+using namespace planck;
+
+constexpr double kHh = 6.62607015e-27;
+
+__device__ double heat_content(double T, const PahSpec& sp) {
+  if (!(T > 0.0)) return 0.0;
+  double e = 0.0;
+  for (int i = 0; i < sp.n_groups; ++i) {
+    double x = sp.theta[i] / T;
+    if (x < 700.0) e += sp.n_modes[i] * kK * sp.theta[i] / expm1(x);
+  }
+  return e;
+}
+
+__device__ double temperature_of(double E, const PahSpec& sp) {
+  if (!(E > 0.0)) return 0.0;
+  double lo = 1e-3, hi = 10.0;
+  while (heat_content(hi, sp) < E && hi < 1e9) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = sqrt(lo * hi);
+    if (heat_content(mid, sp) < E) lo = mid; else hi = mid;
+    if (hi / lo - 1.0 < 1e-14) break;
+  }
+  return sqrt(lo * hi);
+}
+
+// one thread per (PAH, level): temperature, cooling rate (FP64) and emission
+// spectrum per bin (stored FP32)
+__global__ void k_pah_levels(PahBuild pb) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= pb.n_pah * pb.M) return;
+  int p = idx / pb.M, f = idx % pb.M;
+  const PahSpec& sp = pb.spec[p];
+  double T = temperature_of(f * pb.dE[p], sp);
+  const double* sig = pb.sigma + (size_t)p * pb.B;
+  float* s = pb.s + ((size_t)p * pb.M + f) * pb.B;
+  double L = 0.0;
+  for (int b = 0; b < pb.B; ++b) {
+    double v = 4.0 * kPi * sig[b] * planck_bin(pb.nu[b], pb.nu[b + 1], T);
+    s[b] = (float)v;
+    L += v;
+  }
+  pb.L[idx] = L;
+}
+
+// coarse photon energies e_k = h sqrt(nu_lo nu_hi) over each coarse bin's range,
+// and their split q_k + w_k = e_k / dE for every PAH
+__global__ void k_pah_coarse(PahBuild pb) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= pb.n_pah * pb.K) return;
+  int p = idx / pb.K, k = idx % pb.K;
+  int b0 = (k * pb.B + pb.K - 1) / pb.K;          // first fine bin with floor(b K/B) == k
+  int b1 = ((k + 1) * pb.B + pb.K - 1) / pb.K - 1;  // last one
+  double e = kHh * sqrt(pb.nu[b0] * pb.nu[b1 + 1]);
+  if (p == 0) pb.e_k[k] = e;
+  double x = e / pb.dE[p];
+  double q = floor(x);
+  pb.q_k[idx] = (int)q;
+  pb.w_k[idx] = x - q;
+}
+
+// Level populations of PAH p for absorption rates R[k] (smem, per molecule per
+// second), one warp; P and D are this warp's shared-memory arrays of M doubles.
+// Returns the emitted power sum_f P_f L_f of the normalised populations in P.
+__device__ double solve_levels(const PahTables& t, int p, const double* R, double* P,
+                               double* D) {
+  const int lane = threadIdx.x & 31;
+  const int M = t.M, K = t.K;
+  const double dE = t.dE[p];
+  const int* q = t.q_k + p * K;
+  const double* w = t.w_k + p * K;
+  const double* L = t.L + (size_t)p * M;
+  for (int i = lane; i < M; i += 32) {
+    D[i] = 0.0;
+    P[i] = 0.0;
+  }
+  __syncwarp();
+  double up = 0.0;
+  // scatter level i's absorptions into D; returns this lane's upward rate
+  auto scatter = [&](int i, double Pi) {
+    double u = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      double r = R[k];
+      if (!(r > 0.0)) continue;
+      int f = i + q[k];
+      double wk = w[k];
+      if (f >= M - 1) {
+        f = M - 1;
+        wk = 0.0;
+      }
+      if (f > i) {
+        atomicAdd(&D[f], Pi * r * (1.0 - wk));
+        u += r * (1.0 - wk);
+      }
+      if (wk > 0.0 && f + 1 < M) {
+        atomicAdd(&D[f + 1], Pi * r * wk);
+        u += r * wk;
+      }
+    }
+    return u;
+  };
+  double P0 = 1.0;
+  if (lane == 0) P[0] = P0;
+  up = scatter(0, P0);
+  for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(0xffffffffu, up, o);
+  double F = P0 * up;
+  for (int f = 1; f < M; ++f) {
+    __syncwarp();
+    double C = L[f] / dE;
+    double Pf = C > 0.0 ? F / C : 0.0;
+    if (lane == 0) P[f] = Pf;
+    double u = scatter(f, Pf);
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    __syncwarp();
+    F = fmax(F - D[f] + Pf * u, 0.0);
+    if (Pf > 1e250) {  // keep the numbers finite
+      __syncwarp();
+      for (int i = lane; i < M; i += 32) {
+        P[i] *= 1e-250;
+        D[i] *= 1e-250;
+      }
+      F *= 1e-250;
+    }
+  }
+  __syncwarp();
+  double tot = 0.0, em = 0.0;
+  for (int i = lane; i < M; i += 32) tot += P[i];
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  __syncwarp();
+  for (int i = lane; i < M; i += 32) {
+    P[i] /= tot;
+    em += P[i] * L[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) em += __shfl_xor_sync(0xffffffffu, em, o);
+  __syncwarp();
+  return em;
+}
+
+// Template re-emission spectra: one warp per PAH, heated by the source's blackbody
+// at bolometric flux pb.f_ref inside the frequency grid.
+__global__ void k_pah_template(PahTables t, PahBuild pb) {
+  extern __shared__ double sm[];
+  const int p = blockIdx.x;
+  const int lane = threadIdx.x;
+  double* R = sm;            // [K]
+  double* P = R + t.K;       // [M]
+  double* D = P + t.M;       // [M]
+  const double* sig = pb.sigma + (size_t)p * pb.B;
+  // stellar flux per fine bin, summed into coarse photon rates
+  double tot = 0.0;
+  for (int b = lane; b < pb.B; b += 32) tot += planck_bin(pb.nu[b], pb.nu[b + 1], pb.T_star);
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  for (int k = lane; k < t.K; k += 32) R[k] = 0.0;
+  __syncwarp();
+  for (int b = lane; b < pb.B; b += 32) {
+    double fb = pb.f_ref * planck_bin(pb.nu[b], pb.nu[b + 1], pb.T_star) / tot;
+    int k = (int)(((long long)b * t.K) / pb.B);
+    atomicAdd(&R[k], fb * sig[b] / t.e_k[k]);
+  }
+  __syncwarp();
+  solve_levels(t, p, R, P, D);
+  // J_b = sum_f P_f s_fb, then its normalised cumulative
+  float* cdf = pb.template_cdf + (size_t)p * pb.B;
+  double run = 0.0;
+  for (int b0 = 0; b0 < pb.B; b0 += 32) {
+    int b = b0 + lane;
+    double j = 0.0;
+    if (b < pb.B)
+      for (int f = 0; f < t.M; ++f) j += P[f] * (double)t.s[((size_t)p * t.M + f) * pb.B + b];
+    // inclusive scan over the 32 lanes
+    double x = j;
+    for (int o = 1; o < 32; o <<= 1) {
+      double y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (b < pb.B) cdf[b] = (float)(run + x);  // unnormalised for now
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+  __syncwarp();
+  for (int b = lane; b < pb.B; b += 32) cdf[b] = run > 0.0 ? (float)((double)cdf[b] / run) : 1.0f;
+  __syncwarp();
+  if (lane == 0) cdf[pb.B - 1] = 1.0f;
+}
+
+// Exact emission of cells [first, first + n): one warp per cell, all PAH species;
+// j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin).
+__global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, double eps,
+                            double d0, long long first, long long n, float* j_out,
+                            const unsigned char* want) {
+  extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per_warp = t.K + 2 * t.M;
+  double* R = sm + (size_t)warp * per_warp;
+  double* P = R + t.K;
+  double* D = P + t.M;
+  const long long c = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= n) return;
+  const long long cell = first + c;
+  float* out = j_out + (size_t)c * g.B;
+  if (want && !want[c]) return;
+  for (int b = lane; b < g.B; b += 32) out[b] = 0.0f;
+  const int lev = g.level[cell];
+  const double V = d0 * d0 * d0 / (double)(1ll << (3 * lev));
+  for (int p = 0; p < t.n_pah; ++p) {
+    const unsigned* cnt = pahabs + ((size_t)p * g.n_leaves + cell) * t.K;
+    const int s = t.species[p];
+    const double rho = (double)g.rho[cell * g.S + s] / d0;
+    const double n_mol = rho * V / t.mol_mass[p];
+    unsigned any = 0;
+    for (int k = lane; k < t.K; k += 32) {
+      unsigned v = cnt[k];
+      any |= v;
+      R[k] = n_mol > 0.0 ? (double)v * eps / (t.e_k[k] * n_mol) : 0.0;
+    }
+    if (!__any_sync(0xffffffffu, any != 0)) continue;
+    __syncwarp();
+    solve_levels(t, p, R, P, D);
+    for (int b = lane; b < g.B; b += 32) {
+      double j = 0.0;
+      const float* sp = t.s + (size_t)p * t.M * g.B + b;
+      for (int f = 0; f < t.M; ++f) j += P[f] * (double)sp[(size_t)f * g.B];
+      out[b] += (float)(n_mol * j);
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream_t s) {
+  int n = pb.n_pah * pb.M;
+  k_pah_levels<<<(n + 63) / 64, 64, 0, s>>>(pb);
+  int nk = pb.n_pah * pb.K;
+  k_pah_coarse<<<(nk + 63) / 64, 64, 0, s>>>(pb);
+  size_t smem = sizeof(double) * (t.K + 2 * t.M);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_pah_template,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_pah_template<<<pb.n_pah, 32, smem, s>>>(t, pb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
+                             double eps, double d0, long long first, long long n,
+                             float* j_out, const unsigned char* want, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int warps = 4;
+  size_t smem = sizeof(double) * (size_t)warps * (t.K + 2 * t.M);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_pah_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  long long blocks = (n + warps - 1) / warps;
+  k_pah_exact<<<(unsigned)blocks, 32 * warps, smem, s>>>(g, t, pahabs, eps, d0, first, n,
+                                                        j_out, want);
+  return cudaGetLastError();
+}
+
+}  // namespace rt

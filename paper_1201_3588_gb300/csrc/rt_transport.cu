@@ -201,11 +201,13 @@ struct Pkg {
   bool touched;  // interacted at least once
 };
 
-struct Tally {  // per-thread counters
-  unsigned long long emitted, escaped, capped, absorptions, scatters, crossings, errors,
-      clamped;
-  unsigned long long levels;  // sum of the refinement levels of the cells entered
+struct Tally {  // per-thread counters, flushed to the 64-bit device totals
+  unsigned emitted, escaped, capped, absorptions, scatters, crossings, errors, clamped;
+  unsigned levels;  // child-table reads of the walk
 };
+
+// a flush is forced before any per-thread counter could pass 2^31
+constexpr unsigned kTallyFlushAt = 1u << 31;
 
 enum Adv { kCrossed = 0, kInteract = 1, kEscaped = 2, kError = 3 };
 
@@ -289,7 +291,7 @@ struct Cell {
 
 // Enter the grid at the package's position (full descent from the base cube).
 __device__ __forceinline__ int enter(const Pkg<float>& k, const DevGrid& g, Cell& c,
-                                     unsigned long long& child_reads) {
+                                     unsigned& child_reads) {
   int rc = locate<float>(g, k.p, k.d, c.leaf, c.level, c.I);
   if (rc == 0) child_reads += c.level;
   return rc;
@@ -301,7 +303,7 @@ __device__ __forceinline__ int enter(const Pkg<float>& k, const DevGrid& g, Cell
 // descent when the neighbouring region is finer.
 __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevGrid& g,
                                               const Kappa* kap,
-                                              unsigned long long& child_reads) {
+                                              unsigned& child_reads) {
   const float sz = __int_as_float((127 - c.level) << 23);  // 2^-level
   float lo[3], hi[3];
 #pragma unroll
@@ -470,15 +472,32 @@ __device__ __forceinline__ void reemit(Pkg<R>& k, const DevGrid& g, const DevTab
   k.bin = b;
 }
 
+// Absorption by a PAH species: tally the photon in the cell's coarse absorbed
+// spectrum and draw the new bin from the PAH's template emission spectrum.
+template <typename R>
+__device__ __forceinline__ void pah_absorb(Pkg<R>& k, const DevGrid& g, const DevTables& t,
+                                           const DevRun& r, int p, int leaf, const uint4& w1) {
+  const int kc = (k.bin * t.n_coarse) / g.B;
+  atomicAdd(&r.pahabs[((size_t)p * g.n_leaves + leaf) * t.n_coarse + kc], 1u);
+  const float xb = unit<float>(w1.z);
+  const float* cdf = t.pah_cdf + (size_t)p * g.B;
+  int lo = 0, hi = g.B - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(&cdf[mid]) > xb) hi = mid; else lo = mid + 1;
+  }
+  k.bin = lo;
+}
+
 __device__ __forceinline__ int dir_bin(float dz, int n_dir) {
   int b = (int)floorf(0.5f * (dz + 1.0f) * (float)n_dir);
   return min(max(b, 0), n_dir - 1);
 }
 
-__device__ __forceinline__ void flush_tally(const Tally& tl, unsigned long long* c) {
-  unsigned long long v[kNumCounters] = {tl.emitted,   tl.escaped, tl.capped,
-                                        tl.absorptions, tl.scatters, tl.crossings,
-                                        tl.errors,    tl.clamped, tl.levels};
+__device__ __forceinline__ void flush_tally(Tally& tl, unsigned long long* c) {
+  const unsigned v[kNumCounters] = {tl.emitted,   tl.escaped, tl.capped,
+                                    tl.absorptions, tl.scatters, tl.crossings,
+                                    tl.errors,    tl.clamped, tl.levels};
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) {
     unsigned long long x = v[i];
@@ -486,6 +505,7 @@ __device__ __forceinline__ void flush_tally(const Tally& tl, unsigned long long*
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&c[i], x);
   }
+  tl = Tally{};
 }
 
 // ---------------------------------------------------------------- plain kernel
@@ -527,7 +547,10 @@ __global__ void __launch_bounds__(256) k_transport_plain(DevGrid g, DevTables t,
       int s = interact<R>(k, g, t.kap, leaf, r, w1);
       if (s < 0) { ++tl.scatters; continue; }
       unsigned long long n = atomicAdd(&r.count[(size_t)s * g.n_leaves + leaf], 1ull);
-      reemit<R>(k, g, t, r, s, leaf, level, n, w1, tl);
+      if (t.pah_of[s] >= 0)
+        pah_absorb<R>(k, g, t, r, t.pah_of[s], leaf, w1);
+      else
+        reemit<R>(k, g, t, r, s, leaf, level, n, w1, tl);
       ++tl.absorptions;
     }
   }
@@ -543,7 +566,9 @@ __global__ void __launch_bounds__(256) k_transport_plain(DevGrid g, DevTables t,
 // or no lane is left walking, so both phases run with most lanes active. Each
 // package's history is unchanged by this schedule. Absorptions of lanes hitting
 // the same (species, cell) in one phase are merged into one atomic.
-__global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, DevRun r) {
+template <int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks)
+    k_transport_pool(DevGrid g, DevTables t, DevRun r) {
   extern __shared__ unsigned long long smem_u64[];
   const int S = g.S, B = g.B;
   const int n_sed = 2 * g.n_dir * B;
@@ -600,6 +625,8 @@ __global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, 
       }
     }
     if (!__any_sync(kFull, alive)) break;
+    if (__any_sync(kFull, tl.crossings >= kTallyFlushAt || tl.levels >= kTallyFlushAt))
+      flush_tally(tl, r.counters);
     if (lane == 0) stop = global_ns() - t0 > r.budget_ns;
     stop = __shfl_sync(kFull, stop, 0);
     if (stop) {
@@ -655,8 +682,11 @@ __global__ void __launch_bounds__(256) k_transport_pool(DevGrid g, DevTables t, 
           old = atomicAdd(&r.count[(size_t)sp * g.n_leaves + cell.leaf],
                           (unsigned long long)__popc(peers));
         old = __shfl_sync(peers, old, leader);
-        reemit<float>(k, g, t, r, sp, cell.leaf, cell.level, old + __popc(peers & lt_mask), w1,
-                      tl);
+        if (t.pah_of[sp] >= 0)
+          pah_absorb<float>(k, g, t, r, t.pah_of[sp], cell.leaf, w1);
+        else
+          reemit<float>(k, g, t, r, sp, cell.leaf, cell.level, old + __popc(peers & lt_mask),
+                        w1, tl);
         ++tl.absorptions;
       }
     }
@@ -701,7 +731,19 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
     uint4 w1;
     int s = interact<float>(k, g, t.kap, c.leaf, r, w1);
     if (s < 0) { ++rec[2]; continue; }
-    reemit<float>(k, g, t, r, s, c.leaf, c.level, 0ull, w1, tl);
+    if (t.pah_of[s] >= 0) {
+      // replay does not tally: only the new bin is drawn
+      const float xb = unit<float>(w1.z);
+      const float* cdf = t.pah_cdf + (size_t)t.pah_of[s] * g.B;
+      int lo = 0, hi = g.B - 1;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(&cdf[mid]) > xb) hi = mid; else lo = mid + 1;
+      }
+      k.bin = lo;
+    } else {
+      reemit<float>(k, g, t, r, s, c.leaf, c.level, 0ull, w1, tl);
+    }
     ++rec[1];
   }
   rec[0] = k.event;
@@ -767,6 +809,31 @@ static size_t sed_smem(const DevGrid& g) {
   return sizeof(unsigned long long) * 2 * g.n_dir * g.B;
 }
 
+template <int kMinBlocks>
+static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, const DevRun& r,
+                                       int blocks_per_sm, int threads, int sms, cudaStream_t s) {
+  DevRun rr = r;
+  rr.sed_in_smem = table_smem(g) + sed_smem(g) <= kSmemBudget ? 1 : 0;
+  size_t sm = table_smem(g) + (rr.sed_in_smem ? sed_smem(g) : 0);
+  cudaError_t e;
+  if (sm > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_transport_pool<kMinBlocks>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_pool<kMinBlocks>, threads,
+                                                    sm);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  int bps = blocks_per_sm > 0 ? (blocks_per_sm < occ ? blocks_per_sm : occ) : occ;
+  k_transport_pool<kMinBlocks><<<sms * bps, threads, sm, s>>>(g, t, rr);
+  return cudaGetLastError();
+}
+
+// blocks_per_sm selects the register budget: 5 or 6 resident blocks of 256 threads
+// use variants compiled for that occupancy (fewer registers, some spills); other
+// values use the 4-block variant (no spills), capped at its occupancy.
 cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
                                   int blocks_per_sm, int threads, cudaStream_t s) {
   int dev = 0, sms = 0;
@@ -774,22 +841,11 @@ cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const De
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  DevRun rr = r;
-  rr.sed_in_smem = table_smem(g) + sed_smem(g) <= kSmemBudget ? 1 : 0;
-  size_t sm = table_smem(g) + (rr.sed_in_smem ? sed_smem(g) : 0);
-  if (sm > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_transport_pool, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  if (blocks_per_sm <= 0) {
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_pool, threads, sm);
-    if (e != cudaSuccess) return e;
-    blocks_per_sm = occ > 0 ? occ : 1;
-  }
-  k_transport_pool<<<sms * blocks_per_sm, threads, sm, s>>>(g, t, rr);
-  return cudaGetLastError();
+  if (threads == 256 && blocks_per_sm == 6)
+    return launch_pool_variant<6>(g, t, r, blocks_per_sm, threads, sms, s);
+  if (threads == 256 && blocks_per_sm == 5)
+    return launch_pool_variant<5>(g, t, r, blocks_per_sm, threads, sms, s);
+  return launch_pool_variant<4>(g, t, r, blocks_per_sm, threads, sms, s);
 }
 
 cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const DevRun& r,

@@ -16,6 +16,7 @@ import numpy as np
 from . import _build
 
 REEMIT_BW, REEMIT_NOCORR, REEMIT_FROZEN = 0, 1, 2
+PAH_EXACT, PAH_SURROGATE, PAH_AUTO = 0, 1, 2
 KERNEL_POOL, KERNEL_PLAIN_F32, KERNEL_PLAIN_F64 = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
@@ -76,6 +77,11 @@ SIGNATURES = {
     "rt_trace": [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p],
     "rt_philox": [C.c_void_p, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p],
     "rt_status_string": [C.c_int],
+    "rt_set_pah": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_int,
+                   C.c_int, C.c_double],
+    "rt_pah_absorbed": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_pah_emission": [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_float,
+                        C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "rt_cell_temperatures_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_double,
                                      C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
@@ -129,7 +135,8 @@ def _ptr_mem(x):
 class Grid:
     """One model on the device (handle to ``rt_grid``)."""
 
-    def __init__(self, model, n_temp: int = 0, t_min: float = 0.0, t_max: float = 0.0):
+    def __init__(self, model, n_temp: int = 0, t_min: float = 0.0, t_max: float = 0.0,
+                 pah_levels: int = 400, pah_t_top: float = 2500.0):
         L = load()
         t = model.tree
         self.model = model
@@ -154,6 +161,13 @@ class Grid:
             gg = np.ascontiguousarray(g[s])
             _check(L.rt_set_dust(h, s, ka.ctypes.data, ks.ctypes.data, gg.ctypes.data,
                                  self.B, int(sp.is_pah), int(sp.n_carbon)), "rt_set_dust")
+            if sp.is_pah:
+                modes = np.ascontiguousarray(np.array(sp.modes, dtype=np.float64).ravel())
+                _check(L.rt_set_pah(h, s, int(sp.n_carbon), int(sp.n_hydrogen),
+                                    float(sp.mol_mass), modes.ctypes.data, len(sp.modes),
+                                    pah_levels, float(pah_t_top)), "rt_set_pah")
+        self.n_pah = sum(1 for sp in model.species if sp.is_pah)
+        self.n_coarse = min(64, self.B)
 
     # -- lifecycle
     def close(self):
@@ -230,6 +244,26 @@ class Grid:
             counts = np.ascontiguousarray(counts, dtype=np.uint64).reshape(self.S, self.N)
         p, mem = _ptr_mem(counts)
         _check(load().rt_set_counts(self._h, p, mem, _stream(stream)), "rt_set_counts")
+
+    def pah_absorbed(self, out=None, stream=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros((self.n_pah, self.N, self.n_coarse), dtype=np.uint32)
+        p, mem = _ptr_mem(out)
+        _check(load().rt_pah_absorbed(self._h, p, mem, _stream(stream)), "rt_pah_absorbed")
+        return out
+
+    def pah_emission(self, first: int = 0, n: Optional[int] = None, mode: int = PAH_EXACT,
+                     surrogate=None, tol: float = 0.0, out=None, stream=None):
+        n = self.N - first if n is None else n
+        if out is None:
+            out = np.zeros((n, self.B), dtype=np.float32)
+        p, mem = _ptr_mem(out)
+        nf = C.c_uint64()
+        _check(load().rt_pah_emission(self._h, int(first), int(n), int(mode),
+                                      surrogate._h if surrogate is not None else None,
+                                      float(tol), p, mem, C.byref(nf), _stream(stream)),
+               "rt_pah_emission")
+        return out, int(nf.value)
 
     def counters(self) -> dict:
         c = _Counters()

@@ -203,6 +203,9 @@ class Species:
     kappa_v_ext: float      # extinction opacity at 0.55 micron, cm^2/g
     is_pah: int = 0
     n_carbon: int = 0
+    n_hydrogen: int = 0
+    mol_mass: float = 0.0   # g per molecule (PAH)
+    modes: tuple = ()       # ((count, theta_K), ...) vibrational modes (PAH)
 
 
 def powerlaw_species(name: str, nu_edges: np.ndarray, kappa_v_ext: float,
@@ -224,6 +227,64 @@ def grey_species(n_bins: int, kappa_abs: float, kappa_sca: float = 0.0,
                  g: float = 0.0, name: str = "grey") -> Species:
     return Species(name, np.full(n_bins, float(kappa_abs)), np.full(n_bins, float(kappa_sca)),
                    np.full(n_bins, float(g)), float(kappa_abs + kappa_sca))
+
+
+AMU = 1.66053906660e-24     # g
+H_PLANCK = 6.62607015e-27   # erg s (only for the band-centre conversion below)
+
+# Synthetic PAH material data. The real cross sections and band parameters the
+# paper uses are not available; these stand in for them with the same structure:
+# a far-UV-rising continuum with a long-wavelength cut-off that moves redwards with
+# size, plus 17 Lorentzian infrared bands, per carbon atom.
+PAH_N_BANDS = 17
+PAH_BAND_LAMBDA_UM = np.geomspace(3.0, 17.0, PAH_N_BANDS)     # band centres
+PAH_BAND_FWHM_FRAC = 0.03                                      # FWHM / centre (frequency)
+PAH_BAND_PEAK = 4.0e-20                                        # cm^2 per C atom at a peak
+PAH_UV_SIGMA = 7.0e-18                                         # cm^2 per C at 0.1 micron
+
+
+def pah_hydrogens(n_carbon: int) -> int:
+    """Hydrogen count of a compact PAH, N_H ~ sqrt(6 N_C)."""
+    return int(round(math.sqrt(6.0 * n_carbon)))
+
+
+def pah_cross_section_per_carbon(nu_edges: np.ndarray, n_carbon: int) -> np.ndarray:
+    """Bin-averaged absorption cross section per C atom (cm^2): continuum
+    (lambda/0.1um)^-1 / (1 + (lambda/lambda_c)^6) with lambda_c = 0.5 um (N_C/50)^(1/4),
+    taken at the bin centre, plus the Lorentzian bands averaged over each bin in
+    closed form (arctan)."""
+    lam_um = bin_centre_wavelength(nu_edges) / MICRON
+    lam_c = 0.5 * (n_carbon / 50.0) ** 0.25
+    cont = PAH_UV_SIGMA * (lam_um / 0.1) ** -1.0 / (1.0 + (lam_um / lam_c) ** 6)
+    nu0, nu1 = nu_edges[:-1], nu_edges[1:]
+    bands = np.zeros_like(cont)
+    for lc in PAH_BAND_LAMBDA_UM:
+        nuc = C_LIGHT / (lc * MICRON)
+        hw = 0.5 * PAH_BAND_FWHM_FRAC * nuc
+        # Lorentzian with peak PAH_BAND_PEAK: sigma(nu) = peak hw^2 / ((nu-nuc)^2 + hw^2)
+        integral = PAH_BAND_PEAK * hw * (np.arctan((nu1 - nuc) / hw) - np.arctan((nu0 - nuc) / hw))
+        bands += integral / (nu1 - nu0)
+    return cont + bands
+
+
+def pah_modes(n_carbon: int, n_hydrogen: int) -> tuple:
+    """Einstein-type vibrational modes (count, characteristic temperature K):
+    3 N_C - 6 skeletal C-C modes at 900 K, 2 N_H C-H bends at 1600 K and N_H C-H
+    stretches at 4360 K -- 3 (N_C + N_H) - 6 modes in all."""
+    return ((3 * n_carbon - 6, 900.0), (2 * n_hydrogen, 1600.0), (n_hydrogen, 4360.0))
+
+
+def pah_species(nu_edges: np.ndarray, n_carbon: int) -> Species:
+    """A PAH species: absorption only (no scattering), opacity per gram of PAH."""
+    nh = pah_hydrogens(n_carbon)
+    m = (12.011 * n_carbon + 1.008 * nh) * AMU
+    sigma = n_carbon * pah_cross_section_per_carbon(nu_edges, n_carbon)
+    kabs = sigma / m
+    lam = bin_centre_wavelength(nu_edges)
+    kv = float(np.interp(math.log(LAMBDA_V), np.log(lam[::-1]), kabs[::-1]))
+    return Species(f"pah{n_carbon}", kabs, np.zeros_like(kabs), np.zeros_like(kabs), kv,
+                   is_pah=1, n_carbon=n_carbon, n_hydrogen=nh, mol_mass=m,
+                   modes=pah_modes(n_carbon, nh))
 
 
 # Mass split between the two large-grain species, from the abundances [Si] = 31 ppm
