@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--packages", type=float, default=1e8, help="packages per GPU per step")
-    p.add_argument("--workload", choices=["disk", "sphere"], default="disk")
+    p.add_argument("--workload", choices=["disk", "sphere", "batch"], default="disk")
+    p.add_argument("--batch-models", type=int, default=256)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--plain-packages", type=float, default=1e7)
     p.add_argument("--no-plain", action="store_true")
@@ -181,6 +182,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM traffic of the pool kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum over a 2e6-package launch on the disk, scaled per package),
+# valid only for the kernel source it was measured on.
+TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
+                       "paper_1201_3588_gb300/csrc/rt_internal.h"),
+           "sha256": None, "dram_bytes_per_package": None}
+
+
+def traffic_per_launch(n_packages):
+    import hashlib
+    if not TRAFFIC["sha256"] or not TRAFFIC["dram_bytes_per_package"]:
+        return None
+    h = hashlib.sha256()
+    for f in TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != TRAFFIC["sha256"]:
+        return None
+    return TRAFFIC["dram_bytes_per_package"] * n_packages
+
+
 def walk_bytes(c, S):
     """Algorithmic bytes of one transport launch (per unit of work):
     every cell entered reads one base-cube id (4 B), one child id per refinement
@@ -262,7 +284,7 @@ def run_ours(args):
     bytes_launch = walk_bytes(c, S)
     achieved = bytes_launch / kmean / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "frac": achieved / hbm, "traffic": traffic_per_launch(n), "peak_source": src,
             "kernel": "k_transport_pool", "kernel_ms": 1e3 * kmean,
             "algorithmic_bytes_per_launch": bytes_launch}
 
@@ -353,10 +375,59 @@ def e2e_rate(model, n, world, first, steps):
             "ms_per_step": 1e3 * sum(times) / len(times)}
 
 
+def run_batch(args):
+    """Config of many uneven models in one graph-captured persistent launch: a step is
+    one replay of (reset, batched transport, every model's temperatures)."""
+    import torch
+    from paper_1201_3588_gb300 import autotune, rt, workloads as w
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    models = w.batch_models(n_models=args.batch_models, seed=0, n_bins=100)
+    grids = []
+    for m, n in models:
+        g = rt.Grid(m)
+        g.emit_star(n)
+        grids.append(g)
+    npk = [n for _, n in models]
+    total = sum(npk)
+    # tune on the largest model's class
+    big = max(range(len(models)), key=lambda i: grids[i].N)
+    opts = autotune.tune(grids[big], models[big][0].recipe["tau_v"], n_probe=1_000_000)
+    b = rt.Batch(grids, npk, seed=0, **opts)
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        b.run_graph(stream)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        a.record(stream)
+        for _ in range(args.steps):
+            b.run_graph(stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+    el = a.elapsed_time(e) / 1e3
+    c = [g.counters() for g in grids]
+    emitted = sum(x["emitted"] for x in c)
+    line = {"metric": METRIC, "value": total * args.steps / el, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {len(models)} uneven sphere/disk models, 100 bins, "
+                                   "one graph-captured persistent launch",
+                       "packages_per_step": total, "leaves_total": sum(g.N for g in grids),
+                       "autotuned": opts},
+            "gpu_launches": (1 + len(grids)) * args.steps, "clocks": clk.summary(),
+            "check": {"emitted_last_step": emitted,
+                      "errors": sum(x["errors"] for x in c)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -164,6 +164,35 @@ rt_status rt_set_counts(rt_grid *g, const uint64_t *in, int mem, void *stream);
  * last stream and reports device-side faults. */
 rt_status rt_get_counters(rt_grid *g, rt_counters *out);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many models (grids) of uneven size, optical depth and package count in
+ * one persistent launch. Warps take chunks of `chunk` packages (model, index range)
+ * from a device queue, interleaved over the models, and run the packet pool on the
+ * chunk's model. The plan holds every device array the launch needs, so running it
+ * allocates nothing and can be captured in a CUDA graph.
+ * ------------------------------------------------------------------------- */
+typedef struct rt_batch rt_batch;
+
+/* Plan packages 0 .. n_packages[m]-1 of every grid m (seed + m keys model m's Philox
+ * streams; o: as rt_transport, pool kernel only; chunk 0: 4096). Builds missing
+ * tables (synchronising) and allocates the plan's device arrays. The grids must
+ * outlive the plan and stay on the current device. */
+rt_status rt_batch_create(rt_grid *const *grids, int n, const uint64_t *n_packages,
+                          uint64_t seed, const rt_run_opts *o, uint64_t chunk, rt_batch **out);
+rt_status rt_batch_destroy(rt_batch *b);
+
+/* One pass: optionally zero every grid's tallies (reset), the batched transport
+ * launch, and optionally every grid's temperatures into a buffer of the grid
+ * (read with rt_batch_temperatures). Asynchronous on `stream`. */
+rt_status rt_batch_run(rt_batch *b, int reset, int temperatures, void *stream);
+
+/* rt_batch_run(b, 1, 1, .) recorded once into a CUDA graph (on a stream of the
+ * plan's own), then launched on `stream`; later calls replay the graph. */
+rt_status rt_batch_run_graph(rt_batch *b, void *stream);
+
+/* Temperatures [n_species][n_leaves] of model `model` from the last run. */
+rt_status rt_batch_temperatures(rt_batch *b, int model, float *T_out, int mem, void *stream);
+
 /* Replay: the histories of the listed packages (host ids) in the frozen mode,
  * one thread per package with the FP32 transport code. Each record holds
  * {events, absorptions, scatters, crossings, escaped, capped, final_bin,
@@ -198,15 +227,67 @@ rt_status rt_set_pah(rt_grid *g, int species, int n_carbon, int n_hydrogen, doub
 rt_status rt_pah_absorbed(rt_grid *g, uint32_t *out, int mem, void *stream);
 
 /* Emission of the transiently heated PAHs of cells first_cell .. first_cell+n_cells-1
- * into j_out [n_cells][n_bins] (erg/s per bin, summed over PAH species): for each
- * cell the thermal-discrete steady state of each PAH under the photon absorption
- * rates its absorbed spectrum implies (count * eps / (h nu_k N_molecules)), then
- * N_molecules sum_f P_f 4 pi sigma_b P_b(T_f). Emitted power equals absorbed power.
- * mode RT_PAH_EXACT solves every cell (one warp per cell, FP64 populations);
- * `surrogate`, `tol` and n_fallback_out serve the learned mode. */
-rt_status rt_pah_emission(rt_grid *g, int64_t first_cell, int64_t n_cells, int mode,
-                          const void *surrogate, float tol, float *j_out, int mem,
+ * into j_out [n_cells][n_bins] (erg/s per bin; all PAH species summed, or only PAH
+ * number `pah` when pah >= 0). Exact (RT_PAH_EXACT): for each cell and PAH, the
+ * thermal-discrete steady state under the photon absorption rates its absorbed
+ * spectrum implies (count * eps / (h nu_k N_molecules)), then N_molecules
+ * sum_f P_f 4 pi sigma_b P_b(T_f), one warp per cell with FP64 populations; emitted
+ * power equals absorbed power. RT_PAH_SURROGATE: the network `surrogate` (an rt_mlp
+ * with n_in = n_coarse + 2, n_out = n_bins, trained on rt_pah_training_pairs)
+ * predicts each PAH's emission relative to its absorbed power (decoded as
+ * q_b = exp(7 (y_b - 1)) - 1e-6, floored at 0); the prediction is rescaled to
+ * conserve energy. RT_PAH_AUTO: as SURROGATE, but a cell goes to the
+ * exact solution when for any PAH the prediction's energy residual |sum_b q_b - 1|
+ * before rescaling exceeds `tol`, or its absorbed power per molecule lies outside
+ * the range set with rt_mlp_set_range. *n_fallback_out (may be NULL) receives the
+ * number of such cells. Synchronises only for a host output or a fallback count. */
+typedef struct rt_mlp rt_mlp;
+rt_status rt_pah_emission(rt_grid *g, int64_t first_cell, int64_t n_cells, int pah, int mode,
+                          const rt_mlp *surrogate, float tol, float *j_out, int mem,
                           uint64_t *n_fallback_out, void *stream);
+
+/* Training pairs for the surrogate, PAH number `pah`, cells first_cell ..: features
+ * X [n][n_coarse+2] (x_k = ln(a_k + 1e-4)/4.6 + 1 for the fraction a_k of absorbed
+ * photons in coarse bin k; (log10(P_abs/N_molecules) + 12)/4; log10(N_C) - 2), exact
+ * targets Y [n][n_bins] = ln(J_b/P_abs + 1e-6)/7 + 1, and p_abs [n] (erg/s; 0 where
+ * the PAH absorbed nothing -- such rows carry no information). Device buffers. */
+rt_status rt_pah_training_pairs(rt_grid *g, int pah, int64_t first_cell, int64_t n_cells,
+                                float *X, float *Y, float *p_abs, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Multilayer perceptron of the PAH emission surrogate (the learned stand-in for the
+ * transient-heating computation; BF16 tensor-core GEMMs with FP32 accumulation,
+ * FP32 master weights and Adam). Hidden layers use silu(z) = z / (1 + e^-z), the
+ * output layer is linear, the loss is the mean squared error over rows and outputs.
+ * Parameters are exchanged as FP32 host arrays in the layout: for each layer
+ * W [n_out][n_in] row-major, then b [n_out]. A handle is used by one host thread at
+ * a time on the device current at creation.
+ * ------------------------------------------------------------------------- */
+/* n_layers hidden layers of n_hidden units (1..7), He-uniform weights from `seed`. */
+rt_status rt_mlp_create(int n_in, int n_hidden, int n_layers, int n_out, uint64_t seed,
+                        rt_mlp **out);
+rt_status rt_mlp_destroy(rt_mlp *m);
+rt_status rt_mlp_n_params(const rt_mlp *m, int64_t *n);
+rt_status rt_mlp_dims(const rt_mlp *m, int *n_in, int *n_out);
+/* Admissible range of input n_in - 2 (the absorbed power per molecule of the PAH
+ * features); rt_pah_emission in RT_PAH_AUTO sends cells outside it to the exact
+ * solution. Default: unbounded. */
+rt_status rt_mlp_set_range(rt_mlp *m, float lo, float hi);
+rt_status rt_mlp_get_range(const rt_mlp *m, float *lo, float *hi);
+rt_status rt_mlp_get_params(rt_mlp *m, float *out);       /* host [n_params] */
+rt_status rt_mlp_set_params(rt_mlp *m, const float *in);  /* host [n_params] */
+
+/* y [M][n_out] = network(x [M][n_in]); device FP32 buffers; asynchronous. */
+rt_status rt_mlp_forward(rt_mlp *m, const float *x, float *y, int64_t M, void *stream);
+
+/* Loss and gradients of a batch (device x [M][n_in], targets t [M][n_out]) into the
+ * handle's gradient buffer; loss_out / grad_out (host, may be NULL) receive the loss
+ * and a copy of the gradients (synchronising when either is given). */
+rt_status rt_mlp_loss_grad(rt_mlp *m, const float *x, const float *t, int64_t M,
+                           float *loss_out, float *grad_out, void *stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the last gradients. */
+rt_status rt_mlp_adam_step(rt_mlp *m, float lr, void *stream);
 
 const char *rt_status_string(rt_status s);
 

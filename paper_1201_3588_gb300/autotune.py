@@ -1,0 +1,66 @@
+"""Autotuner of the packet-pool launch: for a grid, time the transport of a package
+prefix under each candidate (resident blocks per SM, interaction batch, refill
+period) with CUDA events and keep the fastest. Results are cached in a JSON file
+keyed by the workload class (cells to the nearest power of two, bins, optical-depth
+decade)."""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+from typing import Dict, Optional
+
+from . import rt
+
+CANDIDATES = dict(blocks_per_sm=(0, 5), interaction_batch=(4, 6, 8, 12), refill_period=(4, 8, 16))
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1201_3588_gb300",
+                             "autotune.json")
+
+
+def workload_key(grid: "rt.Grid", tau_v: float) -> str:
+    return (f"cells2^{int(round(math.log2(max(grid.N, 1))))}-bins{grid.B}-"
+            f"tau1e{int(math.floor(math.log10(max(tau_v, 1e-30))))}")
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def tune(grid: "rt.Grid", tau_v: float, n_probe: int = 2_000_000, cache: Optional[str] = None,
+         force: bool = False) -> Dict[str, int]:
+    """Best launch options for this grid's class (the grid must have a source with at
+    least n_probe planned packages; its tallies are reset afterwards)."""
+    import torch
+    path = cache or DEFAULT_CACHE
+    db = _load(path)
+    key = workload_key(grid, tau_v)
+    if key in db and not force:
+        return db[key]["opts"]
+    s = torch.cuda.current_stream()
+    grid.transport(min(n_probe, 100_000), seed=1)      # warm
+    best = None
+    for bps, ib, rp in itertools.product(*CANDIDATES.values()):
+        opts = dict(blocks_per_sm=bps, interaction_batch=ib, refill_period=rp)
+        grid.reset(s)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        grid.transport(n_probe, seed=7, stream=s, **opts)
+        b.record(s)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        if best is None or ms < best[0]:
+            best = (ms, opts)
+    grid.reset(s)
+    torch.cuda.synchronize()
+    db[key] = {"opts": best[1], "ms_per_probe": best[0], "n_probe": n_probe}
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(db, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return best[1]

@@ -60,6 +60,13 @@ struct rt_grid {
   unsigned* d_pahabs = nullptr;
   float* d_jscratch = nullptr;
   size_t jscratch_n = 0;
+  // surrogate scratch (cells per chunk)
+  long long sur_cap = 0;
+  float* d_sx = nullptr;       // [chunk][K+2]
+  float* d_sy = nullptr;       // [n_pah][chunk][B]
+  float* d_spabs = nullptr;    // [n_pah][chunk]
+  unsigned char* d_sflag = nullptr;
+  unsigned long long* d_scount = nullptr;
   // host state
   std::vector<double> nu, kabs, ksca, ghg;   // [S][B]
   std::vector<char> dust_set;
@@ -152,6 +159,11 @@ void free_all(rt_grid* g) {
   dfree(g->d_Tscratch);
   dfree(g->d_pahabs);
   dfree(g->d_jscratch);
+  dfree(g->d_sx);
+  dfree(g->d_sy);
+  dfree(g->d_spabs);
+  dfree(g->d_sflag);
+  dfree(g->d_scount);
 }
 
 // Walk the tree from every base cube: every leaf id must appear exactly once,
@@ -262,6 +274,7 @@ rt_status build_pah_tables(rt_grid* g, cudaStream_t s) {
     pb.dE[p] = pt.dE[p] = e_max / (M - 1);
     pt.mol_mass[p] = g->pah_mass[(size_t)sp];
     pt.species[p] = sp;
+    pt.n_carbon[p] = g->n_carbon[(size_t)sp];
     g->tab.pah_of[sp] = p;
   }
   RT_CUDA(cudaMemcpyAsync(g->d_pah_sigma, sigma.data(), sizeof(double) * P * B,
@@ -864,39 +877,287 @@ rt_status rt_pah_absorbed(rt_grid* g, uint32_t* out, int mem, void* stream) {
   return RT_OK;
 }
 
-rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int mode,
-                          const void* surrogate, float tol, float* j_out, int mem,
+static rt_status surrogate_scratch(rt_grid* g, long long chunk) {
+  if (chunk <= g->sur_cap) return RT_OK;
+  dfree(g->d_sx);
+  dfree(g->d_sy);
+  dfree(g->d_spabs);
+  dfree(g->d_sflag);
+  g->sur_cap = 0;
+  const int K = g->tab.n_coarse, B = g->desc.n_bins, P = g->n_pah;
+  rt_status st;
+  if ((st = dalloc(&g->d_sx, (size_t)chunk * (K + 2))) != RT_OK) return st;
+  if ((st = dalloc(&g->d_sy, (size_t)P * chunk * B)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_spabs, (size_t)P * chunk)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_sflag, (size_t)chunk)) != RT_OK) return st;
+  if (!g->d_scount && (st = dalloc(&g->d_scount, 1)) != RT_OK) return st;
+  g->sur_cap = chunk;
+  return RT_OK;
+}
+
+static float* output_buffer(rt_grid* g, float* j_out, int mem, size_t n, rt_status* st) {
+  *st = RT_OK;
+  if (mem == RT_MEM_DEVICE) return j_out;
+  if (g->jscratch_n < n) {
+    dfree(g->d_jscratch);
+    g->jscratch_n = 0;
+    if ((*st = dalloc(&g->d_jscratch, n)) != RT_OK) return nullptr;
+    g->jscratch_n = n;
+  }
+  return g->d_jscratch;
+}
+
+rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int pah, int mode,
+                          const rt_mlp* surrogate, float tol, float* j_out, int mem,
                           uint64_t* n_fallback_out, void* stream) {
   if (!g || !j_out || first_cell < 0 || n_cells < 0) return RT_ERR_ARG;
   if (first_cell > g->desc.n_leaves || n_cells > g->desc.n_leaves - first_cell)
     return RT_ERR_ARG;
-  if (mode != RT_PAH_EXACT) return RT_ERR_ARG;
-  (void)surrogate;
-  (void)tol;
+  if (mode != RT_PAH_EXACT && mode != RT_PAH_SURROGATE && mode != RT_PAH_AUTO) return RT_ERR_ARG;
+  if (mode != RT_PAH_EXACT && !surrogate) return RT_ERR_ARG;
   cudaStream_t s = as_stream(stream);
   RT_CUDA(cudaSetDevice(g->dev));
   rt_status st = build_tables(g, s);
   if (st != RT_OK) return st;
   if (g->n_pah == 0) return RT_ERR_STATE;
+  if (pah < -1 || pah >= g->n_pah) return RT_ERR_ARG;
+  const int B = g->desc.n_bins, K = g->tab.n_coarse, F = K + 2;
+  if (mode != RT_PAH_EXACT) {
+    int ni = 0, no = 0;
+    float lo = 0, hi = 0;
+    if (rt_mlp_dims(surrogate, &ni, &no) != RT_OK || ni != F || no != B) return RT_ERR_ARG;
+    rt_mlp_get_range(surrogate, &lo, &hi);
+    (void)lo;
+  }
   if (n_fallback_out) *n_fallback_out = 0;
   if (n_cells == 0) return RT_OK;
-  const size_t n = (size_t)n_cells * g->desc.n_bins;
-  float* dst = j_out;
-  if (mem != RT_MEM_DEVICE) {
-    if (g->jscratch_n < n) {
-      dfree(g->d_jscratch);
-      g->jscratch_n = 0;
-      if ((st = dalloc(&g->d_jscratch, n)) != RT_OK) return st;
-      g->jscratch_n = n;
+  const size_t n = (size_t)n_cells * B;
+  float* dst = output_buffer(g, j_out, mem, n, &st);
+  if (st != RT_OK) return st;
+  if (mode == RT_PAH_EXACT) {
+    RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, n_cells, dst,
+                             nullptr, pah, s));
+  } else {
+    rt_mlp* m = const_cast<rt_mlp*>(surrogate);
+    float x_lo = -1e30f, x_hi = 1e30f;
+    rt_mlp_get_range(m, &x_lo, &x_hi);
+    const long long chunk = n_cells < (1ll << 18) ? n_cells : (1ll << 18);
+    if ((st = surrogate_scratch(g, chunk)) != RT_OK) return st;
+    RT_CUDA(cudaMemsetAsync(g->d_scount, 0, sizeof(unsigned long long), s));
+    const float t = mode == RT_PAH_AUTO ? tol : 1e30f;
+    for (long long c0 = 0; c0 < n_cells; c0 += chunk) {
+      const long long nc = n_cells - c0 < chunk ? n_cells - c0 : chunk;
+      float* out = dst + (size_t)c0 * B;
+      RT_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * nc * B, s));
+      RT_CUDA(cudaMemsetAsync(g->d_sflag, 0, (size_t)nc, s));
+      for (int p = 0; p < g->n_pah; ++p) {
+        if (pah >= 0 && p != pah) continue;
+        float* Y = g->d_sy + (size_t)p * chunk * B;
+        float* pa = g->d_spabs + (size_t)p * chunk;
+        RT_CUDA(launch_pah_features(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, p,
+                                    first_cell + c0, nc, g->d_sx, pa, s));
+        if ((st = rt_mlp_forward(m, g->d_sx, Y, nc, s)) != RT_OK) return st;
+        RT_CUDA(launch_surrogate_check(Y, g->d_sx, pa, nc, B, F, t, x_lo, x_hi, g->d_sflag, s));
+      }
+      for (int p = 0; p < g->n_pah; ++p) {
+        if (pah >= 0 && p != pah) continue;
+        RT_CUDA(launch_surrogate_add(g->d_sy + (size_t)p * chunk * B, g->d_spabs + (size_t)p * chunk,
+                                     nc, B, mode == RT_PAH_AUTO ? g->d_sflag : nullptr, out, s));
+      }
+      if (mode == RT_PAH_AUTO)
+        RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell + c0, nc,
+                                 out, g->d_sflag, pah, s));
+      RT_CUDA(launch_count_flags(g->d_sflag, nc, g->d_scount, s));
     }
-    dst = g->d_jscratch;
+    if (n_fallback_out) {
+      unsigned long long nf = 0;
+      RT_CUDA(cudaMemcpyAsync(&nf, g->d_scount, sizeof(nf), cudaMemcpyDeviceToHost, s));
+      RT_CUDA(cudaStreamSynchronize(s));
+      *n_fallback_out = nf;
+    }
   }
-  RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, n_cells,
-                           dst, nullptr, s));
   if (mem != RT_MEM_DEVICE) {
     RT_CUDA(cudaMemcpyAsync(j_out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
     return sync_status(g, s);
   }
+  return RT_OK;
+}
+
+rt_status rt_pah_training_pairs(rt_grid* g, int pah, int64_t first_cell, int64_t n_cells,
+                                float* X, float* Y, float* p_abs, void* stream) {
+  if (!g || !X || !Y || !p_abs || first_cell < 0 || n_cells < 0) return RT_ERR_ARG;
+  if (first_cell > g->desc.n_leaves || n_cells > g->desc.n_leaves - first_cell)
+    return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  if (pah < 0 || pah >= g->n_pah) return RT_ERR_ARG;
+  if (n_cells == 0) return RT_OK;
+  RT_CUDA(launch_pah_features(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, pah, first_cell,
+                              n_cells, X, p_abs, s));
+  RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, n_cells, Y,
+                           nullptr, pah, s));
+  RT_CUDA(launch_pah_encode(Y, p_abs, n_cells, g->desc.n_bins, Y, s));
+  return RT_OK;
+}
+
+}  // extern "C"
+
+struct rt_batch {
+  int dev = 0;
+  std::vector<rt_grid*> grids;
+  std::vector<unsigned long long> n_pk;
+  ModelDesc* d_models = nullptr;
+  BatchChunk* d_chunks = nullptr;
+  unsigned long long* d_next = nullptr;
+  long long n_chunks = 0;
+  int blocks_per_sm = 0;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+};
+
+extern "C" {
+
+rt_status rt_batch_destroy(rt_batch* b) {
+  if (!b) return RT_OK;
+  cudaSetDevice(b->dev);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  dfree(b->d_models);
+  dfree(b->d_chunks);
+  dfree(b->d_next);
+  delete b;
+  return RT_OK;
+}
+
+rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packages, uint64_t seed,
+                          const rt_run_opts* o, uint64_t chunk, rt_batch** out) {
+  if (!grids || !n_packages || !out || n < 1) return RT_ERR_ARG;
+  *out = nullptr;
+  if (chunk == 0) chunk = 4096;
+  if (o && (o->kernel != RT_KERNEL_POOL || o->blocks_per_sm < 0 || o->blocks_per_sm > 32 ||
+            o->refill_period < 0 || o->interaction_batch < 0 || o->interaction_batch > 32))
+    return RT_ERR_ARG;
+  rt_batch* b = new (std::nothrow) rt_batch();
+  if (!b) return RT_ERR_OOM;
+  if (cudaGetDevice(&b->dev) != cudaSuccess) {
+    delete b;
+    return RT_ERR_CUDA;
+  }
+  std::vector<ModelDesc> desc((size_t)n);
+  std::vector<std::vector<BatchChunk>> per((size_t)n);
+  rt_status st = RT_OK;
+  for (int m = 0; m < n && st == RT_OK; ++m) {
+    rt_grid* g = grids[m];
+    if (!g || g->dev != b->dev) { st = RT_ERR_ARG; break; }
+    if ((st = build_tables(g, nullptr)) != RT_OK) break;
+    if (n_packages[m] > g->n_total) { st = RT_ERR_RANGE; break; }
+    DevRun r;
+    if ((st = fill_run(g, n_packages[m], seed + (uint64_t)m, 0, o, &r)) != RT_OK) break;
+    const size_t nT = (size_t)g->desc.n_species * g->desc.n_leaves;
+    if (!g->d_Tscratch && (st = dalloc(&g->d_Tscratch, nT)) != RT_OK) break;
+    desc[(size_t)m].g = g->g;
+    desc[(size_t)m].t = g->tab;
+    desc[(size_t)m].t.u_frozen = g->d_ufrozen;
+    desc[(size_t)m].r = r;
+    b->grids.push_back(g);
+    b->n_pk.push_back(n_packages[m]);
+    for (unsigned long long f = 0; f < n_packages[m]; f += chunk) {
+      BatchChunk c{m, 0, f, n_packages[m] - f < chunk ? n_packages[m] - f : chunk};
+      per[(size_t)m].push_back(c);
+    }
+  }
+  if (st != RT_OK) {
+    rt_batch_destroy(b);
+    return st;
+  }
+  // interleave the models' chunks round-robin so every model is in flight early
+  std::vector<BatchChunk> chunks;
+  for (size_t k = 0;; ++k) {
+    bool any = false;
+    for (int m = 0; m < n; ++m)
+      if (k < per[(size_t)m].size()) {
+        chunks.push_back(per[(size_t)m][k]);
+        any = true;
+      }
+    if (!any) break;
+  }
+  b->n_chunks = (long long)chunks.size();
+  b->blocks_per_sm = o ? o->blocks_per_sm : 0;
+  if ((st = dalloc(&b->d_models, (size_t)n)) != RT_OK ||
+      (st = dalloc(&b->d_chunks, chunks.size())) != RT_OK ||
+      (st = dalloc(&b->d_next, 1)) != RT_OK) {
+    rt_batch_destroy(b);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(b->d_models, desc.data(), sizeof(ModelDesc) * n,
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !chunks.empty())
+    e = cudaMemcpy(b->d_chunks, chunks.data(), sizeof(BatchChunk) * chunks.size(),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    rt_batch_destroy(b);
+    return RT_ERR_CUDA;
+  }
+  *out = b;
+  return RT_OK;
+}
+
+rt_status rt_batch_run(rt_batch* b, int reset, int temperatures, void* stream) {
+  if (!b) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(b->dev));
+  if (reset)
+    for (rt_grid* g : b->grids) {
+      rt_status st = rt_reset(g, stream);
+      if (st != RT_OK) return st;
+    }
+  RT_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), s));
+  if (b->n_chunks > 0)
+    RT_CUDA(launch_transport_batch(b->d_models, b->d_chunks, b->n_chunks, b->d_next,
+                                   b->blocks_per_sm, s));
+  if (temperatures)
+    for (rt_grid* g : b->grids)
+      RT_CUDA(launch_temperatures(g->g, g->tab, g->d_count, g->d_Tscratch, g->d_counters, s));
+  return RT_OK;
+}
+
+rt_status rt_batch_run_graph(rt_batch* b, void* stream) {
+  if (!b) return RT_ERR_ARG;
+  RT_CUDA(cudaSetDevice(b->dev));
+  if (!b->exec) {
+    if (!b->capture_stream)
+      RT_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+    RT_CUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+    rt_status st = rt_batch_run(b, 1, 1, b->capture_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->capture_stream, &graph);
+    if (st != RT_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return RT_ERR_CUDA;
+    b->graph = graph;
+    RT_CUDA(cudaGraphInstantiate(&b->exec, graph, 0));
+  }
+  RT_CUDA(cudaGraphLaunch(b->exec, as_stream(stream)));
+  return RT_OK;
+}
+
+rt_status rt_batch_temperatures(rt_batch* b, int model, float* T_out, int mem, void* stream) {
+  if (!b || model < 0 || model >= (int)b->grids.size() || !T_out) return RT_ERR_ARG;
+  rt_grid* g = b->grids[(size_t)model];
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(b->dev));
+  const size_t n = (size_t)g->desc.n_species * g->desc.n_leaves;
+  RT_CUDA(cudaMemcpyAsync(T_out, g->d_Tscratch, sizeof(float) * n,
+                          mem == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                               : cudaMemcpyDeviceToHost,
+                          s));
+  if (mem != RT_MEM_DEVICE) return sync_status(g, s);
   return RT_OK;
 }
 

@@ -89,7 +89,23 @@ struct DevRun {
   unsigned long long budget_ns;
 };
 
+// One model of a batched launch, and one chunk of its packages.
+struct ModelDesc {
+  DevGrid g;
+  DevTables t;
+  DevRun r;
+};
+
+struct BatchChunk {
+  int model;
+  int pad;
+  unsigned long long first, count;  // package indices [first, first + count)
+};
+
 // Kernel launchers (rt_transport.cu, rt_tables.cu).
+cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* chunks,
+                                   long long n_chunks, unsigned long long* next_chunk,
+                                   int blocks_per_sm, cudaStream_t s);
 cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
                                   int blocks_per_sm, int threads, cudaStream_t s);
 cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const DevRun& r,
@@ -156,12 +172,26 @@ struct PahTables {
   double dE[kMaxPah];
   double mol_mass[kMaxPah];  // g per molecule
   int species[kMaxPah];      // species index of each PAH
+  int n_carbon[kMaxPah];     // C atoms of each PAH
 };
 
 cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream_t s);
 cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                              double eps, double d0, long long first, long long n,
-                             float* j_out, const unsigned char* want, cudaStream_t s);
+                             float* j_out, const unsigned char* want, int pah_only,
+                             cudaStream_t s);
+cudaError_t launch_pah_features(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
+                                double eps, double d0, int p, long long first, long long n,
+                                float* X, float* p_abs, cudaStream_t s);
+cudaError_t launch_pah_encode(const float* J, const float* p_abs, long long n, int B, float* Y,
+                              cudaStream_t s);
+cudaError_t launch_surrogate_check(const float* Y, const float* X, const float* p_abs,
+                                   long long n, int B, int F, float tol, float x_lo, float x_hi,
+                                   unsigned char* flag, cudaStream_t s);
+cudaError_t launch_surrogate_add(const float* Y, const float* p_abs, long long n, int B,
+                                 const unsigned char* flag, float* j_out, cudaStream_t s);
+cudaError_t launch_count_flags(const unsigned char* flag, long long n, unsigned long long* out,
+                               cudaStream_t s);
 
 cudaError_t launch_frozen_u(const DevGrid& g, const DevTables& t, const float* T_frozen,
                             float* u_frozen, float t_min, cudaStream_t s);

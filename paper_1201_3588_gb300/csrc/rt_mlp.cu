@@ -1,0 +1,568 @@
+// rt_mlp.cu -- the multilayer perceptron of the PAH emission surrogate: forward
+// pass, mean-squared-error gradients and Adam, on tensor cores in BF16 with FP32
+// accumulation (WMMA m16n16k16 tiles).
+//
+// Network: a_0 = x; z_l = a_{l-1} W_l^T + b_l; a_l = silu(z_l) for the hidden layers,
+// linear output. Loss = mean over rows and outputs of (y - t)^2. Master weights,
+// gradients and Adam moments are FP32; the GEMM operands are BF16 copies.
+// Internally every dimension is padded to a multiple of 16 (zero weights, zero
+// inputs); the exported parameter layout is the unpadded one: per layer W [out][in]
+// row-major, then b [out].
+
+#include "../../include/rt.h"
+#include "rt_internal.h"
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <mma.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace nvcuda;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int kTile = 64;     // block tile (M and N)
+constexpr int kMaxLayers = 8;
+
+inline int pad16(int x) { return (x + 15) / 16 * 16; }
+
+struct Layer {
+  int n_in, n_out;    // unpadded
+  int in_p, out_p;    // padded to 16
+  size_t w_off, b_off;  // offsets in the padded parameter arrays (floats)
+};
+
+}  // namespace
+
+struct rt_mlp {
+  int dev = 0;
+  int n_layers_total = 0;
+  Layer layer[kMaxLayers];
+  int n_in = 0, n_out = 0;
+  size_t n_padded = 0;     // padded parameter count
+  int64_t n_params = 0;    // unpadded
+  float* d_param = nullptr;  // padded FP32 master
+  float* d_grad = nullptr;
+  float* d_m = nullptr;
+  float* d_v = nullptr;
+  bf16* d_wbf = nullptr;     // padded BF16 weights
+  float* d_loss = nullptr;
+  long long step = 0;
+  float x_lo = -1e30f, x_hi = 1e30f;  // admissible range of the second-to-last input
+  // activations for up to cap rows (padded to 64)
+  long long cap = 0;
+  bf16* d_a[kMaxLayers + 1] = {};   // a_l in BF16 [cap][dim_p]
+  float* d_z[kMaxLayers] = {};      // z_l in FP32 [cap][out_p]
+  float* d_dz = nullptr;            // FP32 scratch [cap][max_p]
+  bf16* d_dzb = nullptr;            // BF16 of dz
+  int max_p = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- kernels
+// C[M][N] (=|+=) A[M][K] . B[K][N]; A row-major (lda) or column-major, B row-major
+// (ldb) or column-major; BF16 operands, FP32 accumulation. Block = 4 warps, tile
+// 64x64, each warp 32x32. gridDim.z splits K into chunks of k_chunk (atomics).
+template <bool kAcol, bool kBcol>
+__global__ void __launch_bounds__(128) k_gemm(const bf16* A, int lda, const bf16* B, int ldb,
+                                              float* C, int ldc, int M, int N, int K,
+                                              int k_chunk, int atomic_out) {
+  typedef typename std::conditional<kAcol, wmma::col_major, wmma::row_major>::type LA;
+  typedef typename std::conditional<kBcol, wmma::col_major, wmma::row_major>::type LB;
+  const int warp = threadIdx.x >> 5;
+  const int m0 = blockIdx.x * kTile + (warp >> 1) * 32;
+  const int n0 = blockIdx.y * kTile + (warp & 1) * 32;
+  const int k_begin = blockIdx.z * k_chunk;
+  const int k_end = min(K, k_begin + k_chunk);
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) wmma::fill_fragment(acc[i][j], 0.0f);
+  wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, LA> fa[2];
+  wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, LB> fb[2];
+  for (int k = k_begin; k < k_end; k += 16) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int m = m0 + 16 * i;
+      if (m < M) {
+        const bf16* pa = kAcol ? A + (size_t)k * lda + m : A + (size_t)m * lda + k;
+        wmma::load_matrix_sync(fa[i], pa, lda);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int n = n0 + 16 * j;
+      if (n < N) {
+        const bf16* pb = kBcol ? B + (size_t)n * ldb + k : B + (size_t)k * ldb + n;
+        wmma::load_matrix_sync(fb[j], pb, ldb);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (m0 + 16 * i < M && n0 + 16 * j < N) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+  }
+  if (!atomic_out) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (m0 + 16 * i < M && n0 + 16 * j < N)
+          wmma::store_matrix_sync(C + (size_t)(m0 + 16 * i) * ldc + n0 + 16 * j, acc[i][j], ldc,
+                                  wmma::mem_row_major);
+    return;
+  }
+  // split-K: add through shared memory staging
+  __shared__ float stage[4][16 * 16];
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      if (m0 + 16 * i >= M || n0 + 16 * j >= N) continue;
+      wmma::store_matrix_sync(stage[warp], acc[i][j], 16, wmma::mem_row_major);
+      __syncwarp();
+      for (int e = lane; e < 256; e += 32) {
+        int r = e >> 4, c = e & 15;
+        atomicAdd(&C[(size_t)(m0 + 16 * i + r) * ldc + n0 + 16 * j + c], stage[warp][e]);
+      }
+      __syncwarp();
+    }
+}
+
+// x [M][n_in] FP32 -> a0 [Mp][in_p] BF16, zero padding
+__global__ void k_pack_input(const float* x, long long M, int n_in, long long Mp, int in_p,
+                             bf16* a0) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= Mp * in_p) return;
+  long long r = idx / in_p;
+  int c = (int)(idx % in_p);
+  float v = (r < M && c < n_in) ? x[r * n_in + c] : 0.0f;
+  a0[idx] = __float2bfloat16(v);
+}
+
+// z += b; a = silu(z) (hidden) or copy (output); padded columns forced to zero
+__global__ void k_bias_act(float* z, const float* b, long long Mp, int out_p, int n_out,
+                           int hidden, bf16* a) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= Mp * out_p) return;
+  int c = (int)(idx % out_p);
+  float v = c < n_out ? z[idx] + b[c] : 0.0f;
+  z[idx] = v;
+  if (a) {
+    float y = hidden ? v / (1.0f + __expf(-v)) : v;
+    a[idx] = __float2bfloat16(y);
+  }
+}
+
+// dz = 2 (y - t) / (M n_out) on valid rows/columns; loss accumulated
+__global__ void k_mse_grad(const float* y, const float* t, long long M, int n_out, long long Mp,
+                           int out_p, float* dz, bf16* dzb, float* loss) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  float l = 0.0f;
+  if (idx < Mp * out_p) {
+    long long r = idx / out_p;
+    int c = (int)(idx % out_p);
+    float d = 0.0f;
+    if (r < M && c < n_out) {
+      float e = y[idx] - t[r * n_out + c];
+      l = e * e;
+      d = 2.0f * e / ((float)M * (float)n_out);
+    }
+    dz[idx] = d;
+    dzb[idx] = __float2bfloat16(d);
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss, l / ((float)M * (float)n_out));
+}
+
+// dz = da * silu'(z) (da in dz, in place) and its BF16 copy
+__global__ void k_act_back(float* dz, const float* z, long long Mp, int p, int n_valid, bf16* dzb) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= Mp * p) return;
+  int c = (int)(idx % p);
+  float v = 0.0f;
+  if (c < n_valid) {
+    float zz = z[idx];
+    float s = 1.0f / (1.0f + __expf(-zz));
+    v = dz[idx] * s * (1.0f + zz * (1.0f - s));
+  }
+  dz[idx] = v;
+  dzb[idx] = __float2bfloat16(v);
+}
+
+// db[c] += sum over rows of dz[r][c]
+__global__ void k_col_sums(const float* dz, long long Mp, int p, float* db) {
+  int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  int r0 = threadIdx.x >> 5;
+  float s = 0.0f;
+  if (c < p)
+    for (long long r = r0 + (long long)blockIdx.y * 8; r < Mp; r += 8ll * gridDim.y) s += dz[r * p + c];
+  __shared__ float red[8][32];
+  red[r0][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (r0 == 0 && c < p) {
+    float t = 0.0f;
+    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x & 31];
+    atomicAdd(&db[c], t);
+  }
+}
+
+__global__ void k_to_bf16(const float* p, bf16* q, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) q[i] = __float2bfloat16(p[i]);
+}
+
+__global__ void k_adam(float* p, const float* g, float* m, float* v, size_t n, float lr,
+                       float b1, float b2, float c1, float c2, float eps) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.0f - b1) * gi;
+  float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// y [M][n_out] <- z_last [Mp][out_p]
+__global__ void k_unpack_output(const float* z, long long M, int n_out, int out_p, float* y) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= M * n_out) return;
+  long long r = idx / n_out;
+  int c = (int)(idx % n_out);
+  y[idx] = z[r * out_p + c];
+}
+
+inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- host helpers
+template <bool Acol, bool Bcol>
+cudaError_t gemm(const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, long long M,
+                 int N, int K, bool split, cudaStream_t s) {
+  dim3 grid(nb(M, kTile), nb(N, kTile), 1);
+  int chunk = K;
+  if (split) {
+    // split the contraction so that the grid fills the GPU
+    long long tiles = (long long)grid.x * grid.y;
+    long long want = (152 * 8 + tiles - 1) / tiles;
+    long long ksteps = K / 16;
+    if (want > ksteps) want = ksteps;
+    if (want < 1) want = 1;
+    chunk = (int)(((ksteps + want - 1) / want) * 16);
+    grid.z = (unsigned)((K + chunk - 1) / chunk);
+  }
+  k_gemm<Acol, Bcol><<<grid, 128, 0, s>>>(A, lda, B, ldb, C, ldc, (int)M, N, K, chunk,
+                                          split ? 1 : 0);
+  return cudaGetLastError();
+}
+
+uint64_t splitmix(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+rt_status alloc(T** p, size_t n) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (n ? n : 1) * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return RT_ERR_OOM;
+  }
+  return e == cudaSuccess ? RT_OK : RT_ERR_CUDA;
+}
+
+template <typename T>
+void release(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_acts(rt_mlp* m) {
+  for (int l = 0; l <= kMaxLayers; ++l) release(m->d_a[l]);
+  for (int l = 0; l < kMaxLayers; ++l) release(m->d_z[l]);
+  release(m->d_dz);
+  release(m->d_dzb);
+  m->cap = 0;
+}
+
+rt_status ensure_rows(rt_mlp* m, long long Mp) {
+  if (Mp <= m->cap) return RT_OK;
+  free_acts(m);
+  rt_status st;
+  const int L = m->n_layers_total;
+  if ((st = alloc(&m->d_a[0], (size_t)Mp * m->layer[0].in_p)) != RT_OK) return st;
+  for (int l = 0; l < L; ++l) {
+    if ((st = alloc(&m->d_z[l], (size_t)Mp * m->layer[l].out_p)) != RT_OK) return st;
+    if ((st = alloc(&m->d_a[l + 1], (size_t)Mp * m->layer[l].out_p)) != RT_OK) return st;
+  }
+  if ((st = alloc(&m->d_dz, (size_t)Mp * m->max_p)) != RT_OK) return st;
+  if ((st = alloc(&m->d_dzb, (size_t)Mp * m->max_p)) != RT_OK) return st;
+  m->cap = Mp;
+  return RT_OK;
+}
+
+rt_status refresh_bf16(rt_mlp* m, cudaStream_t s) {
+  k_to_bf16<<<nb((long long)m->n_padded, 256), 256, 0, s>>>(m->d_param, m->d_wbf, m->n_padded);
+  return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ERR_CUDA;
+}
+
+// forward over Mp padded rows of d_a[0]
+rt_status forward_rows(rt_mlp* m, long long Mp, cudaStream_t s) {
+  const int L = m->n_layers_total;
+  for (int l = 0; l < L; ++l) {
+    const Layer& ly = m->layer[l];
+    if (gemm<false, true>(m->d_a[l], ly.in_p, m->d_wbf + ly.w_off, ly.in_p, m->d_z[l], ly.out_p,
+                          Mp, ly.out_p, ly.in_p, false, s) != cudaSuccess)
+      return RT_ERR_CUDA;
+    k_bias_act<<<nb(Mp * ly.out_p, 256), 256, 0, s>>>(m->d_z[l], m->d_param + ly.b_off, Mp,
+                                                      ly.out_p, ly.n_out, l < L - 1,
+                                                      m->d_a[l + 1]);
+    if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
+  }
+  return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_mlp_create(int n_in, int n_hidden, int n_layers, int n_out, uint64_t seed,
+                        rt_mlp** out) {
+  if (!out || n_in < 1 || n_hidden < 1 || n_layers < 1 || n_layers > kMaxLayers - 1 ||
+      n_out < 1 || n_in > 4096 || n_hidden > 4096 || n_out > 4096)
+    return RT_ERR_ARG;
+  *out = nullptr;
+  rt_mlp* m = new (std::nothrow) rt_mlp();
+  if (!m) return RT_ERR_OOM;
+  if (cudaGetDevice(&m->dev) != cudaSuccess) {
+    delete m;
+    return RT_ERR_CUDA;
+  }
+  m->n_in = n_in;
+  m->n_out = n_out;
+  m->n_layers_total = n_layers + 1;
+  size_t off = 0;
+  int64_t np = 0;
+  for (int l = 0; l <= n_layers; ++l) {
+    Layer& ly = m->layer[l];
+    ly.n_in = l == 0 ? n_in : n_hidden;
+    ly.n_out = l == n_layers ? n_out : n_hidden;
+    ly.in_p = pad16(ly.n_in);
+    ly.out_p = pad16(ly.n_out);
+    ly.w_off = off;
+    off += (size_t)ly.in_p * ly.out_p;
+    ly.b_off = off;
+    off += (size_t)ly.out_p;
+    np += (int64_t)ly.n_in * ly.n_out + ly.n_out;
+    if (ly.in_p > m->max_p) m->max_p = ly.in_p;
+    if (ly.out_p > m->max_p) m->max_p = ly.out_p;
+  }
+  // keep BF16 weight offsets 16-element aligned: offsets are sums of multiples of 16
+  m->n_padded = off;
+  m->n_params = np;
+  rt_status st;
+  if ((st = alloc(&m->d_param, off)) != RT_OK || (st = alloc(&m->d_grad, off)) != RT_OK ||
+      (st = alloc(&m->d_m, off)) != RT_OK || (st = alloc(&m->d_v, off)) != RT_OK ||
+      (st = alloc(&m->d_wbf, off)) != RT_OK || (st = alloc(&m->d_loss, 1)) != RT_OK) {
+    rt_mlp_destroy(m);
+    return st;
+  }
+  // He-uniform weights from a seeded splitmix64 stream, zero biases
+  std::vector<float> h(off, 0.0f);
+  uint64_t x = seed;
+  for (int l = 0; l <= n_layers; ++l) {
+    const Layer& ly = m->layer[l];
+    float lim = std::sqrt(6.0f / (float)ly.n_in);
+    for (int r = 0; r < ly.n_out; ++r)
+      for (int c = 0; c < ly.n_in; ++c) {
+        double u = (double)(splitmix(x) >> 11) * (1.0 / 9007199254740992.0);
+        h[ly.w_off + (size_t)r * ly.in_p + c] = (float)((2.0 * u - 1.0) * lim);
+      }
+  }
+  cudaError_t e = cudaMemcpy(m->d_param, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->d_m, 0, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMemset(m->d_v, 0, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMemset(m->d_grad, 0, sizeof(float) * off);
+  if (e != cudaSuccess || refresh_bf16(m, nullptr) != RT_OK) {
+    rt_mlp_destroy(m);
+    return RT_ERR_CUDA;
+  }
+  *out = m;
+  return RT_OK;
+}
+
+rt_status rt_mlp_destroy(rt_mlp* m) {
+  if (!m) return RT_OK;
+  cudaSetDevice(m->dev);
+  free_acts(m);
+  release(m->d_param);
+  release(m->d_grad);
+  release(m->d_m);
+  release(m->d_v);
+  release(m->d_wbf);
+  release(m->d_loss);
+  delete m;
+  return RT_OK;
+}
+
+rt_status rt_mlp_dims(const rt_mlp* m, int* n_in, int* n_out) {
+  if (!m || !n_in || !n_out) return RT_ERR_ARG;
+  *n_in = m->n_in;
+  *n_out = m->n_out;
+  return RT_OK;
+}
+
+rt_status rt_mlp_set_range(rt_mlp* m, float lo, float hi) {
+  if (!m || !(hi >= lo)) return RT_ERR_ARG;
+  m->x_lo = lo;
+  m->x_hi = hi;
+  return RT_OK;
+}
+
+rt_status rt_mlp_get_range(const rt_mlp* m, float* lo, float* hi) {
+  if (!m || !lo || !hi) return RT_ERR_ARG;
+  *lo = m->x_lo;
+  *hi = m->x_hi;
+  return RT_OK;
+}
+
+rt_status rt_mlp_n_params(const rt_mlp* m, int64_t* n) {
+  if (!m || !n) return RT_ERR_ARG;
+  *n = m->n_params;
+  return RT_OK;
+}
+
+static rt_status copy_params(rt_mlp* m, float* host, const float* src_dev) {
+  std::vector<float> h(m->n_padded);
+  if (cudaMemcpy(h.data(), src_dev, sizeof(float) * m->n_padded, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return RT_ERR_CUDA;
+  size_t o = 0;
+  for (int l = 0; l < m->n_layers_total; ++l) {
+    const Layer& ly = m->layer[l];
+    for (int r = 0; r < ly.n_out; ++r)
+      for (int c = 0; c < ly.n_in; ++c) host[o++] = h[ly.w_off + (size_t)r * ly.in_p + c];
+    for (int r = 0; r < ly.n_out; ++r) host[o++] = h[ly.b_off + r];
+  }
+  return RT_OK;
+}
+
+rt_status rt_mlp_get_params(rt_mlp* m, float* out) {
+  if (!m || !out) return RT_ERR_ARG;
+  if (cudaSetDevice(m->dev) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return RT_ERR_CUDA;
+  return copy_params(m, out, m->d_param);
+}
+
+rt_status rt_mlp_set_params(rt_mlp* m, const float* in) {
+  if (!m || !in) return RT_ERR_ARG;
+  std::vector<float> h(m->n_padded, 0.0f);
+  size_t o = 0;
+  for (int l = 0; l < m->n_layers_total; ++l) {
+    const Layer& ly = m->layer[l];
+    for (int r = 0; r < ly.n_out; ++r)
+      for (int c = 0; c < ly.n_in; ++c) h[ly.w_off + (size_t)r * ly.in_p + c] = in[o++];
+    for (int r = 0; r < ly.n_out; ++r) h[ly.b_off + r] = in[o++];
+  }
+  if (cudaSetDevice(m->dev) != cudaSuccess) return RT_ERR_CUDA;
+  if (cudaMemcpy(m->d_param, h.data(), sizeof(float) * m->n_padded, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return RT_ERR_CUDA;
+  return refresh_bf16(m, nullptr);
+}
+
+rt_status rt_mlp_forward(rt_mlp* m, const float* x, float* y, int64_t M, void* stream) {
+  if (!m || !x || !y || M < 0) return RT_ERR_ARG;
+  if (M == 0) return RT_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(m->dev) != cudaSuccess) return RT_ERR_CUDA;
+  const long long chunk = 1ll << 18;
+  for (long long r0 = 0; r0 < M; r0 += chunk) {
+    long long Mc = M - r0 < chunk ? M - r0 : chunk;
+    long long Mp = (Mc + kTile - 1) / kTile * kTile;
+    rt_status st = ensure_rows(m, Mp);
+    if (st != RT_OK) return st;
+    const Layer& l0 = m->layer[0];
+    k_pack_input<<<nb(Mp * l0.in_p, 256), 256, 0, s>>>(x + r0 * m->n_in, Mc, m->n_in, Mp,
+                                                       l0.in_p, m->d_a[0]);
+    if ((st = forward_rows(m, Mp, s)) != RT_OK) return st;
+    const Layer& ll = m->layer[m->n_layers_total - 1];
+    k_unpack_output<<<nb(Mc * m->n_out, 256), 256, 0, s>>>(m->d_z[m->n_layers_total - 1], Mc,
+                                                           m->n_out, ll.out_p,
+                                                           y + r0 * m->n_out);
+    if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
+  }
+  return RT_OK;
+}
+
+rt_status rt_mlp_loss_grad(rt_mlp* m, const float* x, const float* t, int64_t M, float* loss_out,
+                           float* grad_out, void* stream) {
+  if (!m || !x || !t || M < 1 || M > (1ll << 24)) return RT_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(m->dev) != cudaSuccess) return RT_ERR_CUDA;
+  const long long Mp = (M + kTile - 1) / kTile * kTile;
+  rt_status st = ensure_rows(m, Mp);
+  if (st != RT_OK) return st;
+  const int L = m->n_layers_total;
+  const Layer& l0 = m->layer[0];
+  if (cudaMemsetAsync(m->d_grad, 0, sizeof(float) * m->n_padded, s) != cudaSuccess ||
+      cudaMemsetAsync(m->d_loss, 0, sizeof(float), s) != cudaSuccess)
+    return RT_ERR_CUDA;
+  k_pack_input<<<nb(Mp * l0.in_p, 256), 256, 0, s>>>(x, M, m->n_in, Mp, l0.in_p, m->d_a[0]);
+  if ((st = forward_rows(m, Mp, s)) != RT_OK) return st;
+  const Layer& lo = m->layer[L - 1];
+  k_mse_grad<<<nb(Mp * lo.out_p, 256), 256, 0, s>>>(m->d_z[L - 1], t, M, m->n_out, Mp, lo.out_p,
+                                                    m->d_dz, m->d_dzb, m->d_loss);
+  for (int l = L - 1; l >= 0; --l) {
+    const Layer& ly = m->layer[l];
+    // dW_l = dz^T a_{l-1}: [out_p][in_p], contraction over rows (split)
+    if (gemm<true, false>(m->d_dzb, ly.out_p, m->d_a[l], ly.in_p, m->d_grad + ly.w_off, ly.in_p,
+                          ly.out_p, ly.in_p, (int)Mp, true, s) != cudaSuccess)
+      return RT_ERR_CUDA;
+    dim3 g2(nb(ly.out_p, 32), 64);
+    k_col_sums<<<g2, 256, 0, s>>>(m->d_dz, Mp, ly.out_p, m->d_grad + ly.b_off);
+    if (l > 0) {
+      // da_{l-1} = dz W_l: [Mp][in_p]; then through silu'
+      if (gemm<false, false>(m->d_dzb, ly.out_p, m->d_wbf + ly.w_off, ly.in_p, m->d_dz, ly.in_p,
+                             Mp, ly.in_p, ly.out_p, false, s) != cudaSuccess)
+        return RT_ERR_CUDA;
+      const Layer& lp = m->layer[l - 1];
+      k_act_back<<<nb(Mp * ly.in_p, 256), 256, 0, s>>>(m->d_dz, m->d_z[l - 1], Mp, ly.in_p,
+                                                       lp.n_out, m->d_dzb);
+    }
+    if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
+  }
+  if (loss_out &&
+      cudaMemcpyAsync(loss_out, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return RT_ERR_CUDA;
+  if (grad_out || loss_out) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RT_ERR_CUDA;
+  }
+  if (grad_out) return copy_params(m, grad_out, m->d_grad);
+  return RT_OK;
+}
+
+rt_status rt_mlp_adam_step(rt_mlp* m, float lr, void* stream) {
+  if (!m || !(lr > 0)) return RT_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(m->dev) != cudaSuccess) return RT_ERR_CUDA;
+  m->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  float c1 = 1.0f - std::pow(b1, (float)m->step), c2 = 1.0f - std::pow(b2, (float)m->step);
+  k_adam<<<nb((long long)m->n_padded, 256), 256, 0, s>>>(m->d_param, m->d_grad, m->d_m, m->d_v,
+                                                         m->n_padded, lr, b1, b2, c1, c2, 1e-8f);
+  if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
+  return refresh_bf16(m, s);
+}
+
+}  // extern "C"

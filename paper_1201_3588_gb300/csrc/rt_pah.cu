@@ -206,7 +206,7 @@ __global__ void k_pah_template(PahTables t, PahBuild pb) {
 // j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin).
 __global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, double eps,
                             double d0, long long first, long long n, float* j_out,
-                            const unsigned char* want) {
+                            const unsigned char* want, int pah_only) {
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_warp = t.K + 2 * t.M;
@@ -222,6 +222,7 @@ __global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, doub
   const int lev = g.level[cell];
   const double V = d0 * d0 * d0 / (double)(1ll << (3 * lev));
   for (int p = 0; p < t.n_pah; ++p) {
+    if (pah_only >= 0 && p != pah_only) continue;
     const unsigned* cnt = pahabs + ((size_t)p * g.n_leaves + cell) * t.K;
     const int s = t.species[p];
     const double rho = (double)g.rho[cell * g.S + s] / d0;
@@ -245,6 +246,93 @@ __global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, doub
   }
 }
 
+// Surrogate features of PAH p in cells [first, first + n): the shape of the absorbed
+// spectrum, x_k = ln(a_k + 1e-4)/4.6 + 1 with a_k the fraction of the absorbed
+// photons in coarse bin k; the absorbed power per molecule,
+// x_K = (log10(P_abs / N_mol) + 12) / 4; the size, x_K+1 = log10(N_C) - 2.
+// p_abs[c] = absorbed power of the cell's PAH p (erg/s), 0 without absorptions.
+__global__ void k_pah_features(DevGrid g, PahTables t, const unsigned* pahabs, double eps,
+                               double d0, int p, long long first, long long n, float* X,
+                               float* p_abs) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const long long cell = first + c;
+  const int F = t.K + 2;
+  const unsigned* cnt = pahabs + ((size_t)p * g.n_leaves + cell) * t.K;
+  float* x = X + (size_t)c * F;
+  double tot = 0.0;
+  for (int k = 0; k < t.K; ++k) tot += (double)cnt[k];
+  const int s = t.species[p];
+  const double rho = (double)g.rho[cell * g.S + s] / d0;
+  const int lev = g.level[cell];
+  const double V = d0 * d0 * d0 / (double)(1ll << (3 * lev));
+  const double n_mol = rho * V / t.mol_mass[p];
+  if (!(tot > 0.0) || !(n_mol > 0.0)) {
+    for (int k = 0; k < F; ++k) x[k] = 0.0f;
+    p_abs[c] = 0.0f;
+    return;
+  }
+  for (int k = 0; k < t.K; ++k) x[k] = (float)(log((double)cnt[k] / tot + 1e-4) / 4.6 + 1.0);
+  const double pw = tot * eps;
+  x[t.K] = (float)((log10(pw / n_mol) + 12.0) / 4.0);
+  x[t.K + 1] = (float)(log10(t.n_carbon[p]) - 2.0);
+  p_abs[c] = (float)pw;
+}
+
+// Training targets: y_b = ln(J_b / P_abs + 1e-6) / 7 + 1 from the exact emission (bins
+// below 1e-6 of the cell's power carry no energy worth learning).
+__global__ void k_pah_encode(const float* J, const float* p_abs, long long n, int B, float* Y) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= n * B) return;
+  long long c = idx / B;
+  float pa = p_abs[c];
+  Y[idx] = pa > 0.0f ? (float)(log((double)J[idx] / pa + 1e-6) / 7.0 + 1.0) : 0.0f;
+}
+
+// Decoded surrogate emission: q_b = max(exp(7 (y_b - 1)) - 1e-6, 0); the energy
+// residual |sum_b q_b - 1| (before renormalising) and an out-of-range guard on the
+// absorbed power flag a cell for the exact solution. One warp per cell.
+__global__ void k_surrogate_check(const float* Y, const float* X, const float* p_abs,
+                                  long long n, int B, int F, float tol, float x_lo, float x_hi,
+                                  unsigned char* flag) {
+  const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= n) return;
+  if (!(p_abs[c] > 0.0f)) return;
+  double sum = 0.0;
+  for (int b = lane; b < B; b += 32) sum += fmax(exp(7.0 * ((double)Y[c * B + b] - 1.0)) - 1e-6, 0.0);
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    const float xp = X[c * F + F - 2];
+    if (!(fabs(sum - 1.0) <= (double)tol) || xp < x_lo || xp > x_hi) flag[c] = 1;
+  }
+}
+
+// j_out[c] += P_abs q_b / sum q for cells not flagged. One warp per cell.
+__global__ void k_surrogate_add(const float* Y, const float* p_abs, long long n, int B,
+                                const unsigned char* flag, float* j_out) {
+  const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= n) return;
+  const float pa = p_abs[c];
+  if (!(pa > 0.0f) || (flag && flag[c])) return;
+  double sum = 0.0;
+  for (int b = lane; b < B; b += 32) sum += fmax(exp(7.0 * ((double)Y[c * B + b] - 1.0)) - 1e-6, 0.0);
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (!(sum > 0.0)) return;
+  for (int b = lane; b < B; b += 32) {
+    double q = fmax(exp(7.0 * ((double)Y[c * B + b] - 1.0)) - 1e-6, 0.0);
+    j_out[c * B + b] += (float)((double)pa * q / sum);
+  }
+}
+
+__global__ void k_count_flags(const unsigned char* flag, long long n, unsigned long long* out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool f = i < n && flag[i];
+  unsigned m = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(out, (unsigned long long)__popc(m));
+}
+
 }  // namespace
 
 cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream_t s) {
@@ -264,7 +352,8 @@ cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream
 
 cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                              double eps, double d0, long long first, long long n,
-                             float* j_out, const unsigned char* want, cudaStream_t s) {
+                             float* j_out, const unsigned char* want, int pah_only,
+                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int warps = 4;
   size_t smem = sizeof(double) * (size_t)warps * (t.K + 2 * t.M);
@@ -275,7 +364,51 @@ cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigne
   }
   long long blocks = (n + warps - 1) / warps;
   k_pah_exact<<<(unsigned)blocks, 32 * warps, smem, s>>>(g, t, pahabs, eps, d0, first, n,
-                                                        j_out, want);
+                                                        j_out, want, pah_only);
+  return cudaGetLastError();
+}
+
+}  // namespace rt
+
+namespace rt {
+
+cudaError_t launch_pah_features(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
+                                double eps, double d0, int p, long long first, long long n,
+                                float* X, float* p_abs, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_pah_features<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, t, pahabs, eps, d0, p, first, n,
+                                                              X, p_abs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pah_encode(const float* J, const float* p_abs, long long n, int B, float* Y,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long m = n * B;
+  k_pah_encode<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(J, p_abs, n, B, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_check(const float* Y, const float* X, const float* p_abs,
+                                   long long n, int B, int F, float tol, float x_lo, float x_hi,
+                                   unsigned char* flag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_surrogate_check<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(Y, X, p_abs, n, B, F, tol,
+                                                                       x_lo, x_hi, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_add(const float* Y, const float* p_abs, long long n, int B,
+                                 const unsigned char* flag, float* j_out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_surrogate_add<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(Y, p_abs, n, B, flag, j_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_flags(const unsigned char* flag, long long n, unsigned long long* out,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_count_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flag, n, out);
   return cudaGetLastError();
 }
 

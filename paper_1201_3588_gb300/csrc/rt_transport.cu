@@ -557,57 +557,60 @@ __global__ void __launch_bounds__(256) k_transport_plain(DevGrid g, DevTables t,
   flush_tally(tl, r.counters);
 }
 
-// ---------------------------------------------------------------- pool kernel
-// Persistent packet pool: each lane owns a package slot; dead lanes are refilled
-// from a global package counter every `refill_period` steps (one atomic per warp);
-// the opacity table, the stellar CDF and the escaped-spectrum histogram live in
-// shared memory. A lane that reaches its interaction point waits; the warp runs
-// the (long, divergent) interaction code only once `interaction_batch` lanes wait
-// or no lane is left walking, so both phases run with most lanes active. Each
-// package's history is unchanged by this schedule. Absorptions of lanes hitting
-// the same (species, cell) in one phase are merged into one atomic.
-template <int kMinBlocks>
-__global__ void __launch_bounds__(256, kMinBlocks)
-    k_transport_pool(DevGrid g, DevTables t, DevRun r) {
-  extern __shared__ unsigned long long smem_u64[];
-  const int S = g.S, B = g.B;
-  const int n_sed = 2 * g.n_dir * B;
-  // escaped-spectrum histogram in shared memory when it fits, else in global memory
-  const bool sed_local = r.sed_in_smem != 0;
-  unsigned long long* s_sed = sed_local ? smem_u64 : r.sed;   // [2][n_dir][B]
-  Kappa* s_kap = reinterpret_cast<Kappa*>(smem_u64 + (sed_local ? n_sed : 0));  // [B][S]
-  float* s_cdf = reinterpret_cast<float*>(s_kap + B * S);     // [B]
-  if (sed_local)
-    for (int i = threadIdx.x; i < n_sed; i += blockDim.x) s_sed[i] = 0ull;
-  for (int i = threadIdx.x; i < B * S; i += blockDim.x) s_kap[i] = t.kap[i];
-  for (int i = threadIdx.x; i < B; i += blockDim.x) s_cdf[i] = t.star_cdf[i];
-  __syncthreads();
+// ---------------------------------------------------------------- pool loop
+// Where a warp's package indices come from: one global counter shared by all warps
+// (one model), or a range owned by the warp (one chunk of a batch). take() returns
+// the first of nd consecutive indices to every lane of the warp.
+struct GlobalIds {
+  unsigned long long* next;
+  __device__ __forceinline__ unsigned long long take(int nd, int lane, int leader) {
+    unsigned long long b = 0;
+    if (lane == leader) b = atomicAdd(next, (unsigned long long)nd);
+    return __shfl_sync(kFull, b, leader);
+  }
+};
 
+struct RangeIds {
+  unsigned long long pos;
+  __device__ __forceinline__ unsigned long long take(int nd, int, int) {
+    unsigned long long b = pos;
+    pos += (unsigned long long)nd;
+    return b;
+  }
+};
+
+// One warp of the packet pool: each lane owns a package slot; dead lanes are refilled
+// with indices below n_end every `refill_period` steps. A lane that reaches its
+// interaction point waits; the warp runs the (long, divergent) interaction code only
+// once `interaction_batch` lanes wait or no lane is left walking, so both phases run
+// with most lanes active. Each package's history is unchanged by this schedule.
+// Absorptions of lanes hitting the same (species, cell) in one phase are merged into
+// one atomic. `sed` is the escaped-spectrum histogram (shared or global memory).
+template <class Ids>
+__device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, const DevRun& r,
+                                          const Kappa* kap, const float* star_cdf,
+                                          unsigned long long* sed, unsigned long long n_end,
+                                          Ids& ids, Tally& tl, unsigned long long t0) {
+  const int B = g.B;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  Tally tl = {};
   Pkg<float> k;
   k.id = 0;
   bool alive = false;
   bool pending = false;  // reached an interaction point, waiting for the batch
   Cell cell{0, 0, {0, 0, 0}};
-  bool stop = false;
-  const unsigned long long t0 = global_ns();
   const int K = r.refill_period > 0 ? r.refill_period : 8;
   const int batch = r.interaction_batch > 0 ? r.interaction_batch : 8;
 
-  while (!stop) {
+  for (;;) {
     unsigned dead = __ballot_sync(kFull, !alive);
     if (dead) {
-      int nd = __popc(dead);
-      int leader = __ffs(dead) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(r.next, (unsigned long long)nd);
-      base = __shfl_sync(kFull, base, leader);
+      const int nd = __popc(dead);
+      const unsigned long long base = ids.take(nd, lane, __ffs(dead) - 1);
       if (!alive) {
         unsigned long long j = base + __popc(dead & lt_mask);
-        if (j < r.n_packages) {
-          emit<float>(k, r.first_id + j, r, s_cdf, B);
+        if (j < n_end) {
+          emit<float>(k, r.first_id + j, r, star_cdf, B);
           ++tl.emitted;
           const int rc = enter(k, g, cell, tl.levels);
           if (rc == 0) {
@@ -615,8 +618,8 @@ __global__ void __launch_bounds__(256, kMinBlocks)
           } else if (rc == 1) {  // source outside the grid, moving away
             ++tl.escaped;
             const int db = dir_bin(k.d[2], g.n_dir);
-            atomicAdd(&s_sed[db * B + k.bin], 1ull);
-            atomicAdd(&s_sed[(g.n_dir + db) * B + k.bin], 1ull);
+            atomicAdd(&sed[db * B + k.bin], 1ull);
+            atomicAdd(&sed[(g.n_dir + db) * B + k.bin], 1ull);
           } else {
             ++tl.errors;
             atomicOr(r.status, kStatusTree);
@@ -627,6 +630,7 @@ __global__ void __launch_bounds__(256, kMinBlocks)
     if (!__any_sync(kFull, alive)) break;
     if (__any_sync(kFull, tl.crossings >= kTallyFlushAt || tl.levels >= kTallyFlushAt))
       flush_tally(tl, r.counters);
+    bool stop = false;
     if (lane == 0) stop = global_ns() - t0 > r.budget_ns;
     stop = __shfl_sync(kFull, stop, 0);
     if (stop) {
@@ -636,15 +640,15 @@ __global__ void __launch_bounds__(256, kMinBlocks)
     for (int step = 0; step < K; ++step) {
       // walk phase: lanes not waiting for an interaction cross one cell
       if (alive && !pending) {
-        const int a = advance_linked(k, cell, g, s_kap, tl.levels);
+        const int a = advance_linked(k, cell, g, kap, tl.levels);
         if (a == kCrossed) {
           ++tl.crossings;
         } else if (a == kEscaped) {
           ++tl.crossings;  // the boundary face it left through
           ++tl.escaped;
           int db = dir_bin(k.d[2], g.n_dir);
-          atomicAdd(&s_sed[db * B + k.bin], 1ull);
-          if (!k.touched) atomicAdd(&s_sed[(g.n_dir + db) * B + k.bin], 1ull);
+          atomicAdd(&sed[db * B + k.bin], 1ull);
+          if (!k.touched) atomicAdd(&sed[(g.n_dir + db) * B + k.bin], 1ull);
           alive = false;
         } else if (a == kError) {
           ++tl.errors;
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(256, kMinBlocks)
           ++tl.capped;
           alive = false;
         } else {
-          sp = interact<float>(k, g, s_kap, cell.leaf, r, w1);
+          sp = interact<float>(k, g, kap, cell.leaf, r, w1);
           if (sp < 0) ++tl.scatters; else absorbing = true;
         }
       }
@@ -691,11 +695,67 @@ __global__ void __launch_bounds__(256, kMinBlocks)
       }
     }
   }
+}
+
+// ---------------------------------------------------------------- pool kernel
+// Persistent packet pool over one model: all warps draw package indices from one
+// global counter; the opacity table, the stellar CDF and (when it fits) the
+// escaped-spectrum histogram live in shared memory.
+template <int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks)
+    k_transport_pool(DevGrid g, DevTables t, DevRun r) {
+  extern __shared__ unsigned long long smem_u64[];
+  const int S = g.S, B = g.B;
+  const int n_sed = 2 * g.n_dir * B;
+  const bool sed_local = r.sed_in_smem != 0;
+  unsigned long long* s_sed = sed_local ? smem_u64 : r.sed;   // [2][n_dir][B]
+  Kappa* s_kap = reinterpret_cast<Kappa*>(smem_u64 + (sed_local ? n_sed : 0));  // [B][S]
+  float* s_cdf = reinterpret_cast<float*>(s_kap + B * S);     // [B]
+  if (sed_local)
+    for (int i = threadIdx.x; i < n_sed; i += blockDim.x) s_sed[i] = 0ull;
+  for (int i = threadIdx.x; i < B * S; i += blockDim.x) s_kap[i] = t.kap[i];
+  for (int i = threadIdx.x; i < B; i += blockDim.x) s_cdf[i] = t.star_cdf[i];
+  __syncthreads();
+  Tally tl = {};
+  GlobalIds ids{r.next};
+  pool_warp(g, t, r, s_kap, s_cdf, s_sed, r.n_packages, ids, tl, global_ns());
   flush_tally(tl, r.counters);
   if (sed_local) {
     __syncthreads();
     for (int i = threadIdx.x; i < n_sed; i += blockDim.x)
       if (s_sed[i]) atomicAdd(&r.sed[i], s_sed[i]);
+  }
+}
+
+// ---------------------------------------------------------------- batch kernel
+// Many models in one persistent launch: warps take chunks (model, package range)
+// from a global queue, stage that model's descriptor in shared memory and run the
+// pool loop over the chunk (tables in global memory / L2, spectrum by global
+// atomics). Counters are flushed to the chunk's model when the chunk ends.
+__global__ void __launch_bounds__(256) k_transport_batch(const ModelDesc* models,
+                                                         const BatchChunk* chunks,
+                                                         long long n_chunks,
+                                                         unsigned long long* next_chunk) {
+  __shared__ ModelDesc sdesc[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(next_chunk, 1ull);
+    c = __shfl_sync(kFull, c, 0);
+    if ((long long)c >= n_chunks) break;
+    const BatchChunk ch = chunks[c];
+    const int* src = reinterpret_cast<const int*>(&models[ch.model]);
+    int* dst = reinterpret_cast<int*>(&sdesc[warp]);
+    for (int i = lane; i < (int)(sizeof(ModelDesc) / sizeof(int)); i += 32) dst[i] = src[i];
+    __syncwarp();
+    const ModelDesc& md = sdesc[warp];
+    Tally tl = {};
+    RangeIds ids{ch.first};
+    pool_warp(md.g, md.t, md.r, md.t.kap, md.t.star_cdf, md.r.sed, ch.first + ch.count, ids, tl,
+              t0);
+    flush_tally(tl, md.r.counters);
+    __syncwarp();
   }
 }
 
@@ -857,6 +917,23 @@ cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const D
     k_transport_plain<double><<<(unsigned)nb, threads, 0, s>>>(g, t, r);
   else
     k_transport_plain<float><<<(unsigned)nb, threads, 0, s>>>(g, t, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* chunks,
+                                   long long n_chunks, unsigned long long* next_chunk,
+                                   int blocks_per_sm, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_batch, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
+  k_transport_batch<<<sms * bps, 256, 0, s>>>(models, chunks, n_chunks, next_chunk);
   return cudaGetLastError();
 }
 

@@ -77,11 +77,31 @@ SIGNATURES = {
     "rt_trace": [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p],
     "rt_philox": [C.c_void_p, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p],
     "rt_status_string": [C.c_int],
+    "rt_batch_create": [C.c_void_p, C.c_int, C.c_void_p, C.c_uint64, C.POINTER(_Opts),
+                        C.c_uint64, C.POINTER(C.c_void_p)],
+    "rt_batch_destroy": [C.c_void_p],
+    "rt_batch_run": [C.c_void_p, C.c_int, C.c_int, C.c_void_p],
+    "rt_batch_run_graph": [C.c_void_p, C.c_void_p],
+    "rt_batch_temperatures": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_mlp_create": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_void_p)],
+    "rt_mlp_destroy": [C.c_void_p],
+    "rt_mlp_n_params": [C.c_void_p, C.POINTER(C.c_int64)],
+    "rt_mlp_get_params": [C.c_void_p, C.c_void_p],
+    "rt_mlp_set_params": [C.c_void_p, C.c_void_p],
+    "rt_mlp_forward": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
+    "rt_mlp_loss_grad": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                         C.c_void_p],
+    "rt_mlp_adam_step": [C.c_void_p, C.c_float, C.c_void_p],
     "rt_set_pah": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_int,
                    C.c_int, C.c_double],
     "rt_pah_absorbed": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
-    "rt_pah_emission": [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_float,
-                        C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "rt_pah_emission": [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_void_p,
+                        C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "rt_pah_training_pairs": [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p],
+    "rt_mlp_dims": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "rt_mlp_set_range": [C.c_void_p, C.c_float, C.c_float],
+    "rt_mlp_get_range": [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)],
     "rt_cell_temperatures_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_double,
                                      C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
@@ -253,17 +273,25 @@ class Grid:
         return out
 
     def pah_emission(self, first: int = 0, n: Optional[int] = None, mode: int = PAH_EXACT,
-                     surrogate=None, tol: float = 0.0, out=None, stream=None):
+                     surrogate=None, tol: float = 0.0, out=None, pah: int = -1, stream=None,
+                     count_fallback: bool = True):
         n = self.N - first if n is None else n
         if out is None:
             out = np.zeros((n, self.B), dtype=np.float32)
         p, mem = _ptr_mem(out)
         nf = C.c_uint64()
-        _check(load().rt_pah_emission(self._h, int(first), int(n), int(mode),
+        _check(load().rt_pah_emission(self._h, int(first), int(n), int(pah), int(mode),
                                       surrogate._h if surrogate is not None else None,
-                                      float(tol), p, mem, C.byref(nf), _stream(stream)),
-               "rt_pah_emission")
+                                      float(tol), p, mem,
+                                      C.byref(nf) if count_fallback else None,
+                                      _stream(stream)), "rt_pah_emission")
         return out, int(nf.value)
+
+    def pah_training_pairs(self, pah: int, X, Y, p_abs, first: int = 0, stream=None):
+        n = int(X.shape[0])
+        _check(load().rt_pah_training_pairs(self._h, int(pah), int(first), n, X.data_ptr(),
+                                            Y.data_ptr(), p_abs.data_ptr(), _stream(stream)),
+               "rt_pah_training_pairs")
 
     def counters(self) -> dict:
         c = _Counters()
@@ -286,6 +314,110 @@ def philox(ids, event: int, block: int, seed: int) -> np.ndarray:
     _check(load().rt_philox(idv.ctypes.data, idv.shape[0], event, block, int(seed),
                             out.ctypes.data), "rt_philox")
     return out
+
+
+class Batch:
+    """Handle to ``rt_batch``: many grids transported in one persistent launch."""
+
+    def __init__(self, grids, n_packages, seed: int = 0, mode: int = REEMIT_BW,
+                 max_events: int = 0, blocks_per_sm: int = 0, refill_period: int = 0,
+                 interaction_batch: int = 0, budget_s: float = 0.0, chunk: int = 0):
+        L = load()
+        self.grids = list(grids)
+        arr = (C.c_void_p * len(self.grids))(*[g._h.value for g in self.grids])
+        npk = np.ascontiguousarray(n_packages, dtype=np.uint64)
+        o = _Opts(mode=mode, kernel=KERNEL_POOL, max_events=max_events,
+                  blocks_per_sm=blocks_per_sm, threads=0, refill_period=refill_period,
+                  interaction_batch=interaction_batch, budget_s=budget_s)
+        h = C.c_void_p()
+        _check(L.rt_batch_create(C.cast(arr, C.c_void_p), len(self.grids), npk.ctypes.data,
+                                 int(seed), C.byref(o), int(chunk), C.byref(h)),
+               "rt_batch_create")
+        self._h = h
+
+    def run(self, reset: bool = True, temperatures: bool = True, stream=None):
+        _check(load().rt_batch_run(self._h, int(reset), int(temperatures), _stream(stream)),
+               "rt_batch_run")
+
+    def run_graph(self, stream=None):
+        _check(load().rt_batch_run_graph(self._h, _stream(stream)), "rt_batch_run_graph")
+
+    def temperatures(self, model: int, out=None, stream=None):
+        g = self.grids[model]
+        if out is None:
+            out = np.zeros((g.S, g.N), dtype=np.float32)
+        p, mem = _ptr_mem(out)
+        _check(load().rt_batch_temperatures(self._h, int(model), p, mem, _stream(stream)),
+               "rt_batch_temperatures")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """Handle to ``rt_mlp`` (the surrogate network)."""
+
+    def __init__(self, n_in: int, n_hidden: int = 256, n_layers: int = 3, n_out: int = 200,
+                 seed: int = 0):
+        L = load()
+        h = C.c_void_p()
+        _check(L.rt_mlp_create(n_in, n_hidden, n_layers, n_out, int(seed), C.byref(h)),
+               "rt_mlp_create")
+        self._h = h
+        self.n_in, self.n_hidden, self.n_layers, self.n_out = n_in, n_hidden, n_layers, n_out
+        n = C.c_int64()
+        _check(L.rt_mlp_n_params(h, C.byref(n)), "rt_mlp_n_params")
+        self.n_params = int(n.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rt_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().rt_mlp_get_params(self._h, out.ctypes.data), "rt_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(load().rt_mlp_set_params(self._h, p.ctypes.data), "rt_mlp_set_params")
+
+    def forward(self, x, y, stream=None):
+        _check(load().rt_mlp_forward(self._h, x.data_ptr(), y.data_ptr(), int(x.shape[0]),
+                                     _stream(stream)), "rt_mlp_forward")
+        return y
+
+    def loss_grad(self, x, t, want_loss: bool = True, want_grad: bool = False, stream=None):
+        loss = C.c_float()
+        g = np.zeros(self.n_params, dtype=np.float32) if want_grad else None
+        _check(load().rt_mlp_loss_grad(self._h, x.data_ptr(), t.data_ptr(), int(x.shape[0]),
+                                       C.byref(loss) if want_loss else None,
+                                       g.ctypes.data if want_grad else None, _stream(stream)),
+               "rt_mlp_loss_grad")
+        return (loss.value if want_loss else None), g
+
+    def set_range(self, lo: float, hi: float):
+        _check(load().rt_mlp_set_range(self._h, float(lo), float(hi)), "rt_mlp_set_range")
+
+    def adam_step(self, lr: float, stream=None):
+        _check(load().rt_mlp_adam_step(self._h, float(lr), _stream(stream)), "rt_mlp_adam_step")
 
 
 def cell_temperatures_noalloc(count, rho, volume, kabs, nu_edges, eps: float, T_out,

@@ -513,6 +513,27 @@ def disk_model(n_base: int = 128, max_level: int = 2, n_bins: int = 200,
                              perturbed=perturbed, fractions=list(map(float, fr))))
 
 
+PAH_MASS_FRACTION = 0.05   # of the dust mass, split equally between the two PAH sizes
+
+
+def disk_pah_model(n_base: int = 128, max_level: int = 2, n_bins: int = 200,
+                   tau_v_mid: float = 1.0e3, perturbed: bool = True,
+                   pah_sizes: Sequence[int] = (30, 200)) -> Model:
+    """The disk with the planet's gap and spiral and four species: silicate, amorphous
+    carbon and two PAH sizes (30 and 200 C atoms) carrying PAH_MASS_FRACTION of the
+    dust mass."""
+    nu = frequency_edges(n_bins)
+    sp = two_species(nu) + [pah_species(nu, n) for n in pah_sizes]
+    fr = list(MASS_FRACTION * (1.0 - PAH_MASS_FRACTION)) + \
+        [PAH_MASS_FRACTION / len(pah_sizes)] * len(pah_sizes)
+    m = disk_model(n_base=n_base, max_level=max_level, n_bins=n_bins, tau_v_mid=tau_v_mid,
+                   perturbed=perturbed, species=sp, fractions=fr)
+    m.name = "disk_pah"
+    m.recipe["pah_mass_fraction"] = PAH_MASS_FRACTION
+    m.recipe["pah_sizes"] = list(pah_sizes)
+    return m
+
+
 def uniform_box_model(n_base: int, n_bins: int, tau_half: float, species: List[Species],
                       half_size_cm: float = AU, star: Optional[Star] = None,
                       max_level: int = 0, refine=None, n_sed_dirs: int = 1) -> Model:
@@ -533,6 +554,53 @@ def explicit_model(tree: Tree, rho: np.ndarray, n_bins: int, species: List[Speci
     rho = np.asarray(rho, dtype=np.float64).reshape(len(species), tree.n_leaves)
     return Model(name, half_size_cm, tree, rho, frequency_edges(n_bins), list(species),
                  star if star is not None else Star(), n_sed_dirs)
+
+
+def sphere_refine_fn(n_base: int, frac: float = 0.25):
+    """Refine nodes reaching within frac * half-size of the centre (the star)."""
+    c = n_base / 2.0
+    r0 = frac * c
+
+    def refine(level, lo, hi):
+        near = np.clip(c, lo, hi)
+        return np.sqrt(((near - c) ** 2).sum(axis=1)) < r0
+
+    return refine
+
+
+def batch_models(n_models: int = 256, seed: int = 0, n_bins: int = 100, sizes=None):
+    """The uneven batch: models from random_model_list, each a sphere (radius = half
+    size 1e3 AU, refined near the star) or a flared disk, with its optical depth and
+    package count. Trees and unscaled densities are shared between models of the same
+    kind and shape (optical depth only rescales the density)."""
+    specs = random_model_list(n_models, seed, n_bins)
+    if sizes is not None:
+        for sp in specs:
+            sp["n_base"] = sizes[sp["index"] % len(sizes)]
+    cache = {}
+    out = []
+    for sp in specs:
+        key = (sp["kind"], sp["n_base"], sp["max_level"])
+        if key not in cache:
+            if sp["kind"] == "disk":
+                base = disk_model(n_base=sp["n_base"], max_level=sp["max_level"], n_bins=n_bins,
+                                  tau_v_mid=1.0)
+            else:
+                H = 1.0e3 * AU
+                nu = frequency_edges(n_bins)
+                spc = two_species(nu)
+                tree = build_tree(sp["n_base"], sp["max_level"], sphere_refine_fn(sp["n_base"]))
+                lo, hi = leaf_bounds_cm(tree, H)
+                inside = np.sqrt((((lo + hi) / 2) ** 2).sum(axis=1)) <= H
+                rho = _split_species(inside.astype(np.float64), MASS_FRACTION)
+                rho = normalise_tau(rho, tree, spc, H, 1.0)
+                base = Model("sphere", H, tree, rho, nu, spc, Star(), 1,
+                             recipe=dict(n_base=sp["n_base"], max_level=sp["max_level"]))
+            cache[key] = base
+        b = cache[key]
+        m = dataclasses.replace(b, rho=b.rho * sp["tau_v"], recipe=dict(b.recipe, **sp))
+        out.append((m, sp["n_packages"]))
+    return out
 
 
 def random_model_list(n_models: int = 256, seed: int = 0, n_bins: int = 100):
