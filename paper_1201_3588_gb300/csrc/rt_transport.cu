@@ -237,7 +237,8 @@ __device__ __forceinline__ void emit(Pkg<R>& k, unsigned long long id, const Dev
   set_inverse(k);
 }
 
-// One cell: cross it, or move to the interaction point inside it.
+// One cell: cross it, or move to the interaction point inside it (the leaf is found
+// from the base cube each time: the plain walk).
 template <typename R>
 __device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa* kap,
                                        int& leaf, int& level) {
@@ -245,22 +246,25 @@ __device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa*
   int rc = locate(g, k.p, k.d, leaf, level, I);
   if (rc == 1) return kEscaped;
   if (rc < 0) return kError;
-  R sz = (R)1 / (R)(1 << level);
-  R lo[3], hi[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    lo[a] = (R)I[a] * sz;
-    hi[a] = lo[a] + sz;
-  }
-  R tex = (R)INFINITY;
-  int ax = 0;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R t;
-    if (k.d[a] > (R)0) t = (hi[a] - k.p[a]) * k.inv[a];
-    else if (k.d[a] < (R)0) t = (lo[a] - k.p[a]) * k.inv[a];
-    else continue;
-    if (t < tex) { tex = t; ax = a; }
+  const R sz = (R)1 / (R)(1 << level);
+  const R lo0 = (R)I[0] * sz, lo1 = (R)I[1] * sz, lo2 = (R)I[2] * sz;
+  const R hi0 = lo0 + sz, hi1 = lo1 + sz, hi2 = lo2 + sz;
+  const R d0 = k.d[0], d1 = k.d[1], d2 = k.d[2];
+  const R inf = (R)INFINITY;
+  const R t0 = d0 > (R)0 ? (hi0 - k.p[0]) * k.inv[0] : (d0 < (R)0 ? (lo0 - k.p[0]) * k.inv[0] : inf);
+  const R t1 = d1 > (R)0 ? (hi1 - k.p[1]) * k.inv[1] : (d1 < (R)0 ? (lo1 - k.p[1]) * k.inv[1] : inf);
+  const R t2 = d2 > (R)0 ? (hi2 - k.p[2]) * k.inv[2] : (d2 < (R)0 ? (lo2 - k.p[2]) * k.inv[2] : inf);
+  int ax;
+  R tex;
+  if (t0 <= t1 && t0 <= t2) {
+    ax = 0;
+    tex = t0;
+  } else if (t1 <= t2) {
+    ax = 1;
+    tex = t1;
+  } else {
+    ax = 2;
+    tex = t2;
   }
   tex = fmax(tex, (R)0);
   // extinction per base-cube unit of path: sum_s (rho_s d0) kappa_ext,s(bin)
@@ -268,17 +272,19 @@ __device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa*
   const Kappa* kb = kap + k.bin * g.S;
   R kx = (R)0;
   for (int s = 0; s < g.S; ++s) kx += (R)__ldg(&rho[s]) * (R)kb[s].kext;
-  R dtau = kx * tex;
+  const R dtau = kx * tex;
   if (kx > (R)0 && dtau > k.tau) {
-    R sd = k.tau / kx;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) k.p[a] = fmin(hi[a], fmax(lo[a], k.p[a] + sd * k.d[a]));
+    const R sd = k.tau / kx;
+    k.p[0] = fmin(hi0, fmax(lo0, k.p[0] + sd * d0));
+    k.p[1] = fmin(hi1, fmax(lo1, k.p[1] + sd * d1));
+    k.p[2] = fmin(hi2, fmax(lo2, k.p[2] + sd * d2));
     return kInteract;
   }
   k.tau -= dtau;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) k.p[a] = fmin(hi[a], fmax(lo[a], k.p[a] + tex * k.d[a]));
-  k.p[ax] = k.d[ax] > (R)0 ? hi[ax] : lo[ax];
+  const R f0 = d0 > (R)0 ? hi0 : lo0, f1 = d1 > (R)0 ? hi1 : lo1, f2 = d2 > (R)0 ? hi2 : lo2;
+  k.p[0] = ax == 0 ? f0 : fmin(hi0, fmax(lo0, k.p[0] + tex * d0));
+  k.p[1] = ax == 1 ? f1 : fmin(hi1, fmax(lo1, k.p[1] + tex * d1));
+  k.p[2] = ax == 2 ? f2 : fmin(hi2, fmax(lo2, k.p[2] + tex * d2));
   return kCrossed;
 }
 
@@ -304,25 +310,33 @@ __device__ __forceinline__ int enter(const Pkg<float>& k, const DevGrid& g, Cell
 __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevGrid& g,
                                               const Kappa* kap,
                                               unsigned& child_reads) {
+  // every array below is indexed with constants only, so it stays in registers
   const float sz = __int_as_float((127 - c.level) << 23);  // 2^-level
-  float lo[3], hi[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    lo[a] = (float)c.I[a] * sz;
-    hi[a] = lo[a] + sz;
-  }
-  float tex = INFINITY;
-  int ax = 0;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float t;
-    if (k.d[a] > 0.f) t = (hi[a] - k.p[a]) * k.inv[a];
-    else if (k.d[a] < 0.f) t = (lo[a] - k.p[a]) * k.inv[a];
-    else continue;
-    if (t < tex) { tex = t; ax = a; }
+  const float lo0 = (float)c.I[0] * sz, lo1 = (float)c.I[1] * sz, lo2 = (float)c.I[2] * sz;
+  const float hi0 = lo0 + sz, hi1 = lo1 + sz, hi2 = lo2 + sz;
+  const float d0 = k.d[0], d1 = k.d[1], d2 = k.d[2];
+  const float t0 = d0 > 0.f ? (hi0 - k.p[0]) * k.inv[0]
+                            : (d0 < 0.f ? (lo0 - k.p[0]) * k.inv[0] : INFINITY);
+  const float t1 = d1 > 0.f ? (hi1 - k.p[1]) * k.inv[1]
+                            : (d1 < 0.f ? (lo1 - k.p[1]) * k.inv[1] : INFINITY);
+  const float t2 = d2 > 0.f ? (hi2 - k.p[2]) * k.inv[2]
+                            : (d2 < 0.f ? (lo2 - k.p[2]) * k.inv[2] : INFINITY);
+  // exit axis: the nearest face, the lowest axis on ties
+  int ax;
+  float tex;
+  if (t0 <= t1 && t0 <= t2) {
+    ax = 0;
+    tex = t0;
+  } else if (t1 <= t2) {
+    ax = 1;
+    tex = t1;
+  } else {
+    ax = 2;
+    tex = t2;
   }
   tex = fmaxf(tex, 0.f);
-  const bool up = k.d[ax] > 0.f;
+  const float dax = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
+  const bool up = dax > 0.f;
   const int* rec = g.links + (size_t)c.leaf * 8;
   const int link = __ldg(rec + 2 * ax + (up ? 1 : 0));
   const Kappa* kb = kap + k.bin * g.S;
@@ -338,24 +352,29 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
   const float dtau = kx * tex;
   if (kx > 0.f && dtau > k.tau) {
     const float sd = k.tau / kx;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) k.p[a] = fminf(hi[a], fmaxf(lo[a], k.p[a] + sd * k.d[a]));
+    k.p[0] = fminf(hi0, fmaxf(lo0, k.p[0] + sd * d0));
+    k.p[1] = fminf(hi1, fmaxf(lo1, k.p[1] + sd * d1));
+    k.p[2] = fminf(hi2, fmaxf(lo2, k.p[2] + sd * d2));
     return kInteract;
   }
   k.tau -= dtau;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) k.p[a] = fminf(hi[a], fmaxf(lo[a], k.p[a] + tex * k.d[a]));
-  k.p[ax] = up ? hi[ax] : lo[ax];
+  const float f0 = d0 > 0.f ? hi0 : lo0, f1 = d1 > 0.f ? hi1 : lo1, f2 = d2 > 0.f ? hi2 : lo2;
+  k.p[0] = ax == 0 ? f0 : fminf(hi0, fmaxf(lo0, k.p[0] + tex * d0));
+  k.p[1] = ax == 1 ? f1 : fminf(hi1, fmaxf(lo1, k.p[1] + tex * d1));
+  k.p[2] = ax == 2 ? f2 : fminf(hi2, fmaxf(lo2, k.p[2] + tex * d2));
   if (link == kLinkEscape) return kEscaped;
-  int J[3] = {c.I[0], c.I[1], c.I[2]};
-  J[ax] += up ? 1 : -1;
+  const int step = up ? 1 : -1;
+  int J0 = c.I[0] + (ax == 0 ? step : 0);
+  int J1 = c.I[1] + (ax == 1 ? step : 0);
+  int J2 = c.I[2] + (ax == 2 ? step : 0);
   if (link >= 0) {
     const int nl = link >> 28;
     const int sh = c.level - nl;
     c.leaf = link & kLinkLeafMask;
     c.level = nl;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) c.I[a] = J[a] >> sh;
+    c.I[0] = J0 >> sh;
+    c.I[1] = J1 >> sh;
+    c.I[2] = J2 >> sh;
     return kCrossed;
   }
   // the same-size neighbour is split: descend, staying inside that node
@@ -366,21 +385,21 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
     ++lev;
     ++child_reads;
     const float sc = (float)(1 << lev);
-    int oct = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int j = cell_index(k.p[a] * sc, k.d[a]);
-      j = min(max(j, 2 * J[a]), 2 * J[a] + 1);
-      oct |= (j - 2 * J[a]) << a;
-      J[a] = j;
-    }
+    const int j0 = min(max(cell_index(k.p[0] * sc, d0), 2 * J0), 2 * J0 + 1);
+    const int j1 = min(max(cell_index(k.p[1] * sc, d1), 2 * J1), 2 * J1 + 1);
+    const int j2 = min(max(cell_index(k.p[2] * sc, d2), 2 * J2), 2 * J2 + 1);
+    const int oct = (j0 - 2 * J0) | ((j1 - 2 * J1) << 1) | ((j2 - 2 * J2) << 2);
+    J0 = j0;
+    J1 = j1;
+    J2 = j2;
     const int node = __ldg(&g.child[blk * 8 + oct]);
     if (node >= 0) {
       if ((long long)node >= g.n_leaves) return kError;
       c.leaf = node;
       c.level = lev;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) c.I[a] = J[a];
+      c.I[0] = J0;
+      c.I[1] = J1;
+      c.I[2] = J2;
       return kCrossed;
     }
     blk = -(long long)node - 1;
@@ -396,21 +415,21 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
   w1 = draw(r.seed, k.id, k.event, 1u);
   const float* rho = g.rho + (size_t)leaf * g.S;
   const Kappa* kb = kap + k.bin * g.S;
-  float rs[kMaxSpecies];
   float ksca = 0.f, kext = 0.f, kabs = 0.f;
   for (int s = 0; s < g.S; ++s) {
-    rs[s] = __ldg(&rho[s]);
-    ksca += rs[s] * kb[s].ksca;
-    kext += rs[s] * kb[s].kext;
-    kabs += rs[s] * kb[s].kabs;
+    const float rs = __ldg(&rho[s]);
+    ksca += rs * kb[s].ksca;
+    kext += rs * kb[s].kext;
+    kabs += rs * kb[s].kabs;
   }
   k.touched = true;
-  float xs = unit<float>(w0.y);
+  const float xs = unit<float>(w0.y);
   int sp = g.S - 1;
   if (unit<float>(w0.x) * kext < ksca) {
-    float target = xs * ksca, cum = 0.f;
+    const float target = xs * ksca;
+    float cum = 0.f;
     for (int s = 0; s < g.S; ++s) {
-      cum += rs[s] * kb[s].ksca;
+      cum += __ldg(&rho[s]) * kb[s].ksca;
       if (cum > target) { sp = s; break; }
     }
     R mu = hg_mu<R>((R)kb[sp].g, unit<R>(w0.z));
@@ -419,9 +438,10 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
     k.tau = -log_(unit<R>(w1.x));
     return -1;
   }
-  float target = xs * kabs, cum = 0.f;
+  const float target = xs * kabs;
+  float cum = 0.f;
   for (int s = 0; s < g.S; ++s) {
-    cum += rs[s] * kb[s].kabs;
+    cum += __ldg(&rho[s]) * kb[s].kabs;
     if (cum > target) { sp = s; break; }
   }
   isotropic<R>(unit<R>(w0.z), unit<R>(w0.w), k.d);
@@ -599,7 +619,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
   bool alive = false;
   bool pending = false;  // reached an interaction point, waiting for the batch
   Cell cell{0, 0, {0, 0, 0}};
-  const int K = r.refill_period > 0 ? r.refill_period : 8;
+  const int K = r.refill_period > 0 ? r.refill_period : 16;
   const int batch = r.interaction_batch > 0 ? r.interaction_batch : 8;
 
   for (;;) {
