@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--packages", type=float, default=1e8, help="packages per GPU per step")
-    p.add_argument("--workload", choices=["disk", "sphere", "batch"], default="disk")
+    p.add_argument("--workload", choices=["disk", "sphere", "batch", "disk_pah"],
+                   default="disk")
     p.add_argument("--batch-models", type=int, default=256)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--plain-packages", type=float, default=1e7)
@@ -61,6 +62,11 @@ def build_model(name):
     from paper_1201_3588_gb300 import workloads as w
     if name == "sphere":
         return w.sphere_model(), "dust sphere 16^3, 64 bins, 2 species, tau_V=1"
+    if name == "disk_pah":
+        return (w.disk_pah_model(),
+                "flared disk with gap and spiral, 128^3 base + 2 levels, 200 bins, silicate, "
+                "carbon, PAH 30 C and 200 C; PAH emission by the BF16 surrogate with exact "
+                "fallback (tol 0.05)")
     return (w.disk_model(),
             "flared disk 128^3 base + 2 levels of 2x2x2 refinement, 200 bins, 2 species, "
             "midplane tau_V=1e3, r 0.1-100 AU")
@@ -187,7 +193,8 @@ def run_reference(args):
 # valid only for the kernel source it was measured on.
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": None, "dram_bytes_per_package": None}
+           "sha256": "cd28932466e0c31b116bb145ba4b838fc9382aaf6c4a03c14b1f21c0438741e7",
+           "dram_bytes_per_package": 1072.3}
 
 
 def traffic_per_launch(n_packages):
@@ -232,6 +239,37 @@ def run_ours(args):
     sed_dev = torch.empty((2, model.n_sed_dirs, B), dtype=torch.int64, device=dev)
     cnt_dev = torch.empty((S, N), dtype=torch.int64, device=dev) if world > 1 else None
     first = rank * n
+    pah = args.workload == "disk_pah"
+    net, pah_info = None, {}
+    pah_chunk = 1 << 20
+    j_dev = torch.empty((min(pah_chunk, N), B), dtype=torch.float32, device=dev) if pah else None
+
+    def pah_emission(mode=rt.PAH_AUTO, count=False):
+        nf = 0
+        for c0 in range(0, N, pah_chunk):
+            nc = min(pah_chunk, N - c0)
+            _, f = g.pah_emission(first=c0, n=nc, mode=mode, surrogate=net, tol=0.05,
+                                  out=j_dev[:nc], stream=stream, count_fallback=count)
+            nf += f
+        return nf
+
+    if pah:  # train the surrogate on the exact solutions of a first (untimed) pass
+        from paper_1201_3588_gb300 import surrogate
+        g.transport(n, seed=999, first_id=first, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, Y = surrogate.training_pairs(g)
+        keep = torch.randperm(X.shape[0], device=dev)[:1_000_000]
+        X, Y = X[keep].contiguous(), Y[keep].contiguous()
+        net = rt.MLP(X.shape[1], surrogate.N_HIDDEN, surrogate.N_LAYERS, B, seed=0)
+        hist = surrogate.train(net, X, Y, epochs=8)
+        xp = X[:, -2]
+        net.set_range(float(xp.min()) - 0.25, float(xp.max()) + 0.25)
+        torch.cuda.synchronize()
+        pah_info = {"training_pairs": int(X.shape[0]), "train_s": time.perf_counter() - t0,
+                    "train_loss_first_last": [hist[0], hist[-1]]}
+        del X, Y
+        g.reset(stream)
 
     def step(k, ev=None):
         g.reset(stream)
@@ -247,6 +285,8 @@ def run_ours(args):
             g.set_counts(cnt_dev, stream=stream)
         g.temperatures(out=T_dev, stream=stream)
         g.sed(out=sed_dev, stream=stream)
+        if pah:
+            pah_emission()
 
     for k in range(args.warmup):
         step(k)
@@ -289,9 +329,26 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": bytes_launch}
 
     extra = {}
+    if pah:
+        torch.cuda.synchronize()
+        pah_info["fallback_cells_last_step"] = pah_emission(count=True)
+        pah_info["pah_cells"] = int((torch.from_numpy(g.pah_absorbed().sum(axis=(0, 2)).astype("int64")) > 0).sum())
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pah_emission(mode=rt.PAH_EXACT)
+        e.record(stream)
+        torch.cuda.synchronize()
+        pah_info["exact_pah_ms"] = a.elapsed_time(e)
+        a.record(stream)
+        pah_emission()
+        e.record(stream)
+        torch.cuda.synchronize()
+        pah_info["surrogate_auto_pah_ms"] = a.elapsed_time(e)
+        extra["pah"] = pah_info
     if rank == 0 and not args.no_plain:
         extra["plain"] = plain_rates(g, model, int(args.plain_packages), stream, c, n)
-    e2e = e2e_rate(model, n, world, first, args.e2e_steps) if args.e2e_steps > 0 else None
+    e2e = e2e_rate(model, n, world, first, args.e2e_steps) if args.e2e_steps > 0 and not pah \
+        else None
     if rank == 0:
         cpu_rate, cpu_n, cpu_s = cpu_oracle_rate(model, n * world, args.cpu_seconds)
         line = {
@@ -309,7 +366,7 @@ def run_ours(args):
                              "sample": f"first {cpu_n} packages of the same workload "
                                        f"(BW mode, one thread, {cpu_s:.1f} s)"},
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (2 + (pah_launches(N, pah_chunk) if pah else 0)) * args.steps,
             "clocks": clocks,
             "per_step": {"crossings": c["crossings"], "absorptions": c["absorptions"],
                          "scatters": c["scatters"], "capped": c["capped"],
@@ -321,6 +378,15 @@ def run_ours(args):
     g.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def pah_launches(N, chunk):
+    """Kernels of one surrogate pass over N cells: per chunk and PAH, features,
+    network (per layer GEMM + bias/activation, plus input packing and output
+    unpacking), check and add; the exact fallback; the fallback count."""
+    chunks = (N + chunk - 1) // chunk
+    per_pah = 1 + (2 + 4 * 2) + 1 + 1
+    return chunks * (2 * per_pah + 2)
 
 
 def plain_rates(g, model, n_prefix, stream, c_pool, n_full):
