@@ -380,13 +380,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def pah_launches(N, chunk):
-    """Kernels of one surrogate pass over N cells: per chunk and PAH, features,
-    network (per layer GEMM + bias/activation, plus input packing and output
-    unpacking), check and add; the exact fallback; the fallback count."""
+def pah_launches(N, chunk, n_pah=2):
+    """Kernels of one surrogate pass over N cells, per chunk: the compaction of
+    PAH-active cells; per PAH features, network (input packing, a GEMM and a
+    bias/activation kernel per layer, output unpacking) and check; per PAH the add;
+    the compaction of failed cells and their exact solution."""
     chunks = (N + chunk - 1) // chunk
-    per_pah = 1 + (2 + 4 * 2) + 1 + 1
-    return chunks * (2 * per_pah + 2)
+    per_pah = 1 + (1 + 4 * 2 + 1) + 1 + 1
+    return chunks * (n_pah * per_pah + 3)
 
 
 def plain_rates(g, model, n_prefix, stream, c_pool, n_full):

@@ -95,7 +95,15 @@ typedef struct rt_run_opts {
     int32_t interaction_batch; /* pool: lanes of a warp waiting at an interaction
                                point that start an interaction phase, 1..32; 0: 8 */
     double budget_s;        /* device time budget per launch in s; 0: 120 */
+    int32_t estimators;     /* RT_EST_* bits: extra tallies kept during the launch */
+    int32_t reserved;
 } rt_run_opts;
+
+/* Lucy (1999) path-length estimator: every cell segment a package crosses adds
+ * rho_s kappa_abs,s(bin) * length (an absorption optical depth) to its cell and
+ * species; eps times that sum is the cell's absorbed power, with far less variance
+ * than the absorption counts in optically thin cells. */
+enum { RT_EST_PATHLENGTH = 1 };
 
 typedef struct rt_counters {
     uint64_t emitted, escaped, capped, absorptions, scatters, crossings, errors;
@@ -146,6 +154,13 @@ rt_status rt_reset(rt_grid *g, void *stream);
  * n eps = rho V 4 pi sum_b kappa_abs(b) P_b(T), inverted in FP64. Cells without
  * absorptions (or without the species) get 0. */
 rt_status rt_cell_temperatures(rt_grid *g, float *T_out, int mem, void *stream);
+
+/* Temperatures [n_species][n_leaves] from the path-length tallies instead of the
+ * counts: eps * sum = M S(T) (launches with RT_EST_PATHLENGTH since the last reset). */
+rt_status rt_cell_temperatures_pathlength(rt_grid *g, float *T_out, int mem, void *stream);
+
+/* The raw path-length tallies [n_species][n_leaves] (absorption optical depth). */
+rt_status rt_pathlength(rt_grid *g, float *out, int mem, void *stream);
 
 /* Escaped packages per direction and frequency bin, [2][n_sed_dirs][n_bins]:
  * index 0 counts all escaped packages, index 1 those that never interacted.

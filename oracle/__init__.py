@@ -63,7 +63,7 @@ class _Run(C.Structure):
 
 class _Tally(C.Structure):
     _fields_ = [("count", C.c_void_p), ("sed", C.c_void_p), ("pahabs", C.c_void_p),
-                ("emitted", C.c_uint64),
+                ("pathabs", C.c_void_p), ("emitted", C.c_uint64),
                 ("escaped", C.c_uint64), ("capped", C.c_uint64),
                 ("absorptions", C.c_uint64), ("scatters", C.c_uint64),
                 ("crossings", C.c_uint64), ("errors", C.c_uint64)]
@@ -258,6 +258,7 @@ class Tally:
     count: np.ndarray     # uint64 [S][N]
     sed: np.ndarray       # uint64 [2][n_dir][B]
     pahabs: np.ndarray    # uint64 [n_pah][N][n_coarse]
+    pathabs: np.ndarray   # float64 [S][N] path-length sums (absorption optical depth)
     emitted: int = 0
     escaped: int = 0
     capped: int = 0
@@ -271,7 +272,8 @@ def new_tally(model) -> Tally:
     om = as_oracle(model)
     return Tally(np.zeros((om.S, om.N), dtype=np.uint64),
                  np.zeros((2, om.model.n_sed_dirs, om.B), dtype=np.uint64),
-                 np.zeros((max(om.n_pah, 1), om.N, om.n_coarse), dtype=np.uint64))
+                 np.zeros((max(om.n_pah, 1), om.N, om.n_coarse), dtype=np.uint64),
+                 np.zeros((om.S, om.N), dtype=np.float64))
 
 
 def _run(n_packages, seed, first_id, n_total, mode, max_events, t_min, T_frozen):
@@ -295,6 +297,7 @@ def transport(model, n_packages: int, seed: int = 0, first_id: int = 0,
     r, keep = _run(n_packages, seed, first_id, n_total or n_packages, mode, max_events,
                    t_min, T_frozen)
     ct = _Tally(count=_ptr(tl.count), sed=_ptr(tl.sed), pahabs=_ptr(tl.pahabs),
+                pathabs=_ptr(tl.pathabs),
                 emitted=tl.emitted,
                 escaped=tl.escaped, capped=tl.capped, absorptions=tl.absorptions,
                 scatters=tl.scatters, crossings=tl.crossings, errors=tl.errors)

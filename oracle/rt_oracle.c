@@ -530,6 +530,14 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
         for (int s = 0; s < S; ++s) k += m->rho[(size_t)s * N + leaf] * c->kext[s * B + bin];
         k *= c->d0;
         double dtau = k * tex;
+        if (t && t->pathabs) {
+            /* Lucy (1999): the absorbed energy of a cell is eps times the sum, over
+             * the segments crossing it, of rho kappa_abs times the segment length */
+            double seg = (k > 0.0 && dtau > tau) ? tau / k : tex;
+            for (int s = 0; s < S; ++s)
+                t->pathabs[(size_t)s * N + leaf] +=
+                    m->rho[(size_t)s * N + leaf] * m->kabs[s * B + bin] * seg * c->d0;
+        }
         if (k > 0.0 && dtau > tau) {
             double sdist = tau / k;
             for (int a = 0; a < 3; ++a) p[a] += sdist * d[a];

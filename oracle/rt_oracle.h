@@ -61,6 +61,7 @@ typedef struct {
     uint64_t *count;           /* [S][N] absorption counts, accumulated */
     uint64_t *sed;             /* [2][n_dir][B]: all escaped / escaped uncollided */
     uint64_t *pahabs;          /* [n_pah][N][n_coarse] PAH absorptions, or NULL */
+    double *pathabs;           /* [S][N] Lucy path-length sums of rho kappa_abs l, or NULL */
     uint64_t emitted, escaped, capped, absorptions, scatters, crossings, errors;
 } orc_tally;
 

@@ -42,6 +42,7 @@ def tune(grid: "rt.Grid", tau_v: float, n_probe: int = 2_000_000, cache: Optiona
     if key in db and not force:
         return db[key]["opts"]
     s = torch.cuda.current_stream()
+    n_probe = min(n_probe, getattr(grid, "n_total", n_probe))
     grid.transport(min(n_probe, 100_000), seed=1)      # warm
     best = None
     for bps, ib, rp in itertools.product(*CANDIDATES.values()):

@@ -7,10 +7,13 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
+#include <thread>
 #include <vector>
 
 using namespace rt;
@@ -58,6 +61,7 @@ struct rt_grid {
   double* d_pah_wk = nullptr;
   float* d_pah_cdf = nullptr;
   unsigned* d_pahabs = nullptr;
+  float* d_pathabs = nullptr;  // path-length tallies [S][N]
   float* d_jscratch = nullptr;
   size_t jscratch_n = 0;
   // surrogate scratch (cells per chunk)
@@ -67,6 +71,9 @@ struct rt_grid {
   float* d_spabs = nullptr;    // [n_pah][chunk]
   unsigned char* d_sflag = nullptr;
   unsigned long long* d_scount = nullptr;
+  int* d_list = nullptr;       // [chunk] PAH-active cells of a chunk
+  int* d_list2 = nullptr;      // [chunk] cells sent to the exact solution
+  unsigned* d_ucount = nullptr;  // [2]
   // host state
   std::vector<double> nu, kabs, ksca, ghg;   // [S][B]
   std::vector<char> dust_set;
@@ -158,57 +165,115 @@ void free_all(rt_grid* g) {
   dfree(g->d_ufrozen);
   dfree(g->d_Tscratch);
   dfree(g->d_pahabs);
+  dfree(g->d_pathabs);
   dfree(g->d_jscratch);
   dfree(g->d_sx);
   dfree(g->d_sy);
   dfree(g->d_spabs);
   dfree(g->d_sflag);
   dfree(g->d_scount);
+  dfree(g->d_list);
+  dfree(g->d_list2);
+  dfree(g->d_ucount);
 }
 
 // Walk the tree from every base cube: every leaf id must appear exactly once,
 // every block be referenced exactly once, and no path exceed max_level. Records
-// each leaf's level and integer corner (at its level).
+// each leaf's level and integer corner (at its level). Base cubes are split over
+// host threads; claim flags (atomic) catch a leaf or block reached twice.
 rt_status check_tree(const rt_grid_desc* d, std::vector<int8_t>& level,
                      std::vector<int32_t>& ijk, int* max_seen) {
   const long long n = d->n_base;
   const long long nb = n * n * n;
   level.assign((size_t)d->n_leaves, (int8_t)-1);
   ijk.assign((size_t)d->n_leaves * 3, 0);
-  std::vector<char> seen_blk((size_t)d->n_blocks, 0);
-  struct Item { int32_t node; int lev; int32_t i, j, k; };
-  std::vector<Item> stk;
-  stk.reserve(64);
-  *max_seen = 0;
-  for (long long b = 0; b < nb; ++b) {
-    stk.clear();
-    stk.push_back({d->base[b], 0, (int32_t)(b % n), (int32_t)((b / n) % n), (int32_t)(b / (n * n))});
-    while (!stk.empty()) {
-      Item it = stk.back();
-      stk.pop_back();
-      if (it.lev > d->max_level) return RT_ERR_ARG;
-      if (it.node >= 0) {
-        if ((long long)it.node >= d->n_leaves || level[(size_t)it.node] >= 0) return RT_ERR_ARG;
-        level[(size_t)it.node] = (int8_t)it.lev;
-        ijk[(size_t)it.node * 3 + 0] = it.i;
-        ijk[(size_t)it.node * 3 + 1] = it.j;
-        ijk[(size_t)it.node * 3 + 2] = it.k;
-        if (it.lev > *max_seen) *max_seen = it.lev;
-      } else {
-        long long blk = -(long long)it.node - 1;
-        if (blk >= d->n_blocks || seen_blk[(size_t)blk]) return RT_ERR_ARG;
-        seen_blk[(size_t)blk] = 1;
-        for (int o = 0; o < 8; ++o)
-          stk.push_back({d->child[blk * 8 + o], it.lev + 1, 2 * it.i + (o & 1),
-                         2 * it.j + ((o >> 1) & 1), 2 * it.k + ((o >> 2) & 1)});
+  std::unique_ptr<std::atomic<unsigned char>[]> leaf_seen(
+      new (std::nothrow) std::atomic<unsigned char>[(size_t)d->n_leaves]);
+  std::unique_ptr<std::atomic<unsigned char>[]> blk_seen(
+      new (std::nothrow) std::atomic<unsigned char>[(size_t)(d->n_blocks > 0 ? d->n_blocks : 1)]);
+  if (!leaf_seen || !blk_seen) return RT_ERR_OOM;
+  for (long long i = 0; i < d->n_leaves; ++i) leaf_seen[(size_t)i].store(0, std::memory_order_relaxed);
+  for (long long i = 0; i < d->n_blocks; ++i) blk_seen[(size_t)i].store(0, std::memory_order_relaxed);
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  if (nb < 4096) nt = 1;
+  std::vector<rt_status> res(nt, RT_OK);
+  std::vector<int> mx(nt, 0);
+  auto work = [&](unsigned tid) {
+    struct Item { int32_t node; int lev; int32_t i, j, k; };
+    std::vector<Item> stk;
+    stk.reserve(64);
+    const long long b0 = nb * tid / nt, b1 = nb * (tid + 1) / nt;
+    for (long long b = b0; b < b1; ++b) {
+      stk.clear();
+      stk.push_back({d->base[b], 0, (int32_t)(b % n), (int32_t)((b / n) % n),
+                     (int32_t)(b / (n * n))});
+      while (!stk.empty()) {
+        Item it = stk.back();
+        stk.pop_back();
+        if (it.lev > d->max_level) { res[tid] = RT_ERR_ARG; return; }
+        if (it.node >= 0) {
+          if ((long long)it.node >= d->n_leaves ||
+              leaf_seen[(size_t)it.node].exchange(1, std::memory_order_relaxed)) {
+            res[tid] = RT_ERR_ARG;
+            return;
+          }
+          level[(size_t)it.node] = (int8_t)it.lev;
+          ijk[(size_t)it.node * 3 + 0] = it.i;
+          ijk[(size_t)it.node * 3 + 1] = it.j;
+          ijk[(size_t)it.node * 3 + 2] = it.k;
+          if (it.lev > mx[tid]) mx[tid] = it.lev;
+        } else {
+          long long blk = -(long long)it.node - 1;
+          if (blk >= d->n_blocks || blk_seen[(size_t)blk].exchange(1, std::memory_order_relaxed)) {
+            res[tid] = RT_ERR_ARG;
+            return;
+          }
+          for (int o = 0; o < 8; ++o)
+            stk.push_back({d->child[blk * 8 + o], it.lev + 1, 2 * it.i + (o & 1),
+                           2 * it.j + ((o >> 1) & 1), 2 * it.k + ((o >> 2) & 1)});
+        }
       }
     }
+  };
+  if (nt == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
+  *max_seen = 0;
+  for (unsigned t = 0; t < nt; ++t) {
+    if (res[t] != RT_OK) return res[t];
+    if (mx[t] > *max_seen) *max_seen = mx[t];
   }
   for (long long i = 0; i < d->n_leaves; ++i)
     if (level[(size_t)i] < 0) return RT_ERR_ARG;
   for (long long b = 0; b < d->n_blocks; ++b)
-    if (!seen_blk[(size_t)b]) return RT_ERR_ARG;
+    if (!blk_seen[(size_t)b].load(std::memory_order_relaxed)) return RT_ERR_ARG;
   return RT_OK;
+}
+
+// out[i] = f(i) for i in [0, n), split over host threads
+template <typename F>
+void parallel_for(long long n, F f) {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  if (n < (1 << 16)) nt = 1;
+  if (nt == 1) {
+    for (long long i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&, t]() {
+      const long long a = n * t / nt, b = n * (t + 1) / nt;
+      for (long long i = a; i < b; ++i) f(i);
+    });
+  for (auto& x : th) x.join();
 }
 
 rt_status sync_status(rt_grid* g, cudaStream_t s) {
@@ -443,8 +508,14 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
         (b > 0 && !(d->nu_edges[b] > d->nu_edges[b - 1])))
       return RT_ERR_ARG;
   const long long S = d->n_species, N = d->n_leaves;
-  for (long long i = 0; i < S * N; ++i)
-    if (!(d->rho[i] >= 0) || !std::isfinite(d->rho[i])) return RT_ERR_ARG;
+  {
+    std::atomic<int> bad(0);
+    const double* r = d->rho;
+    parallel_for(S * N, [&bad, r](long long i) {
+      if (!(r[i] >= 0) || !std::isfinite(r[i])) bad.store(1, std::memory_order_relaxed);
+    });
+    if (bad.load()) return RT_ERR_ARG;
+  }
 
   rt_grid* g = new (std::nothrow) rt_grid();
   if (!g) return RT_ERR_OOM;
@@ -491,9 +562,15 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   }
   // densities to [N][S] floats times the base-cube edge
   std::vector<float> rho((size_t)S * N);
-  for (long long c = 0; c < N; ++c)
-    for (long long s = 0; s < S; ++s)
-      rho[(size_t)(c * S + s)] = (float)(d->rho[(size_t)(s * N + c)] * g->d0);
+  {
+    const double d0 = g->d0;
+    const double* src = d->rho;
+    float* dstp = rho.data();
+    parallel_for(N, [=](long long c) {
+      for (long long s = 0; s < S; ++s)
+        dstp[(size_t)(c * S + s)] = (float)(src[(size_t)(s * N + c)] * d0);
+    });
+  }
   const long long nb = (long long)d->n_base * d->n_base * d->n_base;
   const int B = d->n_bins;
 #define ALLOC(p, n) if ((st = dalloc(&(p), (n))) != RT_OK) { free_all(g); delete g; return st; }
@@ -655,6 +732,18 @@ rt_status rt_reset(rt_grid* g, void* stream) {
   if (g->d_pahabs)
     RT_CUDA(cudaMemsetAsync(g->d_pahabs, 0,
                             sizeof(unsigned) * g->n_pah * N * g->tab.n_coarse, s));
+  if (g->d_pathabs) RT_CUDA(cudaMemsetAsync(g->d_pathabs, 0, sizeof(float) * S * N, s));
+  return RT_OK;
+}
+
+// The path-length tallies are allocated (and zeroed) the first time a launch asks
+// for them.
+static rt_status ensure_pathabs(rt_grid* g, const rt_run_opts* o, cudaStream_t s) {
+  if (!o || !(o->estimators & RT_EST_PATHLENGTH) || g->d_pathabs) return RT_OK;
+  const size_t n = (size_t)g->desc.n_species * g->desc.n_leaves;
+  rt_status st = dalloc(&g->d_pathabs, n);
+  if (st != RT_OK) return st;
+  RT_CUDA(cudaMemsetAsync(g->d_pathabs, 0, sizeof(float) * n, s));
   return RT_OK;
 }
 
@@ -675,6 +764,7 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
   r->counters = g->d_counters;
   r->status = g->d_status;
   r->pahabs = g->d_pahabs;
+  r->pathabs = (o && (o->estimators & RT_EST_PATHLENGTH)) ? g->d_pathabs : nullptr;
   for (int a = 0; a < 3; ++a) {
     double p = (g->pos[a] + g->desc.half_size_cm) / g->d0;
     r->src64[a] = p;
@@ -698,12 +788,14 @@ rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
   int threads = (o && o->threads > 0) ? o->threads : 256;
   if (kernel < 0 || kernel > 2 || threads % 32 != 0 || threads > 256) return RT_ERR_ARG;
   if (o && (o->blocks_per_sm < 0 || o->blocks_per_sm > 32 || o->refill_period < 0 ||
-            o->interaction_batch < 0 || o->interaction_batch > 32))
+            o->interaction_batch < 0 || o->interaction_batch > 32 ||
+            (o->estimators & ~RT_EST_PATHLENGTH)))
     return RT_ERR_ARG;
   cudaStream_t s = as_stream(stream);
   RT_CUDA(cudaSetDevice(g->dev));
   rt_status st = build_tables(g, s);
   if (st != RT_OK) return st;
+  if ((st = ensure_pathabs(g, o, s)) != RT_OK) return st;
   if (first_package_id > g->n_total || n_packages > g->n_total - first_package_id)
     return RT_ERR_RANGE;
   if (n_packages == 0) return RT_OK;
@@ -737,6 +829,41 @@ rt_status rt_cell_temperatures(rt_grid* g, float* T_out, int mem, void* stream) 
     RT_CUDA(cudaMemcpyAsync(T_out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
     return sync_status(g, s);
   }
+  return RT_OK;
+}
+
+rt_status rt_cell_temperatures_pathlength(rt_grid* g, float* T_out, int mem, void* stream) {
+  if (!g || !T_out) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  if (!g->d_pathabs) return RT_ERR_STATE;
+  const size_t n = (size_t)g->desc.n_species * g->desc.n_leaves;
+  float* dst = T_out;
+  if (mem != RT_MEM_DEVICE) {
+    if (!g->d_Tscratch && (st = dalloc(&g->d_Tscratch, n)) != RT_OK) return st;
+    dst = g->d_Tscratch;
+  }
+  RT_CUDA(launch_temperatures(g->g, g->tab, g->d_count, dst, g->d_counters, s, g->d_pathabs));
+  if (mem != RT_MEM_DEVICE) {
+    RT_CUDA(cudaMemcpyAsync(T_out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    return sync_status(g, s);
+  }
+  return RT_OK;
+}
+
+rt_status rt_pathlength(rt_grid* g, float* out, int mem, void* stream) {
+  if (!g || !out) return RT_ERR_ARG;
+  if (!g->d_pathabs) return RT_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  const size_t n = (size_t)g->desc.n_species * g->desc.n_leaves;
+  RT_CUDA(cudaMemcpyAsync(out, g->d_pathabs, sizeof(float) * n,
+                          mem == RT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                               : cudaMemcpyDeviceToHost,
+                          s));
+  if (mem != RT_MEM_DEVICE) return sync_status(g, s);
   return RT_OK;
 }
 
@@ -877,21 +1004,31 @@ rt_status rt_pah_absorbed(rt_grid* g, uint32_t* out, int mem, void* stream) {
   return RT_OK;
 }
 
-static rt_status surrogate_scratch(rt_grid* g, long long chunk) {
-  if (chunk <= g->sur_cap) return RT_OK;
-  dfree(g->d_sx);
-  dfree(g->d_sy);
-  dfree(g->d_spabs);
-  dfree(g->d_sflag);
-  g->sur_cap = 0;
+// Work arrays of rt_pah_emission for `chunk` cells: cell lists always, the
+// network's inputs and outputs only when a surrogate is used.
+static rt_status surrogate_scratch(rt_grid* g, long long chunk, bool with_net) {
   const int K = g->tab.n_coarse, B = g->desc.n_bins, P = g->n_pah;
   rt_status st;
-  if ((st = dalloc(&g->d_sx, (size_t)chunk * (K + 2))) != RT_OK) return st;
-  if ((st = dalloc(&g->d_sy, (size_t)P * chunk * B)) != RT_OK) return st;
-  if ((st = dalloc(&g->d_spabs, (size_t)P * chunk)) != RT_OK) return st;
-  if ((st = dalloc(&g->d_sflag, (size_t)chunk)) != RT_OK) return st;
+  if (chunk > g->sur_cap) {
+    dfree(g->d_sx);
+    dfree(g->d_sy);
+    dfree(g->d_spabs);
+    dfree(g->d_sflag);
+    dfree(g->d_list);
+    dfree(g->d_list2);
+    g->sur_cap = 0;
+    if ((st = dalloc(&g->d_sflag, (size_t)chunk)) != RT_OK) return st;
+    if ((st = dalloc(&g->d_list, (size_t)chunk)) != RT_OK) return st;
+    if ((st = dalloc(&g->d_list2, (size_t)chunk)) != RT_OK) return st;
+    g->sur_cap = chunk;
+  }
+  if (with_net && !g->d_sx) {
+    if ((st = dalloc(&g->d_sx, (size_t)g->sur_cap * (K + 2))) != RT_OK) return st;
+    if ((st = dalloc(&g->d_sy, (size_t)P * g->sur_cap * B)) != RT_OK) return st;
+    if ((st = dalloc(&g->d_spabs, (size_t)P * g->sur_cap)) != RT_OK) return st;
+  }
   if (!g->d_scount && (st = dalloc(&g->d_scount, 1)) != RT_OK) return st;
-  g->sur_cap = chunk;
+  if (!g->d_ucount && (st = dalloc(&g->d_ucount, 2)) != RT_OK) return st;
   return RT_OK;
 }
 
@@ -934,48 +1071,58 @@ rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int p
   const size_t n = (size_t)n_cells * B;
   float* dst = output_buffer(g, j_out, mem, n, &st);
   if (st != RT_OK) return st;
-  if (mode == RT_PAH_EXACT) {
-    RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, n_cells, dst,
-                             nullptr, pah, s));
-  } else {
-    rt_mlp* m = const_cast<rt_mlp*>(surrogate);
-    float x_lo = -1e30f, x_hi = 1e30f;
-    rt_mlp_get_range(m, &x_lo, &x_hi);
-    const long long chunk = n_cells < (1ll << 18) ? n_cells : (1ll << 18);
-    if ((st = surrogate_scratch(g, chunk)) != RT_OK) return st;
-    RT_CUDA(cudaMemsetAsync(g->d_scount, 0, sizeof(unsigned long long), s));
-    const float t = mode == RT_PAH_AUTO ? tol : 1e30f;
-    for (long long c0 = 0; c0 < n_cells; c0 += chunk) {
-      const long long nc = n_cells - c0 < chunk ? n_cells - c0 : chunk;
-      float* out = dst + (size_t)c0 * B;
-      RT_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * nc * B, s));
-      RT_CUDA(cudaMemsetAsync(g->d_sflag, 0, (size_t)nc, s));
-      for (int p = 0; p < g->n_pah; ++p) {
-        if (pah >= 0 && p != pah) continue;
-        float* Y = g->d_sy + (size_t)p * chunk * B;
-        float* pa = g->d_spabs + (size_t)p * chunk;
-        RT_CUDA(launch_pah_features(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, p,
-                                    first_cell + c0, nc, g->d_sx, pa, s));
-        if ((st = rt_mlp_forward(m, g->d_sx, Y, nc, s)) != RT_OK) return st;
-        RT_CUDA(launch_surrogate_check(Y, g->d_sx, pa, nc, B, F, t, x_lo, x_hi, g->d_sflag, s));
-      }
-      for (int p = 0; p < g->n_pah; ++p) {
-        if (pah >= 0 && p != pah) continue;
-        RT_CUDA(launch_surrogate_add(g->d_sy + (size_t)p * chunk * B, g->d_spabs + (size_t)p * chunk,
-                                     nc, B, mode == RT_PAH_AUTO ? g->d_sflag : nullptr, out, s));
-      }
-      if (mode == RT_PAH_AUTO)
-        RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell + c0, nc,
-                                 out, g->d_sflag, pah, s));
-      RT_CUDA(launch_count_flags(g->d_sflag, nc, g->d_scount, s));
+  rt_mlp* m = const_cast<rt_mlp*>(surrogate);
+  float x_lo = -1e30f, x_hi = 1e30f;
+  if (m) rt_mlp_get_range(m, &x_lo, &x_hi);
+  const long long chunk = n_cells < (1ll << 20) ? n_cells : (1ll << 20);
+  if ((st = surrogate_scratch(g, chunk, mode != RT_PAH_EXACT)) != RT_OK) return st;
+  const float t = mode == RT_PAH_AUTO ? tol : 1e30f;
+  unsigned long long n_fallback = 0;
+  for (long long c0 = 0; c0 < n_cells; c0 += chunk) {
+    const long long nc = n_cells - c0 < chunk ? n_cells - c0 : chunk;
+    float* out = dst + (size_t)c0 * B;
+    RT_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * nc * B, s));
+    // the cells of this chunk where a PAH absorbed anything
+    RT_CUDA(cudaMemsetAsync(g->d_ucount, 0, 2 * sizeof(unsigned), s));
+    RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell + c0, nc,
+                           nullptr, nullptr, g->d_list, g->d_ucount, s));
+    unsigned na = 0;
+    RT_CUDA(cudaMemcpyAsync(&na, g->d_ucount, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    if (na == 0) continue;
+    if (mode == RT_PAH_EXACT) {
+      RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell + c0, na,
+                               out, nullptr, pah, s, g->d_list));
+      continue;
     }
-    if (n_fallback_out) {
-      unsigned long long nf = 0;
-      RT_CUDA(cudaMemcpyAsync(&nf, g->d_scount, sizeof(nf), cudaMemcpyDeviceToHost, s));
-      RT_CUDA(cudaStreamSynchronize(s));
-      *n_fallback_out = nf;
+    RT_CUDA(cudaMemsetAsync(g->d_sflag, 0, (size_t)na, s));
+    for (int p = 0; p < g->n_pah; ++p) {
+      if (pah >= 0 && p != pah) continue;
+      float* Y = g->d_sy + (size_t)p * chunk * B;
+      float* pa = g->d_spabs + (size_t)p * chunk;
+      RT_CUDA(launch_pah_features(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, p, first_cell + c0,
+                                  na, g->d_sx, pa, s, g->d_list));
+      if ((st = rt_mlp_forward(m, g->d_sx, Y, na, s)) != RT_OK) return st;
+      RT_CUDA(launch_surrogate_check(Y, g->d_sx, pa, na, B, F, t, x_lo, x_hi, g->d_sflag, s));
     }
+    for (int p = 0; p < g->n_pah; ++p) {
+      if (pah >= 0 && p != pah) continue;
+      RT_CUDA(launch_surrogate_add(g->d_sy + (size_t)p * chunk * B, g->d_spabs + (size_t)p * chunk,
+                                   na, B, mode == RT_PAH_AUTO ? g->d_sflag : nullptr, out, s,
+                                   g->d_list));
+    }
+    // cells whose prediction failed its checks
+    RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell + c0, na,
+                           g->d_sflag, g->d_list, g->d_list2, g->d_ucount + 1, s));
+    unsigned nf = 0;
+    RT_CUDA(cudaMemcpyAsync(&nf, g->d_ucount + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    n_fallback += nf;
+    if (mode == RT_PAH_AUTO && nf > 0)
+      RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell + c0, nf,
+                               out, nullptr, pah, s, g->d_list2));
   }
+  if (n_fallback_out) *n_fallback_out = n_fallback;
   if (mem != RT_MEM_DEVICE) {
     RT_CUDA(cudaMemcpyAsync(j_out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
     return sync_status(g, s);
@@ -1054,6 +1201,7 @@ rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packag
     rt_grid* g = grids[m];
     if (!g || g->dev != b->dev) { st = RT_ERR_ARG; break; }
     if ((st = build_tables(g, nullptr)) != RT_OK) break;
+    if ((st = ensure_pathabs(g, o, nullptr)) != RT_OK) break;
     if (n_packages[m] > g->n_total) { st = RT_ERR_RANGE; break; }
     DevRun r;
     if ((st = fill_run(g, n_packages[m], seed + (uint64_t)m, 0, o, &r)) != RT_OK) break;

@@ -79,6 +79,7 @@ struct DevRun {
   unsigned long long* counters;   // [kNumCounters]
   unsigned int* status;
   unsigned* pahabs;               // [n_pah][n_leaves][n_coarse] PAH absorptions
+  float* pathabs;                 // [S][n_leaves] path-length tallies, or null
   float src[3];                   // source position, base-cube units
   float beam[3];
   double src64[3];
@@ -179,17 +180,22 @@ cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream
 cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                              double eps, double d0, long long first, long long n,
                              float* j_out, const unsigned char* want, int pah_only,
-                             cudaStream_t s);
+                             cudaStream_t s, const int* list = nullptr);
 cudaError_t launch_pah_features(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                                 double eps, double d0, int p, long long first, long long n,
-                                float* X, float* p_abs, cudaStream_t s);
+                                float* X, float* p_abs, cudaStream_t s,
+                                const int* list = nullptr);
 cudaError_t launch_pah_encode(const float* J, const float* p_abs, long long n, int B, float* Y,
                               cudaStream_t s);
 cudaError_t launch_surrogate_check(const float* Y, const float* X, const float* p_abs,
                                    long long n, int B, int F, float tol, float x_lo, float x_hi,
                                    unsigned char* flag, cudaStream_t s);
 cudaError_t launch_surrogate_add(const float* Y, const float* p_abs, long long n, int B,
-                                 const unsigned char* flag, float* j_out, cudaStream_t s);
+                                 const unsigned char* flag, float* j_out, cudaStream_t s,
+                                 const int* list = nullptr);
+cudaError_t launch_compact(const PahTables& t, const unsigned* pahabs, long long N, int pah,
+                           long long first, long long n, const unsigned char* flag,
+                           const int* list, int* out, unsigned* count, cudaStream_t s);
 cudaError_t launch_count_flags(const unsigned char* flag, long long n, unsigned long long* out,
                                cudaStream_t s);
 
@@ -197,6 +203,7 @@ cudaError_t launch_frozen_u(const DevGrid& g, const DevTables& t, const float* T
                             float* u_frozen, float t_min, cudaStream_t s);
 cudaError_t launch_temperatures(const DevGrid& g, const DevTables& t,
                                 const unsigned long long* count, float* T_out,
-                                unsigned long long* counters, cudaStream_t s);
+                                unsigned long long* counters, cudaStream_t s,
+                                const float* pathabs = nullptr);
 
 }  // namespace rt

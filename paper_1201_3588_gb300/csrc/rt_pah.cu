@@ -206,18 +206,19 @@ __global__ void k_pah_template(PahTables t, PahBuild pb) {
 // j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin).
 __global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, double eps,
                             double d0, long long first, long long n, float* j_out,
-                            const unsigned char* want, int pah_only) {
+                            const unsigned char* want, int pah_only, const int* list) {
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_warp = t.K + 2 * t.M;
   double* R = sm + (size_t)warp * per_warp;
   double* P = R + t.K;
   double* D = P + t.M;
-  const long long c = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (c >= n) return;
+  const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= n) return;
+  if (want && !want[i]) return;
+  const long long c = list ? (long long)list[i] : i;  // row of j_out (cell - first)
   const long long cell = first + c;
   float* out = j_out + (size_t)c * g.B;
-  if (want && !want[c]) return;
   for (int b = lane; b < g.B; b += 32) out[b] = 0.0f;
   const int lev = g.level[cell];
   const double V = d0 * d0 * d0 / (double)(1ll << (3 * lev));
@@ -253,10 +254,10 @@ __global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, doub
 // p_abs[c] = absorbed power of the cell's PAH p (erg/s), 0 without absorptions.
 __global__ void k_pah_features(DevGrid g, PahTables t, const unsigned* pahabs, double eps,
                                double d0, int p, long long first, long long n, float* X,
-                               float* p_abs) {
+                               float* p_abs, const int* list) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= n) return;
-  const long long cell = first + c;
+  const long long cell = first + (list ? (long long)list[c] : c);
   const int F = t.K + 2;
   const unsigned* cnt = pahabs + ((size_t)p * g.n_leaves + cell) * t.K;
   float* x = X + (size_t)c * F;
@@ -310,7 +311,7 @@ __global__ void k_surrogate_check(const float* Y, const float* X, const float* p
 
 // j_out[c] += P_abs q_b / sum q for cells not flagged. One warp per cell.
 __global__ void k_surrogate_add(const float* Y, const float* p_abs, long long n, int B,
-                                const unsigned char* flag, float* j_out) {
+                                const unsigned char* flag, float* j_out, const int* list) {
   const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= n) return;
@@ -320,10 +321,41 @@ __global__ void k_surrogate_add(const float* Y, const float* p_abs, long long n,
   for (int b = lane; b < B; b += 32) sum += fmax(exp(7.0 * ((double)Y[c * B + b] - 1.0)) - 1e-6, 0.0);
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (!(sum > 0.0)) return;
+  const long long row = list ? (long long)list[c] : c;
   for (int b = lane; b < B; b += 32) {
     double q = fmax(exp(7.0 * ((double)Y[c * B + b] - 1.0)) - 1e-6, 0.0);
-    j_out[c * B + b] += (float)((double)pa * q / sum);
+    j_out[row * B + b] += (float)((double)pa * q / sum);
   }
+}
+
+// Compaction: rows i < n with sel(i) true are appended to out (order not kept);
+// *count receives their number. sel = any PAH absorption in cell first + i (all PAH
+// or only `pah`), or flag[i] when flag is given (then out receives list[i]).
+__global__ void k_compact(const unsigned* pahabs, long long N, int K, int n_pah, int pah,
+                          long long first, long long n, const unsigned char* flag,
+                          const int* list, int* out, unsigned* count) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool sel = false;
+  if (i < n) {
+    if (flag) {
+      sel = flag[i] != 0;
+    } else {
+      for (int p = 0; p < n_pah && !sel; ++p) {
+        if (pah >= 0 && p != pah) continue;
+        const unsigned* cnt = pahabs + ((size_t)p * N + first + i) * K;
+        for (int k = 0; k < K; ++k)
+          if (cnt[k]) { sel = true; break; }
+      }
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, sel);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (sel) out[base + __popc(m & ((1u << lane) - 1u))] = flag ? (list ? list[i] : (int)i) : (int)i;
 }
 
 __global__ void k_count_flags(const unsigned char* flag, long long n, unsigned long long* out) {
@@ -353,7 +385,7 @@ cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream
 cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                              double eps, double d0, long long first, long long n,
                              float* j_out, const unsigned char* want, int pah_only,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int* list) {
   if (n <= 0) return cudaSuccess;
   const int warps = 4;
   size_t smem = sizeof(double) * (size_t)warps * (t.K + 2 * t.M);
@@ -364,7 +396,7 @@ cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigne
   }
   long long blocks = (n + warps - 1) / warps;
   k_pah_exact<<<(unsigned)blocks, 32 * warps, smem, s>>>(g, t, pahabs, eps, d0, first, n,
-                                                        j_out, want, pah_only);
+                                                        j_out, want, pah_only, list);
   return cudaGetLastError();
 }
 
@@ -374,10 +406,10 @@ namespace rt {
 
 cudaError_t launch_pah_features(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                                 double eps, double d0, int p, long long first, long long n,
-                                float* X, float* p_abs, cudaStream_t s) {
+                                float* X, float* p_abs, cudaStream_t s, const int* list) {
   if (n <= 0) return cudaSuccess;
   k_pah_features<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, t, pahabs, eps, d0, p, first, n,
-                                                              X, p_abs);
+                                                              X, p_abs, list);
   return cudaGetLastError();
 }
 
@@ -399,9 +431,20 @@ cudaError_t launch_surrogate_check(const float* Y, const float* X, const float* 
 }
 
 cudaError_t launch_surrogate_add(const float* Y, const float* p_abs, long long n, int B,
-                                 const unsigned char* flag, float* j_out, cudaStream_t s) {
+                                 const unsigned char* flag, float* j_out, cudaStream_t s,
+                                 const int* list) {
   if (n <= 0) return cudaSuccess;
-  k_surrogate_add<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(Y, p_abs, n, B, flag, j_out);
+  k_surrogate_add<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(Y, p_abs, n, B, flag, j_out,
+                                                                     list);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const PahTables& t, const unsigned* pahabs, long long N, int pah,
+                           long long first, long long n, const unsigned char* flag,
+                           const int* list, int* out, unsigned* count, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_compact<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pahabs, N, t.K, t.n_pah, pah, first, n,
+                                                         flag, list, out, count);
   return cudaGetLastError();
 }
 

@@ -154,20 +154,22 @@ __global__ void k_frozen_u(DevGrid g, DevTables t, const float* T_frozen, float*
 // T from n eps = M S(T): binary search in the FP64 S table, then power-law
 // (log-log) interpolation between rows; linear from T = 0 in the first interval.
 __global__ void k_temperatures(DevGrid g, DevTables t, const unsigned long long* count,
-                               float* T_out, unsigned long long* counters) {
+                               float* T_out, unsigned long long* counters,
+                               const float* pathabs) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long tot = (long long)g.S * g.n_leaves;
   bool clamped = false;
   if (idx < tot) {
     int s = (int)(idx / g.n_leaves);
     long long c = idx - (long long)s * g.n_leaves;
-    unsigned long long n = count[idx];
+    // absorbed energy in units of eps: the count, or the path-length tally
+    const double n = pathabs ? (double)pathabs[idx] : (double)count[idx];
     float rho_d0 = g.rho[c * g.S + s];
     float Tv = 0.0f;
-    if (n > 0 && rho_d0 > 0.0f) {
+    if (n > 0.0 && rho_d0 > 0.0f) {
       int lev = g.level[c];
       double rho = (double)rho_d0 / t.d0;
-      double u = (double)n * t.eps_over_V[lev] / rho;
+      double u = n * t.eps_over_V[lev] / rho;
       const double* S = t.S64 + (size_t)s * g.n_T;
       const double* Tg = t.Tgrid;
       int n_T = g.n_T;
@@ -219,9 +221,10 @@ cudaError_t launch_frozen_u(const DevGrid& g, const DevTables& t, const float* T
 
 cudaError_t launch_temperatures(const DevGrid& g, const DevTables& t,
                                 const unsigned long long* count, float* T_out,
-                                unsigned long long* counters, cudaStream_t s) {
+                                unsigned long long* counters, cudaStream_t s,
+                                const float* pathabs) {
   long long n = (long long)g.S * g.n_leaves;
-  k_temperatures<<<nblk(n, 256), 256, 0, s>>>(g, t, count, T_out, counters);
+  k_temperatures<<<nblk(n, 256), 256, 0, s>>>(g, t, count, T_out, counters, pathabs);
   return cudaGetLastError();
 }
 

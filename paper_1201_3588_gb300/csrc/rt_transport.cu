@@ -241,7 +241,7 @@ __device__ __forceinline__ void emit(Pkg<R>& k, unsigned long long id, const Dev
 // from the base cube each time: the plain walk).
 template <typename R>
 __device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa* kap,
-                                       int& leaf, int& level) {
+                                       int& leaf, int& level, float* pathabs) {
   int I[3];
   int rc = locate(g, k.p, k.d, leaf, level, I);
   if (rc == 1) return kEscaped;
@@ -273,6 +273,13 @@ __device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa*
   R kx = (R)0;
   for (int s = 0; s < g.S; ++s) kx += (R)__ldg(&rho[s]) * (R)kb[s].kext;
   const R dtau = kx * tex;
+  if (pathabs) {  // path-length tally of the segment inside this cell
+    const R seg = (kx > (R)0 && dtau > k.tau) ? k.tau / kx : tex;
+    for (int s = 0; s < g.S; ++s) {
+      const float v = (float)((R)__ldg(&rho[s]) * (R)kb[s].kabs * seg);
+      if (v > 0.f) atomicAdd(&pathabs[(size_t)s * g.n_leaves + leaf], v);
+    }
+  }
   if (kx > (R)0 && dtau > k.tau) {
     const R sd = k.tau / kx;
     k.p[0] = fmin(hi0, fmax(lo0, k.p[0] + sd * d0));
@@ -309,7 +316,7 @@ __device__ __forceinline__ int enter(const Pkg<float>& k, const DevGrid& g, Cell
 // descent when the neighbouring region is finer.
 __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevGrid& g,
                                               const Kappa* kap,
-                                              unsigned& child_reads) {
+                                              unsigned& child_reads, float* pathabs) {
   // every array below is indexed with constants only, so it stays in registers
   const float sz = __int_as_float((127 - c.level) << 23);  // 2^-level
   const float lo0 = (float)c.I[0] * sz, lo1 = (float)c.I[1] * sz, lo2 = (float)c.I[2] * sz;
@@ -350,7 +357,16 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
     for (int s = 0; s < g.S; ++s) kx += __ldg(&rho[s]) * kb[s].kext;
   }
   const float dtau = kx * tex;
-  if (kx > 0.f && dtau > k.tau) {
+  const bool hit = kx > 0.f && dtau > k.tau;
+  if (pathabs) {  // path-length tally of the segment inside this cell
+    const float seg = hit ? k.tau / kx : tex;
+    const float* rho = g.rho + (size_t)c.leaf * g.S;
+    for (int s = 0; s < g.S; ++s) {
+      const float v = __ldg(&rho[s]) * kb[s].kabs * seg;
+      if (v > 0.f) atomicAdd(&pathabs[(size_t)s * g.n_leaves + c.leaf], v);
+    }
+  }
+  if (hit) {
     const float sd = k.tau / kx;
     k.p[0] = fminf(hi0, fmaxf(lo0, k.p[0] + sd * d0));
     k.p[1] = fminf(hi1, fmaxf(lo1, k.p[1] + sd * d1));
@@ -547,7 +563,7 @@ __global__ void __launch_bounds__(256) k_transport_plain(DevGrid g, DevTables t,
         break;
       }
       int leaf, level;
-      int a = advance<R>(k, g, t.kap, leaf, level);
+      int a = advance<R>(k, g, t.kap, leaf, level, r.pathabs);
       if (a <= kInteract) tl.levels += level;
       if (a == kCrossed) { ++tl.crossings; continue; }
       if (a == kEscaped) {
@@ -660,7 +676,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
     for (int step = 0; step < K; ++step) {
       // walk phase: lanes not waiting for an interaction cross one cell
       if (alive && !pending) {
-        const int a = advance_linked(k, cell, g, kap, tl.levels);
+        const int a = advance_linked(k, cell, g, kap, tl.levels, r.pathabs);
         if (a == kCrossed) {
           ++tl.crossings;
         } else if (a == kEscaped) {
@@ -802,7 +818,7 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
       break;
     }
     const int lf = c.leaf;
-    const int a = advance_linked(k, c, g, t.kap, tl.levels);
+    const int a = advance_linked(k, c, g, t.kap, tl.levels, nullptr);
     rec[8] = lf;
     if (a == kCrossed) { ++rec[3]; continue; }
     if (a == kEscaped) { ++rec[3]; rec[4] = 1; break; }

@@ -16,6 +16,7 @@ import numpy as np
 from . import _build
 
 REEMIT_BW, REEMIT_NOCORR, REEMIT_FROZEN = 0, 1, 2
+EST_PATHLENGTH = 1
 PAH_EXACT, PAH_SURROGATE, PAH_AUTO = 0, 1, 2
 KERNEL_POOL, KERNEL_PLAIN_F32, KERNEL_PLAIN_F64 = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -46,7 +47,8 @@ class _Opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("kernel", C.c_int32), ("max_events", C.c_uint64),
                 ("blocks_per_sm", C.c_int32), ("threads", C.c_int32),
                 ("refill_period", C.c_int32), ("interaction_batch", C.c_int32),
-                ("budget_s", C.c_double)]
+                ("budget_s", C.c_double), ("estimators", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class _Counters(C.Structure):
@@ -72,6 +74,8 @@ SIGNATURES = {
     "rt_cell_temperatures": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "rt_sed": [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p],
     "rt_counts": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_cell_temperatures_pathlength": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_pathlength": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "rt_set_counts": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "rt_get_counters": [C.c_void_p, C.POINTER(_Counters)],
     "rt_trace": [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p],
@@ -214,6 +218,7 @@ class Grid:
         beam = (C.c_double * 3)(*st.beam_dir)
         _check(load().rt_emit_star(self._h, st.T, st.L, pos, int(st.kind), beam, int(n_total)),
                "rt_emit_star")
+        self.n_total = int(n_total)
 
     def set_frozen_temperatures(self, T, stream=None):
         if not hasattr(T, "data_ptr"):
@@ -226,10 +231,12 @@ class Grid:
     def transport(self, n_packages: int, seed: int = 0, first_id: int = 0,
                   mode: int = REEMIT_BW, kernel: int = KERNEL_POOL, max_events: int = 0,
                   blocks_per_sm: int = 0, threads: int = 0, refill_period: int = 0,
-                  interaction_batch: int = 0, budget_s: float = 0.0, stream=None):
+                  interaction_batch: int = 0, budget_s: float = 0.0, estimators: int = 0,
+                  stream=None):
         o = _Opts(mode=mode, kernel=kernel, max_events=max_events, blocks_per_sm=blocks_per_sm,
                   threads=threads, refill_period=refill_period,
-                  interaction_batch=interaction_batch, budget_s=budget_s)
+                  interaction_batch=interaction_batch, budget_s=budget_s,
+                  estimators=estimators, reserved=0)
         _check(load().rt_transport(self._h, int(n_packages), int(seed), int(first_id),
                                    C.byref(o), _stream(stream)), "rt_transport")
 
@@ -242,6 +249,21 @@ class Grid:
         p, mem = _ptr_mem(out)
         _check(load().rt_cell_temperatures(self._h, p, mem, _stream(stream)),
                "rt_cell_temperatures")
+        return out
+
+    def temperatures_pathlength(self, out=None, stream=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros((self.S, self.N), dtype=np.float32)
+        p, mem = _ptr_mem(out)
+        _check(load().rt_cell_temperatures_pathlength(self._h, p, mem, _stream(stream)),
+               "rt_cell_temperatures_pathlength")
+        return out
+
+    def pathlength(self, out=None, stream=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros((self.S, self.N), dtype=np.float32)
+        p, mem = _ptr_mem(out)
+        _check(load().rt_pathlength(self._h, p, mem, _stream(stream)), "rt_pathlength")
         return out
 
     def sed(self, out=None, stream=None):
@@ -328,7 +350,8 @@ class Batch:
         npk = np.ascontiguousarray(n_packages, dtype=np.uint64)
         o = _Opts(mode=mode, kernel=KERNEL_POOL, max_events=max_events,
                   blocks_per_sm=blocks_per_sm, threads=0, refill_period=refill_period,
-                  interaction_batch=interaction_batch, budget_s=budget_s)
+                  interaction_batch=interaction_batch, budget_s=budget_s, estimators=0,
+                  reserved=0)
         h = C.c_void_p()
         _check(L.rt_batch_create(C.cast(arr, C.c_void_p), len(self.grids), npk.ctypes.data,
                                  int(seed), C.byref(o), int(chunk), C.byref(h)),
