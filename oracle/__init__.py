@@ -58,12 +58,14 @@ class _Run(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("first_id", C.c_uint64), ("n_packages", C.c_uint64),
                 ("n_total", C.c_uint64), ("mode", C.c_int32), ("pad", C.c_int32),
                 ("max_events", C.c_uint64), ("t_min", C.c_double),
-                ("T_frozen", C.c_void_p)]
+                ("T_frozen", C.c_void_p), ("obs_dir", C.c_double * 3),
+                ("plane_of_bin", C.c_void_p), ("n_planes", C.c_int32), ("nx", C.c_int32),
+                ("ny", C.c_int32), ("pad2", C.c_int32), ("img_half", C.c_double)]
 
 
 class _Tally(C.Structure):
     _fields_ = [("count", C.c_void_p), ("sed", C.c_void_p), ("pahabs", C.c_void_p),
-                ("pathabs", C.c_void_p), ("emitted", C.c_uint64),
+                ("pathabs", C.c_void_p), ("image", C.c_void_p), ("emitted", C.c_uint64),
                 ("escaped", C.c_uint64), ("capped", C.c_uint64),
                 ("absorptions", C.c_uint64), ("scatters", C.c_uint64),
                 ("crossings", C.c_uint64), ("errors", C.c_uint64)]
@@ -102,6 +104,8 @@ def lib():
             L.orc_ray_cells.restype = C.c_int64
             L.orc_package_energy.argtypes = [C.POINTER(_Model), C.c_uint64]
             L.orc_package_energy.restype = d
+            L.orc_optical_depth.argtypes = [C.POINTER(_Model), dp, dp, C.c_int]
+            L.orc_optical_depth.restype = d
             L.orc_transport.argtypes = [C.POINTER(_Model), C.POINTER(_Run), C.POINTER(_Tally)]
             L.orc_transport.restype = C.c_int
             L.orc_trace.argtypes = [C.POINTER(_Model), C.POINTER(_Run), dp, C.c_int64, dp]
@@ -253,12 +257,39 @@ def package_energy(model, n_total: int) -> float:
     return lib().orc_package_energy(C.byref(om.s), int(n_total))
 
 
+def optical_depth(model, p_cm, direction, bin: int) -> float:
+    """Extinction optical depth from p (cm, model centre at 0) along `direction` to
+    the model boundary at frequency bin `bin`."""
+    om = as_oracle(model)
+    pp = np.ascontiguousarray(p_cm, dtype=np.float64)
+    dd = np.ascontiguousarray(direction, dtype=np.float64)
+    return lib().orc_optical_depth(C.byref(om.s), _ptr(pp), _ptr(dd), int(bin))
+
+
+@dataclass
+class Peel:
+    """Peel-off images toward a distant observer: `plane_of_bin[b]` is the image
+    plane that bin b contributes to (-1: none); each plane is nx by ny pixels over a
+    square of half width `half_width` cm centred on the model, seen along
+    `obs_dir` (unit vector pointing to the observer)."""
+    obs_dir: np.ndarray
+    plane_of_bin: np.ndarray
+    nx: int
+    ny: int
+    half_width: float
+
+    @property
+    def n_planes(self) -> int:
+        return int(np.max(self.plane_of_bin)) + 1 if np.any(self.plane_of_bin >= 0) else 0
+
+
 @dataclass
 class Tally:
     count: np.ndarray     # uint64 [S][N]
     sed: np.ndarray       # uint64 [2][n_dir][B]
     pahabs: np.ndarray    # uint64 [n_pah][N][n_coarse]
     pathabs: np.ndarray   # float64 [S][N] path-length sums (absorption optical depth)
+    image: Optional[np.ndarray] = None  # float64 [n_planes][ny][nx] erg/s/sr (peel-off)
     emitted: int = 0
     escaped: int = 0
     capped: int = 0
@@ -268,36 +299,56 @@ class Tally:
     errors: int = 0
 
 
-def new_tally(model) -> Tally:
+def new_tally(model, peel: Optional[Peel] = None) -> Tally:
     om = as_oracle(model)
+    img = None
+    if peel is not None:
+        img = np.zeros((peel.n_planes, peel.ny, peel.nx), dtype=np.float64)
     return Tally(np.zeros((om.S, om.N), dtype=np.uint64),
                  np.zeros((2, om.model.n_sed_dirs, om.B), dtype=np.uint64),
                  np.zeros((max(om.n_pah, 1), om.N, om.n_coarse), dtype=np.uint64),
-                 np.zeros((om.S, om.N), dtype=np.float64))
+                 np.zeros((om.S, om.N), dtype=np.float64), img)
 
 
-def _run(n_packages, seed, first_id, n_total, mode, max_events, t_min, T_frozen):
+def _run(n_packages, seed, first_id, n_total, mode, max_events, t_min, T_frozen,
+         peel: Optional[Peel] = None):
     tf = None
     if T_frozen is not None:
         tf = np.ascontiguousarray(T_frozen, dtype=np.float64)
     r = _Run(seed=int(seed), first_id=int(first_id), n_packages=int(n_packages),
              n_total=int(n_total), mode=int(mode), pad=0, max_events=int(max_events),
              t_min=float(t_min), T_frozen=_ptr(tf) if tf is not None else None)
-    return r, tf
+    keep = [tf]
+    if peel is not None:
+        o = np.asarray(peel.obs_dir, dtype=np.float64)
+        o = o / np.linalg.norm(o)
+        pob = np.ascontiguousarray(peel.plane_of_bin, dtype=np.int32)
+        keep.append(pob)
+        r.obs_dir = (C.c_double * 3)(*o)
+        r.plane_of_bin = _ptr(pob)
+        r.n_planes, r.nx, r.ny = peel.n_planes, int(peel.nx), int(peel.ny)
+        r.img_half = float(peel.half_width)
+    return r, keep
 
 
 def transport(model, n_packages: int, seed: int = 0, first_id: int = 0,
               n_total: Optional[int] = None, mode: int = MODE_BW,
               max_events: int = 10_000_000, t_min: float = T_MIN_DEFAULT,
-              T_frozen: Optional[np.ndarray] = None, tally: Optional[Tally] = None) -> Tally:
+              T_frozen: Optional[np.ndarray] = None, tally: Optional[Tally] = None,
+              peel: Optional[Peel] = None) -> Tally:
     """Follow packages ``first_id .. first_id+n_packages-1``; counts accumulate into
-    ``tally`` (a new one if None)."""
+    ``tally`` (a new one if None). With ``peel``, every emission, scattering and
+    re-emission also sends its share toward the observer into ``tally.image``."""
     om = as_oracle(model)
-    tl = tally if tally is not None else new_tally(om)
+    tl = tally if tally is not None else new_tally(om, peel)
+    if peel is not None and (tl.image is None or tl.image.shape !=
+                             (peel.n_planes, peel.ny, peel.nx)):
+        raise ValueError("tally has no image of the peel-off shape")
     r, keep = _run(n_packages, seed, first_id, n_total or n_packages, mode, max_events,
-                   t_min, T_frozen)
+                   t_min, T_frozen, peel)
     ct = _Tally(count=_ptr(tl.count), sed=_ptr(tl.sed), pahabs=_ptr(tl.pahabs),
                 pathabs=_ptr(tl.pathabs),
+                image=_ptr(tl.image) if (peel is not None) else None,
                 emitted=tl.emitted,
                 escaped=tl.escaped, capped=tl.capped, absorptions=tl.absorptions,
                 scatters=tl.scatters, crossings=tl.crossings, errors=tl.errors)

@@ -489,6 +489,79 @@ static int sed_dir_bin(const double d[3], int ndir)
     return k;
 }
 
+/* Extinction optical depth from p (base-cube units) along d to the domain boundary
+ * at bin `bin`, walking the cells like a package that never interacts. */
+static double tau_to_boundary(const orc_model *m, const ctx_t *c, const double p0[3],
+                              const double d[3], int bin)
+{
+    double p[3] = {p0[0], p0[1], p0[2]};
+    const int S = m->n_species, B = m->n_bins;
+    const int64_t N = m->n_leaves;
+    double tau = 0.0;
+    for (int guard = 0; guard < 100000000; ++guard) {
+        int64_t cell[5];
+        int rc = orc_locate(m, p, d, cell);
+        if (rc != 0) break;
+        double lo[3], hi[3];
+        leaf_box(cell, lo, hi);
+        int ax;
+        double t = exit_distance(p, d, lo, hi, &ax);
+        double k = 0.0;
+        for (int s = 0; s < S; ++s) k += m->rho[(size_t)s * N + cell[0]] * c->kext[s * B + bin];
+        tau += k * c->d0 * t;
+        for (int a = 0; a < 3; ++a) p[a] += t * d[a];
+        p[ax] = d[ax] > 0.0 ? hi[ax] : lo[ax];
+        clamp3(p, lo, hi);
+    }
+    return tau;
+}
+
+double orc_optical_depth(const orc_model *m, const double p_cm[3], const double dir[3], int bin)
+{
+    orc_run r;
+    memset(&r, 0, sizeof(r));
+    r.n_total = 1;
+    ctx_t c;
+    if (ctx_init(m, &r, &c)) { ctx_free(&c); return -1.0; }
+    double p[3];
+    for (int a = 0; a < 3; ++a) p[a] = (p_cm[a] + m->half_size) / c.d0;
+    double t = tau_to_boundary(m, &c, p, dir, bin);
+    ctx_free(&c);
+    return t;
+}
+
+/* Peel-off: the share w (per steradian) of the package's energy that leaves the
+ * event at p toward the observer, attenuated by the line of sight, into the pixel
+ * the position projects to. */
+static void peel(const orc_model *m, const orc_run *r, const ctx_t *c, orc_tally *t,
+                 const double p[3], int bin, double w)
+{
+    if (!t || !t->image || r->n_planes <= 0) return;
+    int plane = r->plane_of_bin[bin];
+    if (plane < 0) return;
+    const double *o = r->obs_dir;
+    double tau = tau_to_boundary(m, c, p, o, bin);
+    /* image axes: e1 = normalise(z x o) (x when o is along z), e2 = o x e1 */
+    double e1[3], e2[3];
+    if (fabs(o[2]) < 0.999999) {
+        double nn = sqrt(o[0] * o[0] + o[1] * o[1]);
+        e1[0] = -o[1] / nn; e1[1] = o[0] / nn; e1[2] = 0.0;
+    } else {
+        e1[0] = 1.0; e1[1] = 0.0; e1[2] = 0.0;
+    }
+    e2[0] = o[1] * e1[2] - o[2] * e1[1];
+    e2[1] = o[2] * e1[0] - o[0] * e1[2];
+    e2[2] = o[0] * e1[1] - o[1] * e1[0];
+    double x[3];
+    for (int a = 0; a < 3; ++a) x[a] = p[a] * c->d0 - m->half_size;
+    double u = x[0] * e1[0] + x[1] * e1[1] + x[2] * e1[2];
+    double v = x[0] * e2[0] + x[1] * e2[1] + x[2] * e2[2];
+    int px = (int)floor((u + r->img_half) / (2.0 * r->img_half) * r->nx);
+    int py = (int)floor((v + r->img_half) / (2.0 * r->img_half) * r->ny);
+    if (px < 0 || px >= r->nx || py < 0 || py >= r->ny) return;
+    t->image[((size_t)plane * r->ny + py) * r->nx + px] += c->eps * w * exp(-tau);
+}
+
 /* Follow package `id` until it leaves the grid or reaches the event cap.
  * count may be NULL only in the frozen mode (trajectories then do not depend on
  * the counts). */
@@ -513,6 +586,7 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
     }
     double tau = -log(u[3]);
     for (int a = 0; a < 3; ++a) p[a] = c->src[a];
+    if (m->source_kind != ORC_SOURCE_BEAM) peel(m, r, c, t, p, bin, 1.0 / (4.0 * PI));
 
     for (;;) {
         int64_t cell[5];
@@ -559,6 +633,13 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
             if (u[0] * kext < ksca) {
                 /* 3. scattering by the phase function of the scattering species */
                 int s = sample_discrete(wsca, S, u[1]);
+                if (t && t->image && r->n_planes > 0) {
+                    /* Henyey-Greenstein probability per steradian toward the observer */
+                    double gg = m->g[s * B + bin];
+                    double mo = d[0] * r->obs_dir[0] + d[1] * r->obs_dir[1] + d[2] * r->obs_dir[2];
+                    double w = (1.0 - gg * gg) / (4.0 * PI * pow(1.0 + gg * gg - 2.0 * gg * mo, 1.5));
+                    peel(m, r, c, t, p, bin, w);
+                }
                 double mu = orc_hg_mu(m->g[s * B + bin], u[2]);
                 orc_rotate(d, mu, 2.0 * PI * u[3]);
                 ++n_sca;
@@ -569,16 +650,17 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
                 size_t ci = (size_t)s * N + leaf;
                 uint64_t n = 0;
                 if (count) n = count[ci]++;
-                int p = m->pah_index ? m->pah_index[s] : -1;
-                if (p >= 0) {
+                int pa = m->pah_index ? m->pah_index[s] : -1;
+                if (pa >= 0) {
                     /* PAH: the absorbed photon goes to the cell's coarse absorbed
                      * spectrum; the package leaves at a frequency from the PAH's
                      * template emission spectrum */
                     if (t && t->pahabs) {
                         int kc = (int)(((int64_t)bin * m->n_coarse) / B);
-                        t->pahabs[((size_t)p * N + leaf) * m->n_coarse + kc] += 1;
+                        t->pahabs[((size_t)pa * N + leaf) * m->n_coarse + kc] += 1;
                     }
-                    bin = sample_discrete(m->pah_template + (size_t)p * B, B, v[2]);
+                    bin = sample_discrete(m->pah_template + (size_t)pa * B, B, v[2]);
+                    peel(m, r, c, t, p, bin, 1.0 / (4.0 * PI));
                     isotropic(u[2], u[3], d);
                     ++n_abs;
                     tau = -log(v[0]);
@@ -593,6 +675,7 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
                 }
                 bin = orc_reemit_bin(m, s, r->mode, n, e, uf, r->t_min, v[1], v[2]);
                 if (bin < 0) { err = 1; break; }
+                peel(m, r, c, t, p, bin, 1.0 / (4.0 * PI));
                 isotropic(u[2], u[3], d);
                 ++n_abs;
             }

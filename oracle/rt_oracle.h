@@ -55,6 +55,11 @@ typedef struct {
     uint64_t max_events;       /* interaction cap per package */
     double t_min;              /* temperature floor of the no-correction mode */
     const double *T_frozen;    /* [S][N] for the frozen-temperature mode */
+    /* peel-off toward a distant observer (may be absent: n_planes = 0) */
+    double obs_dir[3];         /* unit vector from the model to the observer */
+    const int32_t *plane_of_bin; /* [B]: image plane of each bin, -1 for none */
+    int32_t n_planes, nx, ny, pad2;
+    double img_half;           /* half width of the square image, cm */
 } orc_run;
 
 typedef struct {
@@ -62,6 +67,7 @@ typedef struct {
     uint64_t *sed;             /* [2][n_dir][B]: all escaped / escaped uncollided */
     uint64_t *pahabs;          /* [n_pah][N][n_coarse] PAH absorptions, or NULL */
     double *pathabs;           /* [S][N] Lucy path-length sums of rho kappa_abs l, or NULL */
+    double *image;             /* [n_planes][ny][nx] peel-off images, erg/s/sr, or NULL */
     uint64_t emitted, escaped, capped, absorptions, scatters, crossings, errors;
 } orc_tally;
 
@@ -86,6 +92,7 @@ int orc_locate(const orc_model *m, const double p[3], const double d[3], int64_t
 int64_t orc_ray_cells(const orc_model *m, const double p0[3], const double d0[3],
                       int64_t max_cells, int64_t *leaves, double *lengths);
 double orc_package_energy(const orc_model *m, uint64_t n_total);
+double orc_optical_depth(const orc_model *m, const double p_cm[3], const double dir[3], int bin);
 int orc_transport(const orc_model *m, const orc_run *r, orc_tally *t);
 int orc_trace(const orc_model *m, const orc_run *r, const uint64_t *ids, int64_t n,
               orc_trace_rec *out);
