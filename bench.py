@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--packages", type=float, default=1e8, help="packages per GPU per step")
-    p.add_argument("--workload", choices=["disk", "sphere", "batch", "disk_pah"],
+    p.add_argument("--workload", choices=["disk", "sphere", "batch", "disk_pah", "disk_images"],
                    default="disk")
     p.add_argument("--batch-models", type=int, default=256)
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -62,6 +62,12 @@ def build_model(name):
     from paper_1201_3588_gb300 import workloads as w
     if name == "sphere":
         return w.sphere_model(), "dust sphere 16^3, 64 bins, 2 species, tau_V=1"
+    if name == "disk_images":
+        return (w.disk_model(),
+                "flared disk 128^3 base + 2 levels of 2x2x2 refinement, 200 bins, 2 species, "
+                "midplane tau_V=1e3, r 0.1-100 AU; peel-off images at the 10 and 11.3 micron "
+                "bins, 256x256 pixels over +-100 AU, inclination 60 deg, and their dual-band "
+                "major-axis profile")
     if name == "disk_pah":
         return (w.disk_pah_model(),
                 "flared disk with gap and spiral, 128^3 base + 2 levels, 200 bins, silicate, "
@@ -212,11 +218,14 @@ def traffic_per_launch(n_packages):
 
 def walk_bytes(c, S):
     """Algorithmic bytes of one transport launch (per unit of work):
-    every cell entered reads one base-cube id (4 B), one child id per refinement
-    level (4 B each) and S densities (4 B each); every absorption is one 8-byte
-    read-modify-write of a count (16 B)."""
+    every cell entered reads its face link (4 B) and S densities (4 B each), every
+    descent into a finer neighbour one child id (4 B); every absorption is one 8-byte
+    read-modify-write of a count (16 B). Peel-off: every cell a sight line crosses
+    reads the same link and densities, every peeled event adds into an FP64 pixel
+    (16 B)."""
     entered = c["crossings"] + c["absorptions"] + c["scatters"] + c["capped"]
-    return entered * (4 + 4 * S) + 4 * c["levels"] + 16 * c["absorptions"]
+    return (entered * (4 + 4 * S) + 4 * c["levels"] + 16 * c["absorptions"]
+            + c.get("peel_crossings", 0) * (4 + 4 * S) + 16 * c.get("peel_events", 0))
 
 
 def run_ours(args):
@@ -240,6 +249,19 @@ def run_ours(args):
     cnt_dev = torch.empty((S, N), dtype=torch.int64, device=dev) if world > 1 else None
     first = rank * n
     pah = args.workload == "disk_pah"
+    images = args.workload == "disk_images"
+    img_dev = prof_dev = None
+    if images:
+        import numpy as np
+        from paper_1201_3588_gb300 import workloads as w
+        lam = w.bin_centre_wavelength(model.nu_edges) / w.MICRON
+        pob = np.full(B, -1, np.int32)
+        pob[int(np.argmin(np.abs(lam - 11.3)))] = 0       # the band
+        pob[int(np.argmin(np.abs(lam - 10.0)))] = 1       # the continuum beside it
+        inc = math.radians(60.0)
+        g.set_images((0.0, math.sin(inc), math.cos(inc)), pob, 256, 256, model.half_size)
+        img_dev = torch.empty((2, 256, 256), dtype=torch.float64, device=dev)
+        prof_dev = torch.empty(256, dtype=torch.float64, device=dev)
     net, pah_info = None, {}
     pah_chunk = 1 << 20
     j_dev = torch.empty((min(pah_chunk, N), B), dtype=torch.float32, device=dev) if pah else None
@@ -287,6 +309,9 @@ def run_ours(args):
         g.sed(out=sed_dev, stream=stream)
         if pah:
             pah_emission()
+        if images:
+            g.images(out=img_dev, stream=stream)
+            g.image_profile(0, 1, 2, out=prof_dev, stream=stream)
 
     for k in range(args.warmup):
         step(k)
@@ -324,8 +349,10 @@ def run_ours(args):
     bytes_launch = walk_bytes(c, S)
     achieved = bytes_launch / kmean / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": traffic_per_launch(n), "peak_source": src,
-            "kernel": "k_transport_pool", "kernel_ms": 1e3 * kmean,
+            "frac": achieved / hbm,
+            "traffic": None if images else traffic_per_launch(n), "peak_source": src,
+            "kernel": "k_transport_pool" + (" (peel-off variant)" if images else ""),
+            "kernel_ms": 1e3 * kmean,
             "algorithmic_bytes_per_launch": bytes_launch}
 
     extra = {}
@@ -345,10 +372,15 @@ def run_ours(args):
         torch.cuda.synchronize()
         pah_info["surrogate_auto_pah_ms"] = a.elapsed_time(e)
         extra["pah"] = pah_info
-    if rank == 0 and not args.no_plain:
+    if images:
+        extra["images"] = {"peel_events": c["peel_events"],
+                           "peel_crossings": c["peel_crossings"],
+                           "band_minus_continuum_total": float((img_dev[0] - img_dev[1]).sum()),
+                           "profile_peak": float(prof_dev.max())}
+    if rank == 0 and not args.no_plain and not images:
         extra["plain"] = plain_rates(g, model, int(args.plain_packages), stream, c, n)
-    e2e = e2e_rate(model, n, world, first, args.e2e_steps) if args.e2e_steps > 0 and not pah \
-        else None
+    e2e = e2e_rate(model, n, world, first, args.e2e_steps) \
+        if args.e2e_steps > 0 and not pah and not images else None
     if rank == 0:
         cpu_rate, cpu_n, cpu_s = cpu_oracle_rate(model, n * world, args.cpu_seconds)
         line = {
@@ -366,7 +398,8 @@ def run_ours(args):
                              "sample": f"first {cpu_n} packages of the same workload "
                                        f"(BW mode, one thread, {cpu_s:.1f} s)"},
             "e2e": e2e,
-            "gpu_launches": (2 + (pah_launches(N, pah_chunk) if pah else 0)) * args.steps,
+            "gpu_launches": (2 + (pah_launches(N, pah_chunk) if pah else 0)
+                             + (4 if images else 0)) * args.steps,
             "clocks": clocks,
             "per_step": {"crossings": c["crossings"], "absorptions": c["absorptions"],
                          "scatters": c["scatters"], "capped": c["capped"],

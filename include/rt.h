@@ -110,6 +110,9 @@ typedef struct rt_counters {
     uint64_t clamped;       /* absorptions whose energy lay beyond the table's t_max */
     uint64_t levels;        /* sum over cells entered (crossed or interacted in) of the
                                cell's refinement level: child-table reads of the walk */
+    uint64_t peel_events;   /* scatterings and re-emissions sent toward the observer */
+    uint64_t peel_crossings;/* cells crossed by their sight lines (and the source's) */
+    uint64_t peel_dropped;  /* events beyond the event buffer's capacity (not imaged) */
 } rt_counters;
 
 /* Create a grid handle; copies the tree and densities to the device. */
@@ -178,6 +181,54 @@ rt_status rt_set_counts(rt_grid *g, const uint64_t *in, int mem, void *stream);
 /* Package totals accumulated since the last reset; synchronises the handle's
  * last stream and reports device-side faults. */
 rt_status rt_get_counters(rt_grid *g, rt_counters *out);
+
+/* ---------------------------------------------------------------------------
+ * Peel-off images (Sec. 3, Fig. 2: images of the model at chosen wavelengths and
+ * flux profiles along the disk's major axis, seen from a distant observer).
+ * While images are set, every pool-kernel launch also sends toward the observer,
+ * from each point-source emission, scattering and re-emission whose (outgoing) bin
+ * has an image plane, the share of the package energy per steradian that leaves
+ * in the observer's direction -- 1/(4 pi) for isotropic emission, the
+ * Henyey-Greenstein phase function of the scattering species at the scattering
+ * angle for a scattering -- attenuated by exp(-tau) along the sight line to the
+ * boundary, into the pixel the event's position projects to. The image is the
+ * observed intensity integrated over each pixel: erg/s/sr per pixel (divide by the
+ * squared distance for the flux). The packages' own paths are unchanged.
+ * A launch records its events in a device buffer (20 bytes each) and a second
+ * kernel traces their sight lines; events beyond the buffer's capacity are counted
+ * as dropped and not imaged.
+ * ------------------------------------------------------------------------- */
+typedef struct rt_image_desc {
+    double obs_dir[3];      /* direction from the model toward the observer (normalised
+                               here). Image axes: u along normalise(z x o) (x when o
+                               lies along z), v = o x u; pixel (ix, iy) holds
+                               u in [-h + ix 2h/nx, ...), v likewise with ny. */
+    int32_t nx, ny;         /* pixels (1 .. 16384 each) */
+    double half_width_cm;   /* h: the images span [-h, h]^2 around the model centre */
+    double tau_max;         /* sight lines deeper than this add nothing (0: 40) */
+    uint64_t event_capacity;/* events one transport launch can record (0: 2^24; at
+                               most 2^31) */
+} rt_image_desc;
+
+/* Set (or, with d == NULL, remove) the images: plane_of_bin (host, [n_bins]) gives
+ * each bin's image plane or -1; the planes are 0 .. max(plane_of_bin), all nx by
+ * ny. Allocates the images and zeroes them; rt_reset zeroes them too. While set,
+ * only the pool kernel may transport (plain kernels: RT_ERR_STATE) and the grid
+ * cannot join a batch (RT_ERR_STATE). RT_ERR_TOO_LARGE beyond 2^28 pixels in all. */
+rt_status rt_set_images(rt_grid *g, const rt_image_desc *d, const int32_t *plane_of_bin);
+
+/* The images, [n_planes][ny][nx] doubles in erg/s/sr per pixel (scaled by the
+ * current package energy eps). mem: where `out` lives; a host copy synchronises and
+ * returns RT_ERR_RANGE (after copying) when events were dropped since the last reset
+ * (rt_get_counters reports them in either case). */
+rt_status rt_images(rt_grid *g, double *out, int mem, void *stream);
+
+/* Profile along the image's u axis (the major axis of a disk in the z = 0 plane
+ * seen inclined about the x axis): out[ix] = mean over the rows whose centres lie
+ * within half_rows pixels of the centre line of (plane_a - plane_b), plane_b = -1
+ * for none (a dual-band difference otherwise). nx doubles, erg/s/sr per pixel. */
+rt_status rt_image_profile(rt_grid *g, int plane_a, int plane_b, int half_rows, double *out,
+                           int mem, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Batches: many models (grids) of uneven size, optical depth and package count in

@@ -33,6 +33,14 @@
  * Frequencies are discrete bins; P_b(T) is the Planck function integrated over
  * bin b. The random numbers come from Philox4x32-10 (Salmon et al. 2011) with
  * key = seed and counter = (package id lo, hi, event index, block index).
+ *
+ * Images (Sec. 3, Fig. 2) by peel-off toward an observer at infinity along o: at
+ * the emission (point source), at every scattering and at every re-emission the
+ * package sends eps * w * exp(-tau) into the pixel its position projects to, with
+ * w the probability per steradian of leaving toward o (1/(4 pi) when isotropic, the
+ * Henyey-Greenstein phase function at the angle between the incoming direction and
+ * o when scattered) and tau the extinction optical depth from the event to the
+ * boundary along o at the outgoing frequency. The package's own path is unchanged.
  */
 #include "rt_oracle.h"
 

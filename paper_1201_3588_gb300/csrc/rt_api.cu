@@ -62,6 +62,17 @@ struct rt_grid {
   float* d_pah_cdf = nullptr;
   unsigned* d_pahabs = nullptr;
   float* d_pathabs = nullptr;  // path-length tallies [S][N]
+  // peel-off images
+  int* d_plane_of_bin = nullptr;         // [B]
+  double* d_image = nullptr;             // [n_planes][ny][nx]
+  unsigned long long* d_nemit = nullptr; // [B]
+  float4* d_ev = nullptr;                // [capacity] recorded peel-off events
+  int* d_ev_bin = nullptr;               // [capacity]
+  unsigned long long* d_nev = nullptr;   // [1]
+  double* d_iscratch = nullptr;          // [max(n_planes*ny*nx, nx)] readout (host copies)
+  size_t iscratch_n = 0;
+  DevPeel peel{};
+  bool images = false;
   float* d_jscratch = nullptr;
   size_t jscratch_n = 0;
   // surrogate scratch (cells per chunk)
@@ -166,6 +177,13 @@ void free_all(rt_grid* g) {
   dfree(g->d_Tscratch);
   dfree(g->d_pahabs);
   dfree(g->d_pathabs);
+  dfree(g->d_plane_of_bin);
+  dfree(g->d_image);
+  dfree(g->d_nemit);
+  dfree(g->d_ev);
+  dfree(g->d_ev_bin);
+  dfree(g->d_nev);
+  dfree(g->d_iscratch);
   dfree(g->d_jscratch);
   dfree(g->d_sx);
   dfree(g->d_sy);
@@ -733,6 +751,11 @@ rt_status rt_reset(rt_grid* g, void* stream) {
     RT_CUDA(cudaMemsetAsync(g->d_pahabs, 0,
                             sizeof(unsigned) * g->n_pah * N * g->tab.n_coarse, s));
   if (g->d_pathabs) RT_CUDA(cudaMemsetAsync(g->d_pathabs, 0, sizeof(float) * S * N, s));
+  if (g->images) {
+    const size_t n = (size_t)g->peel.n_planes * g->peel.ny * g->peel.nx;
+    RT_CUDA(cudaMemsetAsync(g->d_image, 0, sizeof(double) * n, s));
+    RT_CUDA(cudaMemsetAsync(g->d_nemit, 0, sizeof(unsigned long long) * g->desc.n_bins, s));
+  }
   return RT_OK;
 }
 
@@ -803,9 +826,16 @@ rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
   if ((st = fill_run(g, n_packages, seed, first_package_id, o, &r)) != RT_OK) return st;
   DevTables t = g->tab;
   t.u_frozen = g->d_ufrozen;
+  if (g->images && kernel != RT_KERNEL_POOL) return RT_ERR_STATE;
   if (kernel == RT_KERNEL_POOL) {
     RT_CUDA(cudaMemsetAsync(g->d_next, 0, sizeof(unsigned long long), s));
-    RT_CUDA(launch_transport_pool(g->g, t, r, o ? o->blocks_per_sm : 0, threads, s));
+    RT_CUDA(launch_transport_pool(g->g, t, r, o ? o->blocks_per_sm : 0, threads, s,
+                                  g->images ? &g->peel : nullptr));
+    if (g->images) {
+      RT_CUDA(launch_peel_source(g->g, t, r, g->peel, s));
+      RT_CUDA(launch_peel_trace(g->g, t, r, g->peel, s));
+      RT_CUDA(cudaMemsetAsync(g->d_nev, 0, sizeof(unsigned long long), s));
+    }
   } else {
     RT_CUDA(launch_transport_plain(g->g, t, r, kernel == RT_KERNEL_PLAIN_F64, threads, s));
   }
@@ -924,7 +954,159 @@ rt_status rt_get_counters(rt_grid* g, rt_counters* out) {
   out->errors = c[kCErrors];
   out->clamped = c[kCClamped];
   out->levels = c[kCLevels];
+  out->peel_events = c[kCPeelEvents];
+  out->peel_crossings = c[kCPeelCrossings];
+  out->peel_dropped = c[kCPeelDropped];
   return sync_status(g, nullptr);
+}
+
+rt_status rt_set_images(rt_grid* g, const rt_image_desc* d, const int32_t* plane_of_bin) {
+  if (!g) return RT_ERR_ARG;
+  RT_CUDA(cudaSetDevice(g->dev));
+  if (!d) {  // images off
+    RT_CUDA(cudaDeviceSynchronize());
+    dfree(g->d_plane_of_bin);
+    dfree(g->d_image);
+    dfree(g->d_nemit);
+    dfree(g->d_ev);
+    dfree(g->d_ev_bin);
+    dfree(g->d_nev);
+    dfree(g->d_iscratch);
+    g->iscratch_n = 0;
+    g->images = false;
+    g->peel = DevPeel{};
+    return RT_OK;
+  }
+  const int B = g->desc.n_bins;
+  if (!plane_of_bin || !finite3(d->obs_dir) || d->nx < 1 || d->ny < 1 ||
+      d->nx > kMaxImageSide || d->ny > kMaxImageSide || !(d->half_width_cm > 0) ||
+      !std::isfinite(d->half_width_cm) || !(d->tau_max >= 0) || !std::isfinite(d->tau_max))
+    return RT_ERR_ARG;
+  double on = std::sqrt(d->obs_dir[0] * d->obs_dir[0] + d->obs_dir[1] * d->obs_dir[1] +
+                        d->obs_dir[2] * d->obs_dir[2]);
+  if (!(on > 0)) return RT_ERR_ARG;
+  int n_planes = 0;
+  for (int b = 0; b < B; ++b) {
+    if (plane_of_bin[b] < -1 || plane_of_bin[b] >= B) return RT_ERR_ARG;
+    if (plane_of_bin[b] + 1 > n_planes) n_planes = plane_of_bin[b] + 1;
+  }
+  if (n_planes == 0) return RT_ERR_ARG;
+  const size_t n_img = (size_t)n_planes * d->ny * d->nx;
+  if (n_img > kMaxImagePixels) return RT_ERR_TOO_LARGE;
+  const unsigned long long cap = d->event_capacity ? d->event_capacity : kPeelCapacityDefault;
+  if (cap > kPeelCapacityMax) return RT_ERR_TOO_LARGE;
+  RT_CUDA(cudaDeviceSynchronize());
+  dfree(g->d_plane_of_bin);
+  dfree(g->d_image);
+  dfree(g->d_nemit);
+  dfree(g->d_ev);
+  dfree(g->d_ev_bin);
+  dfree(g->d_nev);
+  dfree(g->d_iscratch);
+  g->iscratch_n = 0;
+  g->images = false;
+  rt_status st;
+  if ((st = dalloc(&g->d_plane_of_bin, (size_t)B)) != RT_OK ||
+      (st = dalloc(&g->d_image, n_img)) != RT_OK || (st = dalloc(&g->d_nemit, (size_t)B)) != RT_OK ||
+      (st = dalloc(&g->d_ev, (size_t)cap)) != RT_OK ||
+      (st = dalloc(&g->d_ev_bin, (size_t)cap)) != RT_OK || (st = dalloc(&g->d_nev, 1)) != RT_OK)
+    return st;
+  RT_CUDA(cudaMemset(g->d_nev, 0, sizeof(unsigned long long)));
+  RT_CUDA(cudaMemcpy(g->d_plane_of_bin, plane_of_bin, sizeof(int) * B, cudaMemcpyHostToDevice));
+  RT_CUDA(cudaMemset(g->d_image, 0, sizeof(double) * n_img));
+  RT_CUDA(cudaMemset(g->d_nemit, 0, sizeof(unsigned long long) * B));
+  // image axes: e1 = normalise(z x o) (x when o lies along z), e2 = o x e1
+  double o[3] = {d->obs_dir[0] / on, d->obs_dir[1] / on, d->obs_dir[2] / on};
+  double e1[3] = {1, 0, 0};
+  if (std::fabs(o[2]) < 0.999999) {
+    double nn = std::sqrt(o[0] * o[0] + o[1] * o[1]);
+    e1[0] = -o[1] / nn;
+    e1[1] = o[0] / nn;
+    e1[2] = 0;
+  }
+  double e2[3] = {o[1] * e1[2] - o[2] * e1[1], o[2] * e1[0] - o[0] * e1[2],
+                  o[0] * e1[1] - o[1] * e1[0]};
+  DevPeel& pe = g->peel;
+  pe = DevPeel{};
+  pe.plane_of_bin = g->d_plane_of_bin;
+  pe.image = g->d_image;
+  pe.n_emit = g->d_nemit;
+  pe.ev = g->d_ev;
+  pe.ev_bin = g->d_ev_bin;
+  pe.n_ev = g->d_nev;
+  pe.capacity = cap;
+  for (int a = 0; a < 3; ++a) {
+    pe.o[a] = (float)o[a];
+    pe.e1[a] = (float)e1[a];
+    pe.e2[a] = (float)e2[a];
+  }
+  pe.centre = (float)(0.5 * g->desc.n_base);
+  pe.sx = (float)(g->d0 * d->nx / (2.0 * d->half_width_cm));
+  pe.sy = (float)(g->d0 * d->ny / (2.0 * d->half_width_cm));
+  pe.nx = d->nx;
+  pe.ny = d->ny;
+  pe.n_planes = n_planes;
+  pe.tau_max = d->tau_max > 0 ? (float)d->tau_max : 40.0f;
+  g->images = true;
+  return RT_OK;
+}
+
+// Device output of n doubles: the caller's buffer, or the handle's scratch for a host copy.
+static double* image_buffer(rt_grid* g, double* out, int mem, size_t n, rt_status* st) {
+  *st = RT_OK;
+  if (mem == RT_MEM_DEVICE) return out;
+  if (g->iscratch_n < n) {
+    dfree(g->d_iscratch);
+    g->iscratch_n = 0;
+    if ((*st = dalloc(&g->d_iscratch, n)) != RT_OK) return nullptr;
+    g->iscratch_n = n;
+  }
+  return g->d_iscratch;
+}
+
+rt_status rt_images(rt_grid* g, double* out, int mem, void* stream) {
+  if (!g || !out) return RT_ERR_ARG;
+  if (!g->images) return RT_ERR_STATE;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  const size_t n = (size_t)g->peel.n_planes * g->peel.ny * g->peel.nx;
+  double* dst = image_buffer(g, out, mem, n, &st);
+  if (!dst) return st;
+  RT_CUDA(launch_image_out(g->d_image, (long long)n, g->eps, dst, s));
+  if (mem != RT_MEM_DEVICE) {
+    RT_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if ((st = sync_status(g, s)) != RT_OK) return st;
+    unsigned long long dropped = 0;
+    RT_CUDA(cudaMemcpy(&dropped, g->d_counters + kCPeelDropped, sizeof(dropped),
+                       cudaMemcpyDeviceToHost));
+    return dropped ? RT_ERR_RANGE : RT_OK;
+  }
+  return RT_OK;
+}
+
+rt_status rt_image_profile(rt_grid* g, int plane_a, int plane_b, int half_rows, double* out,
+                           int mem, void* stream) {
+  if (!g || !out) return RT_ERR_ARG;
+  if (!g->images) return RT_ERR_STATE;
+  const DevPeel& pe = g->peel;
+  if (plane_a < 0 || plane_a >= pe.n_planes || plane_b < -1 || plane_b >= pe.n_planes ||
+      half_rows < 0)
+    return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  double* dst = image_buffer(g, out, mem, (size_t)pe.nx, &st);
+  if (!dst) return st;
+  RT_CUDA(launch_image_profile(g->d_image, pe.nx, pe.ny, plane_a, plane_b, half_rows, g->eps,
+                               dst, s));
+  if (mem != RT_MEM_DEVICE) {
+    RT_CUDA(cudaMemcpyAsync(out, dst, sizeof(double) * pe.nx, cudaMemcpyDeviceToHost, s));
+    return sync_status(g, s);
+  }
+  return RT_OK;
 }
 
 rt_status rt_trace(rt_grid* g, const uint64_t* ids, int64_t n, uint64_t seed,
@@ -1200,6 +1382,7 @@ rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packag
   for (int m = 0; m < n && st == RT_OK; ++m) {
     rt_grid* g = grids[m];
     if (!g || g->dev != b->dev) { st = RT_ERR_ARG; break; }
+    if (g->images) { st = RT_ERR_STATE; break; }  // images need the single-model pool
     if ((st = build_tables(g, nullptr)) != RT_OK) break;
     if ((st = ensure_pathabs(g, o, nullptr)) != RT_OK) break;
     if (n_packages[m] > g->n_total) { st = RT_ERR_RANGE; break; }

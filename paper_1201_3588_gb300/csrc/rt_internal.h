@@ -20,7 +20,7 @@ constexpr unsigned kStatusTimeout = 2u;  // a launch ran past its time budget
 // Indices into the device counter array.
 enum Counter {
   kCEmitted = 0, kCEscaped, kCCapped, kCAbsorptions, kCScatters, kCCrossings,
-  kCErrors, kCClamped, kCLevels, kNumCounters
+  kCErrors, kCClamped, kCLevels, kCPeelEvents, kCPeelCrossings, kCPeelDropped, kNumCounters
 };
 
 // Face links of a leaf (record of 8 int32 per leaf: faces -x,+x,-y,+y,-z,+z, then
@@ -90,6 +90,34 @@ struct DevRun {
   unsigned long long budget_ns;
 };
 
+// Peel-off images toward a distant observer. Every scattering and re-emission at a
+// bin that has an image plane sends the share w of the package's energy per
+// steradian toward the observer (HG phase function value, or 1/(4 pi)), attenuated
+// by exp(-tau) along the sight line to the boundary, into the pixel its position
+// projects to. The transport launch only records these events (position, w, bin);
+// a second kernel traces their sight lines. Emissions by a point source are counted
+// per bin and peeled once per bin after the launch (they all start at the source).
+struct DevPeel {
+  const int* plane_of_bin;       // [B] image plane of each bin, -1 for none
+  double* image;                 // [n_planes][ny][nx] sums of w exp(-tau) (times eps: erg/s/sr)
+  unsigned long long* n_emit;    // [B] point-source emissions since the last source peel
+  float4* ev;                    // [capacity] recorded events: position (base units), w
+  int* ev_bin;                   // [capacity] their bins
+  unsigned long long* n_ev;      // events recorded by the current launch
+  unsigned long long capacity;
+  float o[3];                    // unit vector toward the observer
+  float e1[3], e2[3];            // image axes: e1 = normalise(z x o) (x when o ~ z), e2 = o x e1
+  float centre;                  // model centre, base-cube units
+  float sx, sy;                  // pixels per base-cube unit along e1, e2
+  int nx, ny, n_planes;
+  float tau_max;                 // sight lines stop (contribute nothing) beyond this depth
+};
+
+constexpr int kMaxImageSide = 16384;
+constexpr unsigned long long kPeelCapacityDefault = 1ull << 24;
+constexpr unsigned long long kPeelCapacityMax = 1ull << 31;
+constexpr size_t kMaxImagePixels = (size_t)1 << 28;  // all planes together (2 GiB of FP64)
+
 // One model of a batched launch, and one chunk of its packages.
 struct ModelDesc {
   DevGrid g;
@@ -108,7 +136,17 @@ cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* ch
                                    long long n_chunks, unsigned long long* next_chunk,
                                    int blocks_per_sm, cudaStream_t s);
 cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
-                                  int blocks_per_sm, int threads, cudaStream_t s);
+                                  int blocks_per_sm, int threads, cudaStream_t s,
+                                  const DevPeel* peel = nullptr);
+cudaError_t launch_peel_source(const DevGrid& g, const DevTables& t, const DevRun& r,
+                               const DevPeel& peel, cudaStream_t s);
+cudaError_t launch_peel_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
+                              const DevPeel& peel, cudaStream_t s);
+cudaError_t launch_image_out(const double* image, long long n, double scale, double* out,
+                             cudaStream_t s);
+cudaError_t launch_image_profile(const double* image, int nx, int ny, int plane_a,
+                                 int plane_b, int half_rows, double scale, double* out,
+                                 cudaStream_t s);
 cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const DevRun& r,
                                    bool fp64, int threads, cudaStream_t s);
 cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,

@@ -204,6 +204,7 @@ struct Pkg {
 struct Tally {  // per-thread counters, flushed to the 64-bit device totals
   unsigned emitted, escaped, capped, absorptions, scatters, crossings, errors, clamped;
   unsigned levels;  // child-table reads of the walk
+  unsigned peel_events, peel_crossings;  // peel-off sight lines and the cells they cross
 };
 
 // a flush is forced before any per-thread counter could pass 2^31
@@ -313,10 +314,13 @@ __device__ __forceinline__ int enter(const Pkg<float>& k, const DevGrid& g, Cell
 // One cell of the walk using the face links: the exit face follows from the
 // geometry alone, so the face link and the densities come from one record read;
 // the next leaf is the linked one (same size or coarser), or is found by a short
-// descent when the neighbouring region is finer.
+// descent when the neighbouring region is finer. kLos: a sight line, which never
+// interacts and adds the cell's optical depth to *tau_los instead.
+template <bool kLos = false>
 __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevGrid& g,
                                               const Kappa* kap,
-                                              unsigned& child_reads, float* pathabs) {
+                                              unsigned& child_reads, float* pathabs,
+                                              float* tau_los = nullptr) {
   // every array below is indexed with constants only, so it stays in registers
   const float sz = __int_as_float((127 - c.level) << 23);  // 2^-level
   const float lo0 = (float)c.I[0] * sz, lo1 = (float)c.I[1] * sz, lo2 = (float)c.I[2] * sz;
@@ -357,8 +361,14 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
     for (int s = 0; s < g.S; ++s) kx += __ldg(&rho[s]) * kb[s].kext;
   }
   const float dtau = kx * tex;
-  const bool hit = kx > 0.f && dtau > k.tau;
-  if (pathabs) {  // path-length tally of the segment inside this cell
+  bool hit;
+  if constexpr (kLos) {
+    *tau_los += dtau;
+    hit = false;
+  } else {
+    hit = kx > 0.f && dtau > k.tau;
+  }
+  if (!kLos && pathabs) {  // path-length tally of the segment inside this cell
     const float seg = hit ? k.tau / kx : tex;
     const float* rho = g.rho + (size_t)c.leaf * g.S;
     for (int s = 0; s < g.S; ++s) {
@@ -373,7 +383,7 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
     k.p[2] = fminf(hi2, fmaxf(lo2, k.p[2] + sd * d2));
     return kInteract;
   }
-  k.tau -= dtau;
+  if constexpr (!kLos) k.tau -= dtau;
   const float f0 = d0 > 0.f ? hi0 : lo0, f1 = d1 > 0.f ? hi1 : lo1, f2 = d2 > 0.f ? hi2 : lo2;
   k.p[0] = ax == 0 ? f0 : fminf(hi0, fmaxf(lo0, k.p[0] + tex * d0));
   k.p[1] = ax == 1 ? f1 : fminf(hi1, fmaxf(lo1, k.p[1] + tex * d1));
@@ -422,11 +432,23 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
   }
 }
 
+constexpr float kInv4Pi = 0.0795774715459476679f;  // 1 / (4 pi)
+
+// Henyey-Greenstein phase function per steradian at cos(angle) = mu.
+__device__ __forceinline__ float hg_per_sr(float g, float mu) {
+  const float den = fmaxf(1.f + g * g - 2.f * g * mu, 1e-30f);
+  return (1.f - g * g) * kInv4Pi / (den * sqrtf(den));
+}
+
 // Interaction part 1: draw the event's numbers; scatter completely, or pick the
 // absorbing species. Returns the species (>= 0) for an absorption, -1 for a scatter.
+// peel_o / peel_w (peel-off): for a scattering, *peel_w receives the phase function
+// per steradian toward the unit vector peel_o, at the direction before the turn.
 template <typename R>
 __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa* kap,
-                                        int leaf, const DevRun& r, uint4& w1) {
+                                        int leaf, const DevRun& r, uint4& w1,
+                                        const float* peel_o = nullptr,
+                                        float* peel_w = nullptr) {
   uint4 w0 = draw(r.seed, k.id, k.event, 0u);
   w1 = draw(r.seed, k.id, k.event, 1u);
   const float* rho = g.rho + (size_t)leaf * g.S;
@@ -448,6 +470,9 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
       cum += __ldg(&rho[s]) * kb[s].ksca;
       if (cum > target) { sp = s; break; }
     }
+    if (peel_w)
+      *peel_w = hg_per_sr(kb[sp].g, (float)k.d[0] * peel_o[0] + (float)k.d[1] * peel_o[1] +
+                                        (float)k.d[2] * peel_o[2]);
     R mu = hg_mu<R>((R)kb[sp].g, unit<R>(w0.z));
     turn<R>(k.d, mu, unit<R>(w0.w));
     set_inverse(k);
@@ -533,7 +558,8 @@ __device__ __forceinline__ int dir_bin(float dz, int n_dir) {
 __device__ __forceinline__ void flush_tally(Tally& tl, unsigned long long* c) {
   const unsigned v[kNumCounters] = {tl.emitted,   tl.escaped, tl.capped,
                                     tl.absorptions, tl.scatters, tl.crossings,
-                                    tl.errors,    tl.clamped, tl.levels};
+                                    tl.errors,    tl.clamped, tl.levels,
+                                    tl.peel_events, tl.peel_crossings};
 #pragma unroll
   for (int i = 0; i < kNumCounters; ++i) {
     unsigned long long x = v[i];
@@ -542,6 +568,125 @@ __device__ __forceinline__ void flush_tally(Tally& tl, unsigned long long* c) {
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&c[i], x);
   }
   tl = Tally{};
+}
+
+// ---------------------------------------------------------------- peel-off
+// Sight line from the point x (base-cube units) toward the observer at bin `bin`:
+// the pixel x projects to and the attenuation exp(-tau) to the boundary. Returns
+// false when x falls outside the image, tau passes pe.tau_max, or the walk fails
+// (then the tree status bit is set).
+__device__ __forceinline__ bool sight_line(const DevGrid& g, const Kappa* kap,
+                                           const DevPeel& pe, float x0, float x1, float x2,
+                                           int bin, float& att, size_t& pix,
+                                           unsigned& crossings, unsigned* status) {
+  const float r0 = x0 - pe.centre, r1 = x1 - pe.centre, r2 = x2 - pe.centre;
+  const float u = r0 * pe.e1[0] + r1 * pe.e1[1] + r2 * pe.e1[2];
+  const float v = r0 * pe.e2[0] + r1 * pe.e2[1] + r2 * pe.e2[2];
+  const int px = (int)floorf(u * pe.sx + 0.5f * (float)pe.nx);
+  const int py = (int)floorf(v * pe.sy + 0.5f * (float)pe.ny);
+  const int plane = __ldg(&pe.plane_of_bin[bin]);
+  if (plane < 0 || px < 0 || px >= pe.nx || py < 0 || py >= pe.ny) return false;
+  Pkg<float> k;
+  k.p[0] = x0;
+  k.p[1] = x1;
+  k.p[2] = x2;
+  k.d[0] = pe.o[0];
+  k.d[1] = pe.o[1];
+  k.d[2] = pe.o[2];
+  set_inverse(k);
+  k.bin = bin;
+  k.tau = 0.f;
+  Cell c;
+  unsigned lv = 0;
+  float tau = 0.f;
+  const int rc = locate<float>(g, k.p, k.d, c.leaf, c.level, c.I);
+  if (rc < 0) {
+    atomicOr(status, kStatusTree);
+    return false;
+  }
+  if (rc == 0) {
+    // a straight line crosses at most 3 n 2^L finest cells of the n^3 base grid
+    const long long cap = 3ll * ((long long)g.n_base << g.max_level) + 8;
+    for (long long i = 0;; ++i) {
+      const int a = advance_linked<true>(k, c, g, kap, lv, nullptr, &tau);
+      ++crossings;
+      if (a == kEscaped) break;
+      if (a == kError || i >= cap) {
+        atomicOr(status, kStatusTree);
+        return false;
+      }
+      if (tau > pe.tau_max) return false;
+    }
+  }
+  att = expf(-tau);
+  pix = ((size_t)plane * pe.ny + py) * pe.nx + px;
+  return true;
+}
+
+// Point-source emissions: all start at the source, so each bin's emissions of the
+// launch are peeled together, then its count is cleared.
+__global__ void k_peel_source(DevGrid g, DevTables t, DevRun r, DevPeel pe) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= g.B) return;
+  const unsigned long long n = pe.n_emit[b];
+  if (n == 0) return;
+  pe.n_emit[b] = 0;
+  if (r.source_kind == 1) return;
+  float att;
+  size_t pix;
+  unsigned cr = 0;
+  if (sight_line(g, t.kap, pe, r.src[0], r.src[1], r.src[2], b, att, pix, cr, r.status))
+    atomicAdd(&pe.image[pix], (double)n * (double)kInv4Pi * (double)att);
+  if (cr) atomicAdd(&r.counters[kCPeelCrossings], (unsigned long long)cr);
+}
+
+// The events a transport launch recorded: one sight line per thread (grid-stride).
+// Events beyond the buffer's capacity were not recorded; their number is added to
+// the dropped counter.
+__global__ void __launch_bounds__(256) k_peel_trace(DevGrid g, DevTables t, DevRun r,
+                                                    const __grid_constant__ DevPeel pe) {
+  const unsigned long long n_rec = *pe.n_ev;
+  const unsigned long long n = n_rec < pe.capacity ? n_rec : pe.capacity;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && n_rec > n)
+    atomicAdd(&r.counters[kCPeelDropped], n_rec - n);
+  unsigned cr = 0;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const float4 e = pe.ev[i];
+    const int bin = pe.ev_bin[i];
+    float att;
+    size_t pix;
+    if (sight_line(g, t.kap, pe, e.x, e.y, e.z, bin, att, pix, cr, r.status))
+      atomicAdd(&pe.image[pix], (double)(e.w * att));
+  }
+  unsigned long long x = cr;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  if ((threadIdx.x & 31) == 0 && x) atomicAdd(&r.counters[kCPeelCrossings], x);
+}
+
+__global__ void k_image_out(const double* image, long long n, double scale, double* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = image[i] * scale;
+}
+
+// Mean over the rows whose centres lie within half_rows pixels of the image's
+// centre line (|py + 1/2 - ny/2| <= half_rows) of plane a minus plane b (b < 0:
+// none), times scale; one thread per column.
+__global__ void k_image_profile(const double* image, int nx, int ny, int plane_a, int plane_b,
+                                int half_rows, double scale, double* out) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x;
+  if (px >= nx) return;
+  double sum = 0.0;
+  int rows = 0;
+  for (int py = 0; py < ny; ++py) {
+    if (fabs(py + 0.5 - 0.5 * ny) > (double)half_rows) continue;
+    double v = image[((size_t)plane_a * ny + py) * nx + px];
+    if (plane_b >= 0) v -= image[((size_t)plane_b * ny + py) * nx + px];
+    sum += v;
+    ++rows;
+  }
+  out[px] = rows ? sum * scale / rows : 0.0;
 }
 
 // ---------------------------------------------------------------- plain kernel
@@ -622,11 +767,16 @@ struct RangeIds {
 // with most lanes active. Each package's history is unchanged by this schedule.
 // Absorptions of lanes hitting the same (species, cell) in one phase are merged into
 // one atomic. `sed` is the escaped-spectrum histogram (shared or global memory).
-template <class Ids>
+// kPeel: scatterings and re-emissions at image bins are recorded (position, w,
+// bin) in the peel-off event buffer, one slot range per warp and phase; point-source
+// emissions are counted per bin in s_nemit.
+template <bool kPeel, class Ids>
 __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, const DevRun& r,
                                           const Kappa* kap, const float* star_cdf,
                                           unsigned long long* sed, unsigned long long n_end,
-                                          Ids& ids, Tally& tl, unsigned long long t0) {
+                                          Ids& ids, Tally& tl, unsigned long long t0,
+                                          const DevPeel* pe = nullptr,
+                                          unsigned long long* s_nemit = nullptr) {
   const int B = g.B;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -648,6 +798,9 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
         if (j < n_end) {
           emit<float>(k, r.first_id + j, r, star_cdf, B);
           ++tl.emitted;
+          if constexpr (kPeel) {
+            if (r.source_kind != 1) atomicAdd(&s_nemit[k.bin], 1ull);
+          }
           const int rc = enter(k, g, cell, tl.levels);
           if (rc == 0) {
             alive = true;
@@ -702,14 +855,22 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
       int sp = -1;
       uint4 w1 = make_uint4(0, 0, 0, 0);
       bool absorbing = false;
+      bool scattered = false;
+      float wv = kInv4Pi;  // peel-off weight per steradian of this lane's event
       if (pending) {
         pending = false;
         if (++k.event > r.max_events) {
           ++tl.capped;
           alive = false;
         } else {
-          sp = interact<float>(k, g, kap, cell.leaf, r, w1);
-          if (sp < 0) ++tl.scatters; else absorbing = true;
+          sp = interact<float>(k, g, kap, cell.leaf, r, w1, kPeel ? pe->o : nullptr,
+                               kPeel ? &wv : nullptr);
+          if (sp < 0) {
+            ++tl.scatters;
+            scattered = true;
+          } else {
+            absorbing = true;
+          }
         }
       }
       const unsigned am = __ballot_sync(kFull, absorbing);
@@ -729,6 +890,25 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
                         w1, tl);
         ++tl.absorptions;
       }
+      if constexpr (kPeel) {
+        // the event's share toward the observer, at the bin it leaves with
+        const bool ev = (scattered || absorbing) && __ldg(&pe->plane_of_bin[k.bin]) >= 0;
+        const unsigned em = __ballot_sync(kFull, ev);
+        if (em) {
+          const int leader = __ffs(em) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(pe->n_ev, (unsigned long long)__popc(em));
+          base = __shfl_sync(kFull, base, leader);
+          if (ev) {
+            const unsigned long long slot = base + __popc(em & lt_mask);
+            if (slot < pe->capacity) {
+              pe->ev[slot] = make_float4(k.p[0], k.p[1], k.p[2], wv);
+              pe->ev_bin[slot] = k.bin;
+            }
+            ++tl.peel_events;
+          }
+        }
+      }
     }
   }
 }
@@ -737,9 +917,9 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
 // Persistent packet pool over one model: all warps draw package indices from one
 // global counter; the opacity table, the stellar CDF and (when it fits) the
 // escaped-spectrum histogram live in shared memory.
-template <int kMinBlocks>
+template <int kMinBlocks, bool kPeel>
 __global__ void __launch_bounds__(256, kMinBlocks)
-    k_transport_pool(DevGrid g, DevTables t, DevRun r) {
+    k_transport_pool(DevGrid g, DevTables t, DevRun r, const __grid_constant__ DevPeel pe) {
   extern __shared__ unsigned long long smem_u64[];
   const int S = g.S, B = g.B;
   const int n_sed = 2 * g.n_dir * B;
@@ -751,15 +931,27 @@ __global__ void __launch_bounds__(256, kMinBlocks)
     for (int i = threadIdx.x; i < n_sed; i += blockDim.x) s_sed[i] = 0ull;
   for (int i = threadIdx.x; i < B * S; i += blockDim.x) s_kap[i] = t.kap[i];
   for (int i = threadIdx.x; i < B; i += blockDim.x) s_cdf[i] = t.star_cdf[i];
+  // peel-off: the block's point-source emission counts per bin
+  unsigned long long* s_nemit = nullptr;
+  if constexpr (kPeel) {
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(s_cdf + B) + 15) & ~(uintptr_t)15;
+    s_nemit = reinterpret_cast<unsigned long long*>(a);
+    for (int i = threadIdx.x; i < B; i += blockDim.x) s_nemit[i] = 0ull;
+  }
   __syncthreads();
   Tally tl = {};
   GlobalIds ids{r.next};
-  pool_warp(g, t, r, s_kap, s_cdf, s_sed, r.n_packages, ids, tl, global_ns());
+  pool_warp<kPeel>(g, t, r, s_kap, s_cdf, s_sed, r.n_packages, ids, tl, global_ns(), &pe,
+                   s_nemit);
   flush_tally(tl, r.counters);
+  if (sed_local || kPeel) __syncthreads();
   if (sed_local) {
-    __syncthreads();
     for (int i = threadIdx.x; i < n_sed; i += blockDim.x)
       if (s_sed[i]) atomicAdd(&r.sed[i], s_sed[i]);
+  }
+  if constexpr (kPeel) {
+    for (int i = threadIdx.x; i < B; i += blockDim.x)
+      if (s_nemit[i]) atomicAdd(&pe.n_emit[i], s_nemit[i]);
   }
 }
 
@@ -788,8 +980,8 @@ __global__ void __launch_bounds__(256) k_transport_batch(const ModelDesc* models
     const ModelDesc& md = sdesc[warp];
     Tally tl = {};
     RangeIds ids{ch.first};
-    pool_warp(md.g, md.t, md.r, md.t.kap, md.t.star_cdf, md.r.sed, ch.first + ch.count, ids, tl,
-              t0);
+    pool_warp<false>(md.g, md.t, md.r, md.t.kap, md.t.star_cdf, md.r.sed, ch.first + ch.count,
+                     ids, tl, t0);
     flush_tally(tl, md.r.counters);
     __syncwarp();
   }
@@ -905,43 +1097,85 @@ static size_t sed_smem(const DevGrid& g) {
   return sizeof(unsigned long long) * 2 * g.n_dir * g.B;
 }
 
-template <int kMinBlocks>
+static size_t peel_smem(const DevGrid& g) { return 16 + sizeof(unsigned long long) * g.B; }
+
+template <int kMinBlocks, bool kPeel>
 static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, const DevRun& r,
-                                       int blocks_per_sm, int threads, int sms, cudaStream_t s) {
+                                       const DevPeel& pe, int blocks_per_sm, int threads,
+                                       int sms, cudaStream_t s) {
   DevRun rr = r;
-  rr.sed_in_smem = table_smem(g) + sed_smem(g) <= kSmemBudget ? 1 : 0;
-  size_t sm = table_smem(g) + (rr.sed_in_smem ? sed_smem(g) : 0);
+  const size_t extra = kPeel ? peel_smem(g) : 0;
+  rr.sed_in_smem = table_smem(g) + extra + sed_smem(g) <= kSmemBudget ? 1 : 0;
+  size_t sm = table_smem(g) + extra + (rr.sed_in_smem ? sed_smem(g) : 0);
   cudaError_t e;
   if (sm > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_transport_pool<kMinBlocks>,
+    e = cudaFuncSetAttribute(k_transport_pool<kMinBlocks, kPeel>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_pool<kMinBlocks>, threads,
-                                                    sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_pool<kMinBlocks, kPeel>,
+                                                    threads, sm);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   int bps = blocks_per_sm > 0 ? (blocks_per_sm < occ ? blocks_per_sm : occ) : occ;
-  k_transport_pool<kMinBlocks><<<sms * bps, threads, sm, s>>>(g, t, rr);
+  k_transport_pool<kMinBlocks, kPeel><<<sms * bps, threads, sm, s>>>(g, t, rr, pe);
   return cudaGetLastError();
 }
 
 // blocks_per_sm selects the register budget: 5 or 6 resident blocks of 256 threads
 // use variants compiled for that occupancy (fewer registers, some spills); other
 // values use the 4-block variant (no spills), capped at its occupancy.
+// With peel-off images the 4-block variant is used.
 cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
-                                  int blocks_per_sm, int threads, cudaStream_t s) {
+                                  int blocks_per_sm, int threads, cudaStream_t s,
+                                  const DevPeel* peel) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  if (peel) return launch_pool_variant<4, true>(g, t, r, *peel, blocks_per_sm, threads, sms, s);
+  const DevPeel none{};
   if (threads == 256 && blocks_per_sm == 6)
-    return launch_pool_variant<6>(g, t, r, blocks_per_sm, threads, sms, s);
+    return launch_pool_variant<6, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
   if (threads == 256 && blocks_per_sm == 5)
-    return launch_pool_variant<5>(g, t, r, blocks_per_sm, threads, sms, s);
-  return launch_pool_variant<4>(g, t, r, blocks_per_sm, threads, sms, s);
+    return launch_pool_variant<5, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
+  return launch_pool_variant<4, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
+}
+
+cudaError_t launch_peel_source(const DevGrid& g, const DevTables& t, const DevRun& r,
+                               const DevPeel& peel, cudaStream_t s) {
+  k_peel_source<<<(g.B + 127) / 128, 128, 0, s>>>(g, t, r, peel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_peel_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
+                              const DevPeel& peel, cudaStream_t s) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peel_trace, 256, 0);
+  if (e != cudaSuccess) return e;
+  k_peel_trace<<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(g, t, r, peel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_out(const double* image, long long n, double scale, double* out,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_image_out<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(image, n, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_profile(const double* image, int nx, int ny, int plane_a,
+                                 int plane_b, int half_rows, double scale, double* out,
+                                 cudaStream_t s) {
+  k_image_profile<<<(nx + 127) / 128, 128, 0, s>>>(image, nx, ny, plane_a, plane_b, half_rows,
+                                                    scale, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const DevRun& r,

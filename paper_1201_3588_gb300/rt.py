@@ -54,7 +54,14 @@ class _Opts(C.Structure):
 class _Counters(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("emitted", "escaped", "capped", "absorptions",
                                           "scatters", "crossings", "errors", "clamped",
-                                          "levels")]
+                                          "levels", "peel_events", "peel_crossings",
+                                          "peel_dropped")]
+
+
+class _ImageDesc(C.Structure):
+    _fields_ = [("obs_dir", C.c_double * 3), ("nx", C.c_int32), ("ny", C.c_int32),
+                ("half_width_cm", C.c_double), ("tau_max", C.c_double),
+                ("event_capacity", C.c_uint64)]
 
 
 _lib = None
@@ -78,6 +85,10 @@ SIGNATURES = {
     "rt_pathlength": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "rt_set_counts": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "rt_get_counters": [C.c_void_p, C.POINTER(_Counters)],
+    "rt_set_images": [C.c_void_p, C.POINTER(_ImageDesc), C.c_void_p],
+    "rt_images": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_image_profile": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                         C.c_void_p],
     "rt_trace": [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p],
     "rt_philox": [C.c_void_p, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p],
     "rt_status_string": [C.c_int],
@@ -314,6 +325,41 @@ class Grid:
         _check(load().rt_pah_training_pairs(self._h, int(pah), int(first), n, X.data_ptr(),
                                             Y.data_ptr(), p_abs.data_ptr(), _stream(stream)),
                "rt_pah_training_pairs")
+
+    image_shape = (0, 0, 0)
+
+    def set_images(self, obs_dir, plane_of_bin, nx: int, ny: int, half_width_cm: float,
+                   tau_max: float = 0.0, event_capacity: int = 0):
+        """Peel-off images toward `obs_dir`; plane_of_bin[b] = image plane of bin b or -1.
+        None for plane_of_bin removes the images."""
+        if plane_of_bin is None:
+            _check(load().rt_set_images(self._h, None, None), "rt_set_images")
+            self.n_planes = 0
+            self.image_shape = (0, 0, 0)
+            return
+        pob = np.ascontiguousarray(plane_of_bin, dtype=np.int32)
+        d = _ImageDesc(obs_dir=(C.c_double * 3)(*[float(x) for x in obs_dir]), nx=int(nx),
+                       ny=int(ny), half_width_cm=float(half_width_cm), tau_max=float(tau_max),
+                       event_capacity=int(event_capacity))
+        _check(load().rt_set_images(self._h, C.byref(d), pob.ctypes.data), "rt_set_images")
+        self.n_planes = int(pob.max()) + 1
+        self.image_shape = (self.n_planes, int(ny), int(nx))
+
+    def images(self, out=None, stream=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros(self.image_shape, dtype=np.float64)
+        p, mem = _ptr_mem(out)
+        _check(load().rt_images(self._h, p, mem, _stream(stream)), "rt_images")
+        return out
+
+    def image_profile(self, plane_a: int, plane_b: int = -1, half_rows: int = 0, out=None,
+                      stream=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros(max(self.image_shape[2], 1), dtype=np.float64)
+        p, mem = _ptr_mem(out)
+        _check(load().rt_image_profile(self._h, int(plane_a), int(plane_b), int(half_rows), p,
+                                       mem, _stream(stream)), "rt_image_profile")
+        return out
 
     def counters(self) -> dict:
         c = _Counters()
