@@ -51,7 +51,8 @@ class _Model(C.Structure):
                 ("star_L", C.c_double), ("star_pos", C.c_double * 3),
                 ("source_kind", C.c_int32), ("n_sed_dirs", C.c_int32),
                 ("beam_dir", C.c_double * 3), ("pah_index", C.c_void_p),
-                ("pah_template", C.c_void_p), ("n_coarse", C.c_int32), ("n_pah", C.c_int32)]
+                ("pah_template", C.c_void_p), ("n_coarse", C.c_int32), ("n_pah", C.c_int32),
+                ("pah_cell_w", C.c_void_p)]
 
 
 class _Run(C.Structure):
@@ -174,9 +175,11 @@ N_COARSE = 64
 
 class OracleModel:
     """ctypes view of a ``workloads.Model`` (arrays kept alive here). For PAH species
-    the template re-emission spectra come from ``oracle.pah`` unless given."""
+    the template re-emission spectra come from ``oracle.pah`` unless given;
+    ``pah_cell_spectra`` [n_pah][N][B] gives each cell its own PAH re-emission
+    spectrum (rows of zeros: the template)."""
 
-    def __init__(self, model, pah_template=None):
+    def __init__(self, model, pah_template=None, pah_cell_spectra=None):
         t = model.tree
         self.model = model
         self.base = np.ascontiguousarray(t.base, dtype=np.int32)
@@ -201,6 +204,10 @@ class OracleModel:
                                                             st.T) for i in self.pah_species])
         self.pah_template = (np.ascontiguousarray(pah_template, dtype=np.float64)
                              if self.n_pah else np.zeros(1))
+        self.pah_cell = None
+        if pah_cell_spectra is not None:
+            self.pah_cell = np.ascontiguousarray(pah_cell_spectra, dtype=np.float64).reshape(
+                self.n_pah, t.n_leaves, model.n_bins)
         self.s = _Model(half_size=model.half_size, n_base=t.n_base, max_level=t.max_level,
                         base=_ptr(self.base), child=_ptr(self.child), n_blocks=t.n_blocks,
                         n_leaves=t.n_leaves, n_species=model.n_species,
@@ -211,7 +218,8 @@ class OracleModel:
                         beam_dir=(C.c_double * 3)(*st.beam_dir),
                         pah_index=_ptr(self.pah_index) if self.n_pah else None,
                         pah_template=_ptr(self.pah_template), n_coarse=self.n_coarse,
-                        n_pah=self.n_pah)
+                        n_pah=self.n_pah,
+                        pah_cell_w=_ptr(self.pah_cell) if self.pah_cell is not None else None)
 
     @property
     def S(self):

@@ -662,12 +662,21 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
                 if (pa >= 0) {
                     /* PAH: the absorbed photon goes to the cell's coarse absorbed
                      * spectrum; the package leaves at a frequency from the PAH's
-                     * template emission spectrum */
+                     * emission spectrum in this cell (its template unless a
+                     * per-cell spectrum is given) */
                     if (t && t->pahabs) {
                         int kc = (int)(((int64_t)bin * m->n_coarse) / B);
                         t->pahabs[((size_t)pa * N + leaf) * m->n_coarse + kc] += 1;
                     }
-                    bin = sample_discrete(m->pah_template + (size_t)pa * B, B, v[2]);
+                    const double *wrow = m->pah_template + (size_t)pa * B;
+                    if (m->pah_cell_w) {
+                        /* the cell's own PAH emission spectrum, where one is given */
+                        const double *cw = m->pah_cell_w + ((size_t)pa * N + leaf) * B;
+                        double tot = 0.0;
+                        for (int b = 0; b < B; ++b) tot += cw[b];
+                        if (tot > 0.0) wrow = cw;
+                    }
+                    bin = sample_discrete(wrow, B, v[2]);
                     peel(m, r, c, t, p, bin, 1.0 / (4.0 * PI));
                     isotropic(u[2], u[3], d);
                     ++n_abs;

@@ -45,6 +45,9 @@ typedef struct {
     const int32_t *pah_index;  /* [S] or NULL */
     const double *pah_template;/* [n_pah][B] */
     int32_t n_coarse, n_pah;
+    /* per-cell PAH re-emission spectra (may be absent): [n_pah][N][B] weights; a
+     * cell whose row sums to zero re-emits from the template */
+    const double *pah_cell_w;
 } orc_model;
 
 typedef struct {
