@@ -74,12 +74,14 @@ def coarse_photon_energy(nu_edges, n_coarse: int = 64):
     return e
 
 
-def level_tables(sigma_mol, modes, nu_edges, n_levels=400, t_top=2500.0):
+def level_tables(sigma_mol, modes, nu_edges, n_levels=400, t_top=2500.0, e_photon=None):
     """Energy levels E_f = f dE (dE = E_max/(n_levels-1), E_max = E(t_top) plus the
-    largest photon energy of the grid), their temperatures, cooling rates L_f and
-    per-bin emission s_fb = 4 pi sigma_b P_b(T_f) (erg/s per molecule)."""
+    largest photon energy: that of the grid, or `e_photon` when given), their
+    temperatures, cooling rates L_f and per-bin emission s_fb = 4 pi sigma_b P_b(T_f)
+    (erg/s per molecule)."""
     B = len(nu_edges) - 1
-    e_max = float(internal_energy(t_top, modes)) + H * nu_edges[-1]
+    e_top = H * nu_edges[-1] if e_photon is None else float(e_photon)
+    e_max = float(internal_energy(t_top, modes)) + e_top
     E = np.linspace(0.0, e_max, n_levels)
     T = np.array([temperature_of_energy(x, modes) for x in E])
     s = np.zeros((n_levels, B))
@@ -203,3 +205,20 @@ def template_spectrum(species, nu_edges, T_star, flux=F_REF, n_levels=400, t_top
     P, _ = populations(R, e, tab)
     J = emission(P, tab)
     return J / J.sum()
+
+
+def temperature_distribution(modes, sigma_mol, nu_edges, h_nu, flux, sigma_line,
+                             n_levels=400, t_top=2500.0, t_sub=2500.0):
+    """P(T) of a PAH in a monochromatic field (Fig. 3): photons of energy h_nu (erg)
+    at flux `flux` (erg/s/cm^2), absorbed with cross section sigma_line (cm^2) at the
+    rate R = sigma_line flux / h_nu; levels span 0 .. E(t_top) + h_nu; cooling by the
+    cross sections sigma_mol on the frequency grid. Returns the populations P_f, the
+    level temperatures, the time fraction spent above t_sub (the shaded region of
+    Fig. 3: hotter than graphite sublimates), the emission per bin and R."""
+    tab = level_tables(sigma_mol, modes, nu_edges, n_levels=n_levels, t_top=t_top,
+                       e_photon=h_nu)
+    R = sigma_line * flux / h_nu
+    P, truncated = populations(np.array([R]), np.array([h_nu]), tab)
+    return dict(P=P, T=tab["T"], E=tab["E"], L=tab["L"],
+                p_above=float(P[tab["T"] > t_sub].sum()), emission=emission(P, tab),
+                rate=R, truncated=truncated, dE=tab["dE"])
