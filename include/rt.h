@@ -312,6 +312,49 @@ rt_status rt_pah_emission(rt_grid *g, int64_t first_cell, int64_t n_cells, int p
                           const rt_mlp *surrogate, float tol, float *j_out, int mem,
                           uint64_t *n_fallback_out, void *stream);
 
+/* Per-cell PAH re-emission spectra, the step that couples the PAH emission back
+ * into the transport (Sec. 2: PAH treatment in the Monte Carlo scheme; iterate
+ * transport -> rt_pah_emission -> this call -> transport). Rows J [n_cells][n_bins]
+ * (erg/s per bin, e.g. rt_pah_emission's output for PAH number `pah`; negative
+ * entries count as 0) for cells first_cell .. first_cell+n_cells-1: afterwards a
+ * package absorbed by that PAH in such a cell leaves at a bin drawn with
+ * probabilities proportional to the cell's row; cells whose row has nothing
+ * positive, and cells never set, keep the template spectrum. The spectra stay set
+ * until replaced; J == NULL removes them for every PAH. Allocates n_pah x n_leaves x
+ * n_bins floats on first use. mem: where J lives; host rows synchronise. */
+rt_status rt_set_pah_spectra(rt_grid *g, int pah, int64_t first_cell, int64_t n_cells,
+                             const float *J, int mem, void *stream);
+
+/* Temperature distribution P(T) of PAH molecules in a monochromatic radiation field
+ * (Sec. 3, Fig. 3: a PAH exposed to photons of 3.8 eV .. 1 keV at a fixed flux), and
+ * how long they stay hotter than graphite sublimates (Sec. 4: hard photons destroy
+ * PAHs). For every case: internal-energy levels E_f = f dE, f = 0 .. n_levels-1, up
+ * to E(t_top) + h_nu (E(T) from Einstein mode groups); absorptions at `rate` move a
+ * molecule from E_i to E_i + h_nu (split over the two levels around it so that the
+ * energy is kept; cut at the top level); cooling L(E) = 4 pi sum_b sigma_b P_b(T(E))
+ * over the frequency grid, a step down at rate L/dE; the steady state follows level
+ * by level (the same thermal-discrete solution as rt_pah_emission). Outputs (host):
+ * P_out, T_out [n_cases][n_levels] normalised populations and level temperatures;
+ * p_above_out [n_cases] the time fraction spent above t_sub; emission_out
+ * [n_cases][n_bins] the emitted power per bin, erg/s per molecule (its sum equals
+ * rate * h_nu up to the energy cut at the top). Inputs: nu_edges [n_bins+1] (Hz,
+ * increasing), sigma [n_cases][n_bins] absorption cross sections per molecule (cm^2),
+ * n_levels 16..4096. One GPU block per case; allocates and frees its device arrays;
+ * synchronises. */
+typedef struct rt_pah_pt_case {
+    double modes[4][2];     /* mode groups: (number of modes, Einstein temperature K) */
+    int32_t n_groups;       /* 1..4 */
+    int32_t reserved;
+    double h_nu_erg;        /* photon energy of the field */
+    double rate;            /* absorbed photons per molecule per second (sigma F / h_nu) */
+    double t_top;           /* levels reach E(t_top) + h_nu (0: 2500 K) */
+} rt_pah_pt_case;
+rt_status rt_pah_temperature_distribution(const rt_pah_pt_case *cases, int n_cases,
+                                          const double *nu_edges, int n_bins,
+                                          const double *sigma, int n_levels, double t_sub,
+                                          double *P_out, double *T_out, double *p_above_out,
+                                          double *emission_out, void *stream);
+
 /* Training pairs for the surrogate, PAH number `pah`, cells first_cell ..: features
  * X [n][n_coarse+2] (x_k = ln(a_k + 1e-4)/4.6 + 1 for the fraction a_k of absorbed
  * photons in coarse bin k; (log10(P_abs/N_molecules) + 12)/4; log10(N_C) - 2), exact

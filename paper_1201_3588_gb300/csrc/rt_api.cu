@@ -60,6 +60,7 @@ struct rt_grid {
   int* d_pah_qk = nullptr;
   double* d_pah_wk = nullptr;
   float* d_pah_cdf = nullptr;
+  float* d_pah_cell_cdf = nullptr;  // [n_pah][N][B] per-cell re-emission spectra
   unsigned* d_pahabs = nullptr;
   float* d_pathabs = nullptr;  // path-length tallies [S][N]
   // peel-off images
@@ -184,6 +185,7 @@ void free_all(rt_grid* g) {
   dfree(g->d_ev_bin);
   dfree(g->d_nev);
   dfree(g->d_iscratch);
+  dfree(g->d_pah_cell_cdf);
   dfree(g->d_jscratch);
   dfree(g->d_sx);
   dfree(g->d_sy);
@@ -826,6 +828,7 @@ rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
   if ((st = fill_run(g, n_packages, seed, first_package_id, o, &r)) != RT_OK) return st;
   DevTables t = g->tab;
   t.u_frozen = g->d_ufrozen;
+  t.pah_cell_cdf = g->d_pah_cell_cdf;
   if (g->images && kernel != RT_KERNEL_POOL) return RT_ERR_STATE;
   if (kernel == RT_KERNEL_POOL) {
     RT_CUDA(cudaMemsetAsync(g->d_next, 0, sizeof(unsigned long long), s));
@@ -1124,6 +1127,7 @@ rt_status rt_trace(rt_grid* g, const uint64_t* ids, int64_t n, uint64_t seed,
   if ((st = fill_run(g, 0, seed, 0, &o, &r)) != RT_OK) return st;
   DevTables t = g->tab;
   t.u_frozen = g->d_ufrozen;
+  t.pah_cell_cdf = g->d_pah_cell_cdf;
   unsigned long long* d_ids = nullptr;
   long long* d_out = nullptr;
   if ((st = dalloc(&d_ids, (size_t)n)) != RT_OK) return st;
@@ -1184,6 +1188,129 @@ rt_status rt_pah_absorbed(rt_grid* g, uint32_t* out, int mem, void* stream) {
                           s));
   if (mem != RT_MEM_DEVICE) return sync_status(g, s);
   return RT_OK;
+}
+
+rt_status rt_set_pah_spectra(rt_grid* g, int pah, int64_t first_cell, int64_t n_cells,
+                             const float* J, int mem, void* stream) {
+  if (!g) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  if (!J) {  // back to the templates everywhere
+    if (g->d_pah_cell_cdf) {
+      RT_CUDA(cudaStreamSynchronize(s));
+      RT_CUDA(cudaDeviceSynchronize());
+      dfree(g->d_pah_cell_cdf);
+    }
+    return RT_OK;
+  }
+  rt_status st = build_tables(g, s);
+  if (st != RT_OK) return st;
+  const long long N = g->desc.n_leaves;
+  const int B = g->desc.n_bins;
+  if (g->n_pah == 0) return RT_ERR_STATE;
+  if (pah < 0 || pah >= g->n_pah || first_cell < 0 || n_cells < 0 || first_cell > N ||
+      n_cells > N - first_cell)
+    return RT_ERR_ARG;
+  if (!g->d_pah_cell_cdf) {
+    const size_t n = (size_t)g->n_pah * N * B;
+    if ((st = dalloc(&g->d_pah_cell_cdf, n)) != RT_OK) return st;
+    RT_CUDA(cudaMemsetAsync(g->d_pah_cell_cdf, 0, sizeof(float) * n, s));
+  }
+  float* dst = g->d_pah_cell_cdf + ((size_t)pah * N + first_cell) * B;
+  if (mem == RT_MEM_DEVICE) {
+    RT_CUDA(launch_pah_cell_cdf(J, n_cells, B, dst, s));
+    return RT_OK;
+  }
+  // host rows: through the handle's scratch, a chunk at a time
+  const long long chunk = n_cells < (1ll << 18) ? n_cells : (1ll << 18);
+  if (g->jscratch_n < (size_t)chunk * B) {
+    RT_CUDA(cudaStreamSynchronize(s));
+    dfree(g->d_jscratch);
+    g->jscratch_n = 0;
+    if ((st = dalloc(&g->d_jscratch, (size_t)chunk * B)) != RT_OK) return st;
+    g->jscratch_n = (size_t)chunk * B;
+  }
+  for (long long c0 = 0; c0 < n_cells; c0 += chunk) {
+    const long long nc = n_cells - c0 < chunk ? n_cells - c0 : chunk;
+    RT_CUDA(cudaMemcpyAsync(g->d_jscratch, J + (size_t)c0 * B, sizeof(float) * nc * B,
+                            cudaMemcpyHostToDevice, s));
+    RT_CUDA(launch_pah_cell_cdf(g->d_jscratch, nc, B, dst + (size_t)c0 * B, s));
+  }
+  return sync_status(g, s);
+}
+
+rt_status rt_pah_temperature_distribution(const rt_pah_pt_case* cases, int n_cases,
+                                           const double* nu_edges, int n_bins,
+                                           const double* sigma, int n_levels, double t_sub,
+                                           double* P_out, double* T_out, double* p_above_out,
+                                           double* emission_out, void* stream) {
+  if (!cases || !nu_edges || !sigma || !P_out || !T_out || !p_above_out || !emission_out)
+    return RT_ERR_ARG;
+  if (n_cases < 1 || n_cases > 65535 || n_bins < 1 || n_bins > kMaxBins || n_levels < 16 ||
+      n_levels > 4096 || !(t_sub >= 0) || !std::isfinite(t_sub))
+    return RT_ERR_ARG;
+  for (int b = 0; b <= n_bins; ++b)
+    if (!(nu_edges[b] > 0) || !std::isfinite(nu_edges[b]) || (b > 0 && !(nu_edges[b] > nu_edges[b - 1])))
+      return RT_ERR_ARG;
+  std::vector<PtCase> pc((size_t)n_cases);
+  for (int i = 0; i < n_cases; ++i) {
+    const rt_pah_pt_case& c = cases[i];
+    if (c.n_groups < 1 || c.n_groups > kMaxModeGroups || !(c.h_nu_erg > 0) ||
+        !std::isfinite(c.h_nu_erg) || !(c.rate >= 0) || !std::isfinite(c.rate) ||
+        !(c.t_top >= 0) || !std::isfinite(c.t_top))
+      return RT_ERR_ARG;
+    PtCase& d = pc[(size_t)i];
+    d = PtCase{};
+    d.spec.n_groups = c.n_groups;
+    for (int k = 0; k < c.n_groups; ++k) {
+      if (!(c.modes[k][0] > 0) || !(c.modes[k][1] > 0)) return RT_ERR_ARG;
+      d.spec.n_modes[k] = c.modes[k][0];
+      d.spec.theta[k] = c.modes[k][1];
+    }
+    d.h_nu = c.h_nu_erg;
+    d.rate = c.rate;
+    d.t_top = c.t_top > 0 ? c.t_top : 2500.0;
+  }
+  for (size_t i = 0; i < (size_t)n_cases * n_bins; ++i)
+    if (!(sigma[i] >= 0) || !std::isfinite(sigma[i])) return RT_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  const size_t nP = (size_t)n_cases * n_levels, nE = (size_t)n_cases * n_bins;
+  PtCase* d_cases = nullptr;
+  double *d_nu = nullptr, *d_sig = nullptr, *d_P = nullptr, *d_T = nullptr, *d_a = nullptr,
+         *d_em = nullptr;
+  rt_status st = RT_OK;
+  if ((st = dalloc(&d_cases, (size_t)n_cases)) == RT_OK &&
+      (st = dalloc(&d_nu, (size_t)n_bins + 1)) == RT_OK && (st = dalloc(&d_sig, nE)) == RT_OK &&
+      (st = dalloc(&d_P, nP)) == RT_OK && (st = dalloc(&d_T, nP)) == RT_OK &&
+      (st = dalloc(&d_a, (size_t)n_cases)) == RT_OK && (st = dalloc(&d_em, nE)) == RT_OK) {
+    cudaError_t e = cudaMemcpyAsync(d_cases, pc.data(), sizeof(PtCase) * n_cases,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_nu, nu_edges, sizeof(double) * (n_bins + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_sig, sigma, sizeof(double) * nE, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_pah_pt(d_cases, n_cases, d_nu, n_bins, d_sig, n_levels, t_sub, d_P, d_T, d_a,
+                        d_em, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P_out, d_P, sizeof(double) * nP, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(T_out, d_T, sizeof(double) * nP, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p_above_out, d_a, sizeof(double) * n_cases, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(emission_out, d_em, sizeof(double) * nE, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    st = cuda_status(e);
+  }
+  dfree(d_cases);
+  dfree(d_nu);
+  dfree(d_sig);
+  dfree(d_P);
+  dfree(d_T);
+  dfree(d_a);
+  dfree(d_em);
+  return st;
 }
 
 // Work arrays of rt_pah_emission for `chunk` cells: cell lists always, the
@@ -1393,6 +1520,7 @@ rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packag
     desc[(size_t)m].g = g->g;
     desc[(size_t)m].t = g->tab;
     desc[(size_t)m].t.u_frozen = g->d_ufrozen;
+    desc[(size_t)m].t.pah_cell_cdf = g->d_pah_cell_cdf;
     desc[(size_t)m].r = r;
     b->grids.push_back(g);
     b->n_pk.push_back(n_packages[m]);

@@ -62,6 +62,8 @@ struct DevTables {
   float u_inv[kMaxSpecies];   // (n_T - 1) / (ln S_s(T_last) - ln S_s(T_1))
   const float* u_frozen;      // [S][n_leaves] (frozen mode) or null
   const float* pah_cdf;       // [n_pah][B] template re-emission spectrum of each PAH
+  const float* pah_cell_cdf;  // [n_pah][n_leaves][B] per-cell PAH re-emission spectra
+                              // (normalised cumulative; last entry 0: the template), or null
   int pah_of[kMaxSpecies];    // PAH number of each species, -1 for grains
   int n_coarse;               // coarse bins of the PAH absorbed spectrum
   float u_tmin[kMaxSpecies];  // S_s(t_min)
@@ -236,6 +238,18 @@ cudaError_t launch_compact(const PahTables& t, const unsigned* pahabs, long long
                            const int* list, int* out, unsigned* count, cudaStream_t s);
 cudaError_t launch_count_flags(const unsigned char* flag, long long n, unsigned long long* out,
                                cudaStream_t s);
+cudaError_t launch_pah_cell_cdf(const float* J, long long n, int B, float* out, cudaStream_t s);
+
+// One P(T) problem: a PAH in a monochromatic field.
+struct PtCase {
+  PahSpec spec;
+  double h_nu;   // photon energy, erg
+  double rate;   // absorbed photons per molecule per second
+  double t_top;  // levels span 0 .. E(t_top) + h_nu
+};
+cudaError_t launch_pah_pt(const PtCase* cases, int n_cases, const double* nu, int B,
+                          const double* sigma, int M, double t_sub, double* P_out,
+                          double* T_out, double* p_above, double* em_out, cudaStream_t s);
 
 cudaError_t launch_frozen_u(const DevGrid& g, const DevTables& t, const float* T_frozen,
                             float* u_frozen, float t_min, cudaStream_t s);

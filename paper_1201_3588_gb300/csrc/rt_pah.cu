@@ -439,6 +439,160 @@ cudaError_t launch_surrogate_add(const float* Y, const float* p_abs, long long n
   return cudaGetLastError();
 }
 
+// P(T) of a PAH in a monochromatic field (Fig. 3), one block per case: levels
+// E_f = f dE up to E(t_top) + h nu with their temperatures and cooling rates
+// (threads over levels), populations by the level-by-level flux balance for the
+// single photon energy (one thread), then the time fraction above t_sub and the
+// emission per bin (threads over bins). Shared memory: T, L, D [M] doubles.
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+__global__ void k_pah_pt(const PtCase* cases, const double* nu, int B, const double* sigma,
+                         int M, double t_sub, double* P_out, double* T_out, double* p_above,
+                         double* em_out) {
+  extern __shared__ double sm[];
+  double* T = sm;
+  double* L = T + M;
+  double* D = L + M;
+  double* red = D + M;  // [32]
+  const PtCase c = cases[blockIdx.x];
+  const double* sig = sigma + (size_t)blockIdx.x * B;
+  double* P = P_out + (size_t)blockIdx.x * M;
+  const double dE = (heat_content(c.t_top, c.spec) + c.h_nu) / (double)(M - 1);
+  for (int f = threadIdx.x; f < M; f += blockDim.x) {
+    const double Tf = f == 0 ? 0.0 : temperature_of(f * dE, c.spec);
+    double l = 0.0;
+    if (f > 0)
+      for (int b = 0; b < B; ++b) l += sig[b] * planck_bin(nu[b], nu[b + 1], Tf);
+    T[f] = Tf;
+    L[f] = 4.0 * kPi * l;
+    D[f] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double x = c.h_nu / dE;
+    const int q = (int)floor(x);
+    const double w = x - floor(x);
+    const double R = c.rate;
+    // arrivals from level i: level i + q (weight 1 - w) and i + q + 1 (weight w),
+    // both cut at the top level; returns the upward rate out of level i
+    auto scatter = [&](int i, double Pi) {
+      int f = i + q;
+      double wk = w;
+      if (f >= M - 1) {
+        f = M - 1;
+        wk = 0.0;
+      }
+      double up = 0.0;
+      if (f > i) {
+        D[f] += Pi * R * (1.0 - wk);
+        up += R * (1.0 - wk);
+      }
+      if (wk > 0.0 && f + 1 < M) {
+        D[f + 1] += Pi * R * wk;
+        up += R * wk;
+      }
+      return up;
+    };
+    P[0] = 1.0;
+    double F = scatter(0, 1.0);
+    for (int f = 1; f < M; ++f) {
+      const double C = L[f] / dE;
+      const double Pf = C > 0.0 ? F / C : 0.0;
+      P[f] = Pf;
+      const double u = scatter(f, Pf);
+      F = fmax(F - D[f] + Pf * u, 0.0);
+      if (Pf > 1e250) {  // keep the numbers finite
+        for (int i = 0; i <= f; ++i) P[i] *= 1e-250;
+        for (int i = 0; i < M; ++i) D[i] *= 1e-250;
+        F *= 1e-250;
+      }
+    }
+  }
+  __syncthreads();
+  double s = 0.0, a = 0.0;
+  for (int f = threadIdx.x; f < M; f += blockDim.x) s += P[f];
+  const double tot = block_sum(s, red);
+  for (int f = threadIdx.x; f < M; f += blockDim.x) {
+    const double v = P[f] / tot;
+    P[f] = v;
+    T_out[(size_t)blockIdx.x * M + f] = T[f];
+    if (T[f] > t_sub) a += v;
+  }
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) p_above[blockIdx.x] = a;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    double e = 0.0;
+    for (int f = 1; f < M; ++f) e += P[f] * planck_bin(nu[b], nu[b + 1], T[f]);
+    em_out[(size_t)blockIdx.x * B + b] = 4.0 * kPi * sig[b] * e;
+  }
+}
+
+cudaError_t launch_pah_pt(const PtCase* cases, int n_cases, const double* nu, int B,
+                          const double* sigma, int M, double t_sub, double* P_out,
+                          double* T_out, double* p_above, double* em_out, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (3 * (size_t)M + 32);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_pah_pt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_pah_pt<<<n_cases, 256, smem, s>>>(cases, nu, B, sigma, M, t_sub, P_out, T_out, p_above,
+                                      em_out);
+  return cudaGetLastError();
+}
+
+// Per-cell re-emission spectra: each row of J [n][B] (erg/s per bin; negative or NaN
+// entries count as 0) becomes its normalised cumulative sum, the last entry exactly
+// 1; a row with nothing positive becomes zeros (the transport then uses the
+// template). One warp per row, FP64 sums, a 32-wide inclusive scan per chunk.
+__global__ void k_pah_cell_cdf(const float* J, long long n, int B, float* out) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long row = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); row < n;
+       row += warps) {
+    const float* j = J + row * B;
+    float* o = out + row * B;
+    double tot = 0.0;
+    for (int b = lane; b < B; b += 32) tot += (double)fmaxf(j[b], 0.f);
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, s);
+    if (!(tot > 0.0)) {
+      for (int b = lane; b < B; b += 32) o[b] = 0.f;
+      continue;
+    }
+    double carry = 0.0;
+    for (int base = 0; base < B; base += 32) {
+      const int b = base + lane;
+      double v = b < B ? (double)fmaxf(j[b], 0.f) : 0.0;
+#pragma unroll
+      for (int s = 1; s < 32; s <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v, s);
+        if (lane >= s) v += u;
+      }
+      if (b < B) o[b] = b == B - 1 ? 1.f : (float)((carry + v) / tot);
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+}
+
+cudaError_t launch_pah_cell_cdf(const float* J, long long n, int B, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 7) / 8;
+  if (blocks > 65536) blocks = 65536;
+  k_pah_cell_cdf<<<(unsigned)blocks, 256, 0, s>>>(J, n, B, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_compact(const PahTables& t, const unsigned* pahabs, long long N, int pah,
                            long long first, long long n, const unsigned char* flag,
                            const int* list, int* out, unsigned* count, cudaStream_t s) {

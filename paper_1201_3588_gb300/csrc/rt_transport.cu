@@ -533,21 +533,33 @@ __device__ __forceinline__ void reemit(Pkg<R>& k, const DevGrid& g, const DevTab
   k.bin = b;
 }
 
-// Absorption by a PAH species: tally the photon in the cell's coarse absorbed
-// spectrum and draw the new bin from the PAH's template emission spectrum.
+// New bin after an absorption by PAH number p: drawn from the PAH's emission
+// spectrum in this cell (its template unless a per-cell spectrum is set).
 template <typename R>
-__device__ __forceinline__ void pah_absorb(Pkg<R>& k, const DevGrid& g, const DevTables& t,
-                                           const DevRun& r, int p, int leaf, const uint4& w1) {
-  const int kc = (k.bin * t.n_coarse) / g.B;
-  atomicAdd(&r.pahabs[((size_t)p * g.n_leaves + leaf) * t.n_coarse + kc], 1u);
+__device__ __forceinline__ void pah_bin(Pkg<R>& k, const DevGrid& g, const DevTables& t, int p,
+                                        int leaf, const uint4& w1) {
   const float xb = unit<float>(w1.z);
   const float* cdf = t.pah_cdf + (size_t)p * g.B;
+  if (t.pah_cell_cdf) {
+    const float* cc = t.pah_cell_cdf + ((size_t)p * g.n_leaves + leaf) * g.B;
+    if (__ldg(&cc[g.B - 1]) > 0.f) cdf = cc;
+  }
   int lo = 0, hi = g.B - 1;
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
     if (__ldg(&cdf[mid]) > xb) hi = mid; else lo = mid + 1;
   }
   k.bin = lo;
+}
+
+// Absorption by a PAH species: tally the photon in the cell's coarse absorbed
+// spectrum, then draw the new bin.
+template <typename R>
+__device__ __forceinline__ void pah_absorb(Pkg<R>& k, const DevGrid& g, const DevTables& t,
+                                           const DevRun& r, int p, int leaf, const uint4& w1) {
+  const int kc = (k.bin * t.n_coarse) / g.B;
+  atomicAdd(&r.pahabs[((size_t)p * g.n_leaves + leaf) * t.n_coarse + kc], 1u);
+  pah_bin(k, g, t, p, leaf, w1);
 }
 
 __device__ __forceinline__ int dir_bin(float dz, int n_dir) {
@@ -1020,15 +1032,7 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
     int s = interact<float>(k, g, t.kap, c.leaf, r, w1);
     if (s < 0) { ++rec[2]; continue; }
     if (t.pah_of[s] >= 0) {
-      // replay does not tally: only the new bin is drawn
-      const float xb = unit<float>(w1.z);
-      const float* cdf = t.pah_cdf + (size_t)t.pah_of[s] * g.B;
-      int lo = 0, hi = g.B - 1;
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (__ldg(&cdf[mid]) > xb) hi = mid; else lo = mid + 1;
-      }
-      k.bin = lo;
+      pah_bin(k, g, t, t.pah_of[s], c.leaf, w1);  // replay does not tally
     } else {
       reemit<float>(k, g, t, r, s, c.leaf, c.level, 0ull, w1, tl);
     }

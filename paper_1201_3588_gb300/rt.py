@@ -58,6 +58,12 @@ class _Counters(C.Structure):
                                           "peel_dropped")]
 
 
+class _PtCase(C.Structure):
+    _fields_ = [("modes", (C.c_double * 2) * 4), ("n_groups", C.c_int32),
+                ("reserved", C.c_int32), ("h_nu_erg", C.c_double), ("rate", C.c_double),
+                ("t_top", C.c_double)]
+
+
 class _ImageDesc(C.Structure):
     _fields_ = [("obs_dir", C.c_double * 3), ("nx", C.c_int32), ("ny", C.c_int32),
                 ("half_width_cm", C.c_double), ("tau_max", C.c_double),
@@ -110,6 +116,11 @@ SIGNATURES = {
     "rt_set_pah": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_int,
                    C.c_int, C.c_double],
     "rt_pah_absorbed": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "rt_pah_temperature_distribution": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                        C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p],
+    "rt_set_pah_spectra": [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_int,
+                           C.c_void_p],
     "rt_pah_emission": [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_void_p,
                         C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "rt_pah_training_pairs": [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_void_p,
@@ -320,6 +331,19 @@ class Grid:
                                       _stream(stream)), "rt_pah_emission")
         return out, int(nf.value)
 
+    def set_pah_spectra(self, pah: int, J, first: int = 0, stream=None):
+        """Per-cell re-emission spectra of PAH `pah` for cells first .. first+len(J)-1
+        (rows [n][B]); None removes the spectra of every PAH."""
+        if J is None:
+            _check(load().rt_set_pah_spectra(self._h, 0, 0, 0, None, MEM_HOST,
+                                             _stream(stream)), "rt_set_pah_spectra")
+            return
+        if not hasattr(J, "data_ptr"):
+            J = np.ascontiguousarray(J, dtype=np.float32).reshape(-1, self.B)
+        p, mem = _ptr_mem(J)
+        _check(load().rt_set_pah_spectra(self._h, int(pah), int(first), int(J.shape[0]), p, mem,
+                                         _stream(stream)), "rt_set_pah_spectra")
+
     def pah_training_pairs(self, pah: int, X, Y, p_abs, first: int = 0, stream=None):
         n = int(X.shape[0])
         _check(load().rt_pah_training_pairs(self._h, int(pah), int(first), n, X.data_ptr(),
@@ -374,6 +398,37 @@ class Grid:
         _check(load().rt_trace(self._h, idv.ctypes.data, idv.shape[0], int(seed),
                                int(max_events), out.ctypes.data), "rt_trace")
         return out
+
+
+def pah_temperature_distribution(cases, nu_edges, sigma, n_levels: int = 400,
+                                 t_sub: float = 2500.0):
+    """P(T) of PAHs in monochromatic fields. `cases`: dicts with modes ((n, theta),
+    ...), h_nu (erg), rate (photons/s per molecule) and optionally t_top (K); sigma
+    [n_cases][n_bins] cross sections per molecule. Returns P, T [n][n_levels],
+    p_above [n] and the emission per bin [n][n_bins]."""
+    n = len(cases)
+    arr = (_PtCase * n)()
+    for i, c in enumerate(cases):
+        modes = list(c["modes"])
+        for k, (cnt, th) in enumerate(modes):
+            arr[i].modes[k][0] = float(cnt)
+            arr[i].modes[k][1] = float(th)
+        arr[i].n_groups = len(modes)
+        arr[i].h_nu_erg = float(c["h_nu"])
+        arr[i].rate = float(c["rate"])
+        arr[i].t_top = float(c.get("t_top", 0.0))
+    nu = np.ascontiguousarray(nu_edges, dtype=np.float64)
+    B = nu.shape[0] - 1
+    sig = np.ascontiguousarray(sigma, dtype=np.float64).reshape(n, B)
+    P = np.zeros((n, n_levels))
+    T = np.zeros((n, n_levels))
+    a = np.zeros(n)
+    em = np.zeros((n, B))
+    _check(load().rt_pah_temperature_distribution(arr, n, nu.ctypes.data, B, sig.ctypes.data,
+                                                  int(n_levels), float(t_sub), P.ctypes.data,
+                                                  T.ctypes.data, a.ctypes.data, em.ctypes.data,
+                                                  None), "rt_pah_temperature_distribution")
+    return P, T, a, em
 
 
 def philox(ids, event: int, block: int, seed: int) -> np.ndarray:
