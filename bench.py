@@ -199,8 +199,8 @@ def run_reference(args):
 # valid only for the kernel source it was measured on.
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": "cd28932466e0c31b116bb145ba4b838fc9382aaf6c4a03c14b1f21c0438741e7",
-           "dram_bytes_per_package": 1072.3}
+           "sha256": "39edcfff36beca193e38a031f4f7ef8970c6be26a9d2c58f9d78c4d3e36ca2d5",
+           "dram_bytes_per_package": 1081.3}
 
 
 def traffic_per_launch(n_packages):

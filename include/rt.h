@@ -91,7 +91,7 @@ typedef struct rt_run_opts {
     uint64_t max_events;    /* interactions per package before it is capped; 0: 1e7 */
     int32_t blocks_per_sm;  /* pool: resident blocks per SM; 0: from occupancy */
     int32_t threads;        /* threads per block, multiple of 32; 0: 256 */
-    int32_t refill_period;  /* pool: steps between refills of dead lanes; 0: 16 */
+    int32_t refill_period;  /* pool: steps between refills of dead lanes; 0: 32 */
     int32_t interaction_batch; /* pool: lanes of a warp waiting at an interaction
                                point that start an interaction phase, 1..32; 0: 8 */
     double budget_s;        /* device time budget per launch in s; 0: 120 */

@@ -13,7 +13,7 @@ from typing import Dict, Optional
 
 from . import rt
 
-CANDIDATES = dict(blocks_per_sm=(0, 5), interaction_batch=(4, 6, 8, 12), refill_period=(4, 8, 16))
+CANDIDATES = dict(blocks_per_sm=(0, 5), interaction_batch=(4, 6, 8, 12), refill_period=(8, 16, 32))
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1201_3588_gb300",
                              "autotune.json")
 

@@ -799,7 +799,7 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
   }
   r->source_kind = g->source_kind;
   r->mode = mode;
-  r->refill_period = (o && o->refill_period > 0) ? o->refill_period : 16;
+  r->refill_period = (o && o->refill_period > 0) ? o->refill_period : 32;
   r->interaction_batch = (o && o->interaction_batch > 0) ? o->interaction_batch : 8;
   double budget = (o && o->budget_s > 0) ? o->budget_s : 120.0;
   r->budget_ns = (unsigned long long)(budget * 1e9);

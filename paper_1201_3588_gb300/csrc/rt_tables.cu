@@ -95,7 +95,7 @@ __global__ void k_u_guides(TableBuild tb) {
   tb.u_guide[idx] = lo;
 }
 
-__global__ void k_opacity_and_star(TableBuild tb) {
+__global__ void k_opacity(TableBuild tb) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < tb.B) {
     for (int s = 0; s < tb.S; ++s) {
@@ -108,12 +108,22 @@ __global__ void k_opacity_and_star(TableBuild tb) {
       tb.kap[(size_t)b * tb.S + s] = k;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+}
+
+// Stellar CDF and the in-range fraction of the blackbody: the bins' Planck
+// integrals in parallel (one block of 1024 threads), the sums by one thread in bin
+// order.
+__global__ void __launch_bounds__(1024) k_star_cdf(TableBuild tb) {
+  __shared__ double P[kMaxBins];
+  for (int i = threadIdx.x; i < tb.B; i += blockDim.x)
+    P[i] = planck_bin(tb.nu[i], tb.nu[i + 1], tb.T_star);
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double tot = 0.0;
-    for (int i = 0; i < tb.B; ++i) tot += planck_bin(tb.nu[i], tb.nu[i + 1], tb.T_star);
+    for (int i = 0; i < tb.B; ++i) tot += P[i];
     double cum = 0.0;
     for (int i = 0; i < tb.B; ++i) {
-      cum += planck_bin(tb.nu[i], tb.nu[i + 1], tb.T_star);
+      cum += P[i];
       tb.star_cdf[i] = tot > 0.0 ? (float)(cum / tot) : 1.0f;
     }
     tb.star_cdf[tb.B - 1] = 1.0f;
@@ -151,7 +161,7 @@ __global__ void k_frozen_u(DevGrid g, DevTables t, const float* T_frozen, float*
   u_frozen[idx] = (float)u;
 }
 
-// T from n eps = M S(T): binary search in the FP64 S table, then power-law
+// T from n eps = M S(T): the FP64 S table's interval (guide + scan), then power-law
 // (log-log) interpolation between rows; linear from T = 0 in the first interval.
 __global__ void k_temperatures(DevGrid g, DevTables t, const unsigned long long* count,
                                float* T_out, unsigned long long* counters,
@@ -177,17 +187,23 @@ __global__ void k_temperatures(DevGrid g, DevTables t, const unsigned long long*
         Tv = (float)Tg[n_T - 1];
         clamped = true;
       } else {
-        int lo = 0, hi = n_T - 1;  // S[lo] <= u < S[hi]
-        while (hi - lo > 1) {
-          int mid = (lo + hi) >> 1;
-          if (S[mid] <= u) lo = mid; else hi = mid;
-        }
+        // interval i with S[i] <= u < S[i+1]: start from the guide of ln S (the
+        // re-emission draws use the same one), finish by scanning
+        const int nI = n_T - 1;
+        float kf = (__logf(fmaxf((float)u, 1e-30f)) - t.u_ln0[s]) * t.u_inv[s];
+        int kk = (int)fminf(fmaxf(kf, 0.0f), (float)nI);
+        int i = t.u_guide[s * n_T + kk];
+        while (i > 0 && S[i] > u) --i;
+        while (i + 1 < nI && S[i + 1] <= u) ++i;
         double T;
-        if (lo == 0 || !(S[lo] > 0.0)) {
-          T = Tg[hi] * u / S[hi];
+        if (i == 0 || !(S[i] > 0.0)) {
+          T = Tg[i + 1] * u / S[i + 1];
         } else {
-          double a = log(u / S[lo]) / log(S[hi] / S[lo]);
-          T = Tg[lo] * exp(a * log(Tg[hi] / Tg[lo]));
+          // power law between the rows: ln(T/T_i) = ln(u/S_i) ln(T_i+1/T_i) / ln(S_i+1/S_i);
+          // the ratios are formed in FP64, their logarithms (of numbers near 1) in FP32
+          const double inv = 1.0 / S[i];
+          const float a = log1pf((float)(u * inv - 1.0)) / log1pf((float)(S[i + 1] * inv - 1.0));
+          T = Tg[i] * (double)expf(a * logf((float)(Tg[i + 1] / Tg[i])));
         }
         Tv = (float)T;
       }
@@ -208,7 +224,8 @@ cudaError_t launch_build_tables(const TableBuild& tb, cudaStream_t s) {
   k_difference_cdfs<<<nblk((long long)tb.S * (tb.n_T - 1), 128), 128, 0, s>>>(tb);
   k_cdf_guides<<<nblk((long long)tb.S * (tb.n_T - 1), 128), 128, 0, s>>>(tb);
   k_u_guides<<<nblk((long long)tb.S * tb.n_T, 128), 128, 0, s>>>(tb);
-  k_opacity_and_star<<<nblk(tb.B, 128), 128, 0, s>>>(tb);
+  k_opacity<<<nblk(tb.B, 128), 128, 0, s>>>(tb);
+  k_star_cdf<<<1, 1024, 0, s>>>(tb);
   return cudaGetLastError();
 }
 
