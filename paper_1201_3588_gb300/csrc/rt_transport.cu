@@ -797,7 +797,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
   bool alive = false;
   bool pending = false;  // reached an interaction point, waiting for the batch
   Cell cell{0, 0, {0, 0, 0}};
-  const int K = r.refill_period > 0 ? r.refill_period : 16;
+  const int K = r.refill_period > 0 ? r.refill_period : 32;
   const int batch = r.interaction_batch > 0 ? r.interaction_batch : 8;
 
   for (;;) {
