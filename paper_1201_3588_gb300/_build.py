@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt_gb300.so")
-SOURCES = ["rt_api.cu", "rt_tables.cu", "rt_transport.cu", "rt_noalloc.cu", "rt_pah.cu",
+SOURCES = ["rt_api.cu", "rt_grid.cu", "rt_tables.cu", "rt_transport.cu", "rt_noalloc.cu", "rt_pah.cu",
            "rt_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

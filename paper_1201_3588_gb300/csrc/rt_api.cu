@@ -197,105 +197,6 @@ void free_all(rt_grid* g) {
   dfree(g->d_ucount);
 }
 
-// Walk the tree from every base cube: every leaf id must appear exactly once,
-// every block be referenced exactly once, and no path exceed max_level. Records
-// each leaf's level and integer corner (at its level). Base cubes are split over
-// host threads; claim flags (atomic) catch a leaf or block reached twice.
-rt_status check_tree(const rt_grid_desc* d, std::vector<int8_t>& level,
-                     std::vector<int32_t>& ijk, int* max_seen) {
-  const long long n = d->n_base;
-  const long long nb = n * n * n;
-  level.assign((size_t)d->n_leaves, (int8_t)-1);
-  ijk.assign((size_t)d->n_leaves * 3, 0);
-  std::unique_ptr<std::atomic<unsigned char>[]> leaf_seen(
-      new (std::nothrow) std::atomic<unsigned char>[(size_t)d->n_leaves]);
-  std::unique_ptr<std::atomic<unsigned char>[]> blk_seen(
-      new (std::nothrow) std::atomic<unsigned char>[(size_t)(d->n_blocks > 0 ? d->n_blocks : 1)]);
-  if (!leaf_seen || !blk_seen) return RT_ERR_OOM;
-  for (long long i = 0; i < d->n_leaves; ++i) leaf_seen[(size_t)i].store(0, std::memory_order_relaxed);
-  for (long long i = 0; i < d->n_blocks; ++i) blk_seen[(size_t)i].store(0, std::memory_order_relaxed);
-  unsigned nt = std::thread::hardware_concurrency();
-  if (nt < 1) nt = 1;
-  if (nt > 32) nt = 32;
-  if (nb < 4096) nt = 1;
-  std::vector<rt_status> res(nt, RT_OK);
-  std::vector<int> mx(nt, 0);
-  auto work = [&](unsigned tid) {
-    struct Item { int32_t node; int lev; int32_t i, j, k; };
-    std::vector<Item> stk;
-    stk.reserve(64);
-    const long long b0 = nb * tid / nt, b1 = nb * (tid + 1) / nt;
-    for (long long b = b0; b < b1; ++b) {
-      stk.clear();
-      stk.push_back({d->base[b], 0, (int32_t)(b % n), (int32_t)((b / n) % n),
-                     (int32_t)(b / (n * n))});
-      while (!stk.empty()) {
-        Item it = stk.back();
-        stk.pop_back();
-        if (it.lev > d->max_level) { res[tid] = RT_ERR_ARG; return; }
-        if (it.node >= 0) {
-          if ((long long)it.node >= d->n_leaves ||
-              leaf_seen[(size_t)it.node].exchange(1, std::memory_order_relaxed)) {
-            res[tid] = RT_ERR_ARG;
-            return;
-          }
-          level[(size_t)it.node] = (int8_t)it.lev;
-          ijk[(size_t)it.node * 3 + 0] = it.i;
-          ijk[(size_t)it.node * 3 + 1] = it.j;
-          ijk[(size_t)it.node * 3 + 2] = it.k;
-          if (it.lev > mx[tid]) mx[tid] = it.lev;
-        } else {
-          long long blk = -(long long)it.node - 1;
-          if (blk >= d->n_blocks || blk_seen[(size_t)blk].exchange(1, std::memory_order_relaxed)) {
-            res[tid] = RT_ERR_ARG;
-            return;
-          }
-          for (int o = 0; o < 8; ++o)
-            stk.push_back({d->child[blk * 8 + o], it.lev + 1, 2 * it.i + (o & 1),
-                           2 * it.j + ((o >> 1) & 1), 2 * it.k + ((o >> 2) & 1)});
-        }
-      }
-    }
-  };
-  if (nt == 1) {
-    work(0);
-  } else {
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
-    for (auto& x : th) x.join();
-  }
-  *max_seen = 0;
-  for (unsigned t = 0; t < nt; ++t) {
-    if (res[t] != RT_OK) return res[t];
-    if (mx[t] > *max_seen) *max_seen = mx[t];
-  }
-  for (long long i = 0; i < d->n_leaves; ++i)
-    if (level[(size_t)i] < 0) return RT_ERR_ARG;
-  for (long long b = 0; b < d->n_blocks; ++b)
-    if (!blk_seen[(size_t)b].load(std::memory_order_relaxed)) return RT_ERR_ARG;
-  return RT_OK;
-}
-
-// out[i] = f(i) for i in [0, n), split over host threads
-template <typename F>
-void parallel_for(long long n, F f) {
-  unsigned nt = std::thread::hardware_concurrency();
-  if (nt < 1) nt = 1;
-  if (nt > 32) nt = 32;
-  if (n < (1 << 16)) nt = 1;
-  if (nt == 1) {
-    for (long long i = 0; i < n; ++i) f(i);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < nt; ++t)
-    th.emplace_back([&, t]() {
-      const long long a = n * t / nt, b = n * (t + 1) / nt;
-      for (long long i = a; i < b; ++i) f(i);
-    });
-  for (auto& x : th) x.join();
-}
-
 rt_status sync_status(rt_grid* g, cudaStream_t s) {
   RT_CUDA(cudaStreamSynchronize(s));
   unsigned st = 0;
@@ -528,15 +429,6 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
         (b > 0 && !(d->nu_edges[b] > d->nu_edges[b - 1])))
       return RT_ERR_ARG;
   const long long S = d->n_species, N = d->n_leaves;
-  {
-    std::atomic<int> bad(0);
-    const double* r = d->rho;
-    parallel_for(S * N, [&bad, r](long long i) {
-      if (!(r[i] >= 0) || !std::isfinite(r[i])) bad.store(1, std::memory_order_relaxed);
-    });
-    if (bad.load()) return RT_ERR_ARG;
-  }
-
   rt_grid* g = new (std::nothrow) rt_grid();
   if (!g) return RT_ERR_OOM;
   g->desc = *d;
@@ -548,23 +440,10 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   if (g->desc.t_min == 0) g->desc.t_min = 1.0;
   if (g->desc.t_max == 0) g->desc.t_max = 3000.0;
   if (g->desc.n_temp < 3 || g->desc.n_temp > 65536 || !(g->desc.t_min > 0) ||
-      !(g->desc.t_max > g->desc.t_min)) {
+      !(g->desc.t_max > g->desc.t_min) || d->n_leaves >= kMaxLinkedLeaves) {
     delete g;
     return RT_ERR_ARG;
   }
-  std::vector<int8_t> level;
-  std::vector<int32_t> ijk;
-  int max_seen = 0;
-  if (d->n_leaves >= kMaxLinkedLeaves) {
-    delete g;
-    return RT_ERR_ARG;
-  }
-  rt_status st = check_tree(d, level, ijk, &max_seen);
-  if (st != RT_OK) {
-    delete g;
-    return st;
-  }
-  g->n_levels_used = max_seen + 1;
   g->d0 = 2.0 * d->half_size_cm / d->n_base;
   g->nu.assign(d->nu_edges, d->nu_edges + d->n_bins + 1);
   g->kabs.assign((size_t)S * d->n_bins, 0.0);
@@ -580,19 +459,9 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
     delete g;
     return RT_ERR_CUDA;
   }
-  // densities to [N][S] floats times the base-cube edge
-  std::vector<float> rho((size_t)S * N);
-  {
-    const double d0 = g->d0;
-    const double* src = d->rho;
-    float* dstp = rho.data();
-    parallel_for(N, [=](long long c) {
-      for (long long s = 0; s < S; ++s)
-        dstp[(size_t)(c * S + s)] = (float)(src[(size_t)(s * N + c)] * d0);
-    });
-  }
   const long long nb = (long long)d->n_base * d->n_base * d->n_base;
   const int B = d->n_bins;
+  rt_status st;
 #define ALLOC(p, n) if ((st = dalloc(&(p), (n))) != RT_OK) { free_all(g); delete g; return st; }
   ALLOC(g->d_base, (size_t)nb);
   ALLOC(g->d_child, (size_t)d->n_blocks * 8);
@@ -605,21 +474,69 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   ALLOC(g->d_next, 1);
   ALLOC(g->d_status, 1);
 #undef ALLOC
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMemcpy(g->d_base, d->base, sizeof(int32_t) * nb, cudaMemcpyHostToDevice);
+  // work arrays of the device tree walk and the density conversion
+  int32_t *d_ijk = nullptr, *d_blk_ijk = nullptr;
+  int8_t* d_blk_level = nullptr;
+  unsigned *d_leaf_seen = nullptr, *d_blk_seen = nullptr, *d_err = nullptr;
+  double* d_rho64 = nullptr;
+  auto free_work = [&]() {
+    dfree(d_ijk);
+    dfree(d_blk_ijk);
+    dfree(d_blk_level);
+    dfree(d_leaf_seen);
+    dfree(d_blk_seen);
+    dfree(d_err);
+    dfree(d_rho64);
+  };
+  const long long nbk = d->n_blocks > 0 ? d->n_blocks : 1;
+  if ((st = dalloc(&d_ijk, (size_t)N * 3)) != RT_OK ||
+      (st = dalloc(&d_blk_ijk, (size_t)nbk * 3)) != RT_OK ||
+      (st = dalloc(&d_blk_level, (size_t)nbk)) != RT_OK ||
+      (st = dalloc(&d_leaf_seen, (size_t)((N + 31) >> 5))) != RT_OK ||
+      (st = dalloc(&d_blk_seen, (size_t)((nbk + 31) >> 5))) != RT_OK ||
+      (st = dalloc(&d_err, 2)) != RT_OK || (st = dalloc(&d_rho64, (size_t)S * N)) != RT_OK) {
+    free_work();
+    free_all(g);
+    delete g;
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(g->d_base, d->base, sizeof(int32_t) * nb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && d->n_blocks > 0)
     e = cudaMemcpy(g->d_child, d->child, sizeof(int32_t) * 8 * d->n_blocks, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(g->d_rho, rho.data(), sizeof(float) * S * N, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(g->d_level, level.data(), (size_t)N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d_rho64, d->rho, sizeof(double) * S * N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(d_err, 0, 2 * sizeof(unsigned));
+  TreeBuild tb{};
+  tb.base = g->d_base;
+  tb.child = g->d_child;
+  tb.n_leaves = N;
+  tb.n_blocks = d->n_blocks;
+  tb.n_base = d->n_base;
+  tb.max_level = d->max_level;
+  tb.level = g->d_level;
+  tb.ijk = d_ijk;
+  tb.blk_level = d_blk_level;
+  tb.blk_ijk = d_blk_ijk;
+  tb.leaf_seen = d_leaf_seen;
+  tb.blk_seen = d_blk_seen;
+  tb.err = d_err;
+  tb.max_seen = reinterpret_cast<int*>(d_err + 1);
+  if (e == cudaSuccess) e = launch_tree_walk(tb, nullptr);
+  if (e == cudaSuccess) e = launch_rho_convert(d_rho64, N, (int)S, g->d0, g->d_rho, d_err, nullptr);
+  unsigned host_err[2] = {0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpy(host_err, d_err, sizeof(host_err), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(g->d_count, 0, sizeof(unsigned long long) * S * N);
   if (e == cudaSuccess) e = cudaMemset(g->d_sed, 0, sizeof(unsigned long long) * 2 * d->n_sed_dirs * B);
   if (e == cudaSuccess) e = cudaMemset(g->d_counters, 0, sizeof(unsigned long long) * kNumCounters);
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess || host_err[0] != 0) {
+    free_work();
     free_all(g);
     delete g;
-    return RT_ERR_CUDA;
+    return e != cudaSuccess ? RT_ERR_CUDA : RT_ERR_ARG;
   }
+  g->n_levels_used = (int)host_err[1] + 1;
   g->g.base = g->d_base;
   g->g.child = g->d_child;
   g->g.rho = g->d_rho;
@@ -634,22 +551,13 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   g->g.n_dir = d->n_sed_dirs;
   g->g.n_T = g->desc.n_temp;
   // face links of every leaf, built on the device from the leaf corners
-  {
-    int32_t* d_ijk = nullptr;
-    if ((st = dalloc(&d_ijk, (size_t)N * 3)) != RT_OK) {
-      free_all(g);
-      delete g;
-      return st;
-    }
-    e = cudaMemcpy(d_ijk, ijk.data(), sizeof(int32_t) * 3 * N, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_build_links(g->g, d_ijk, g->d_links, nullptr);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    dfree(d_ijk);
-    if (e != cudaSuccess) {
-      free_all(g);
-      delete g;
-      return RT_ERR_CUDA;
-    }
+  e = launch_build_links(g->g, d_ijk, g->d_links, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  free_work();
+  if (e != cudaSuccess) {
+    free_all(g);
+    delete g;
+    return RT_ERR_CUDA;
   }
   *out = g;
   return RT_OK;

@@ -156,6 +156,25 @@ cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
                          cudaStream_t s);
 cudaError_t launch_build_links(const DevGrid& g, const int32_t* leaf_ijk, int32_t* links,
                                cudaStream_t s);
+
+// Device walk of the tree (rt_grid.cu): inputs, outputs and work arrays.
+struct TreeBuild {
+  const int32_t* base;     // [n^3]
+  const int32_t* child;    // [n_blocks][8]
+  long long n_leaves, n_blocks;
+  int n_base, max_level;
+  int8_t* level;           // [n_leaves] out
+  int32_t* ijk;            // [n_leaves][3] out: integer corner at the leaf's level
+  int8_t* blk_level;       // [n_blocks] work
+  int32_t* blk_ijk;        // [n_blocks][3] work
+  unsigned* leaf_seen;     // [(n_leaves + 31) / 32] work bitmap
+  unsigned* blk_seen;      // [(n_blocks + 31) / 32] work bitmap
+  unsigned* err;           // nonzero: malformed tree (bit 0) or bad density (bit 1)
+  int* max_seen;           // deepest level reached
+};
+cudaError_t launch_tree_walk(const TreeBuild& tb, cudaStream_t s);
+cudaError_t launch_rho_convert(const double* src, long long N, int S, double d0, float* dst,
+                               unsigned* err, cudaStream_t s);
 cudaError_t launch_philox(const unsigned long long* ids, long long n, unsigned event,
                           unsigned block, unsigned long long seed, unsigned* out,
                           cudaStream_t s);

@@ -49,7 +49,9 @@ def _create(d):
     return rt.load().rt_grid_create(C.byref(d), C.byref(h))
 
 
-def test_malformed_trees_are_rejected_on_the_host():
+@pytest.mark.gpu
+def test_malformed_trees_are_rejected():
+    """The tree is walked on the device: a malformed one is rejected before use."""
     t = w.build_tree(2, 1, lambda l, lo, hi: (lo == 0).all(axis=1))
     nu = w.frequency_edges(4)
     rho = np.ones(t.n_leaves)
@@ -74,8 +76,11 @@ def test_malformed_trees_are_rejected_on_the_host():
     assert _create(d) == 1
 
 
-@pytest.mark.parametrize("what", ["nu_order", "rho_nan", "rho_neg", "species", "bins"])
-def test_bad_descriptors_are_rejected_on_the_host(what):
+@pytest.mark.parametrize("what", [
+    "nu_order", "species", "bins",
+    pytest.param("rho_nan", marks=pytest.mark.gpu),   # densities are checked on the device
+    pytest.param("rho_neg", marks=pytest.mark.gpu)])
+def test_bad_descriptors_are_rejected(what):
     t = w.build_tree(2, 0)
     nu = w.frequency_edges(4)
     rho = np.ones(t.n_leaves)
