@@ -199,8 +199,8 @@ def run_reference(args):
 # valid only for the kernel source it was measured on.
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": "39edcfff36beca193e38a031f4f7ef8970c6be26a9d2c58f9d78c4d3e36ca2d5",
-           "dram_bytes_per_package": 1081.3}
+           "sha256": "e4701bbb50d62c83254828a7e02534f3a8c2981fd49a5167a77473a02d8c823e",
+           "dram_bytes_per_package": 1080.7}
 
 
 def traffic_per_launch(n_packages):
