@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--packages", type=float, default=1e8, help="packages per GPU per step")
-    p.add_argument("--workload", choices=["disk", "sphere", "batch", "disk_pah", "disk_images"],
+    p.add_argument("--workload", choices=["disk", "sphere", "batch", "disk_pah", "disk_images",
+                                          "large_disk"],
                    default="disk")
     p.add_argument("--batch-models", type=int, default=256)
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -68,6 +69,11 @@ def build_model(name):
                 "midplane tau_V=1e3, r 0.1-100 AU; peel-off images at the 10 and 11.3 micron "
                 "bins, 256x256 pixels over +-100 AU, inclination 60 deg, and their dual-band "
                 "major-axis profile")
+    if name == "large_disk":
+        return (w.large_disk_model(),
+                "large disk with gap and spiral, 256^3 base + 3 levels (1.73e8 cells), 400 bins, "
+                "silicate, carbon, PAH 30 C and 200 C; PAH emission by the BF16 surrogate with "
+                "exact fallback (tol 0.05)")
     if name == "disk_pah":
         return (w.disk_pah_model(),
                 "flared disk with gap and spiral, 128^3 base + 2 levels, 200 bins, silicate, "
@@ -248,7 +254,7 @@ def run_ours(args):
     sed_dev = torch.empty((2, model.n_sed_dirs, B), dtype=torch.int64, device=dev)
     cnt_dev = torch.empty((S, N), dtype=torch.int64, device=dev) if world > 1 else None
     first = rank * n
-    pah = args.workload == "disk_pah"
+    pah = args.workload in ("disk_pah", "large_disk")
     images = args.workload == "disk_images"
     img_dev = prof_dev = None
     if images:

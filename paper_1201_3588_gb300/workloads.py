@@ -458,9 +458,11 @@ def _disk_cell_average(lo: np.ndarray, hi: np.ndarray, r_in: float, r_out: float
     return acc / (ns * ns)
 
 
-def disk_refine_fn(n_base: int, half_size: float, r_in: float, r_out: float):
+def disk_refine_fn(n_base: int, half_size: float, r_in: float, r_out: float,
+                   zfac: Sequence[float] = (2.0,)):
     """Refine a node if it comes within 2 r_in of the star, or if it reaches below
-    twice the local scale height |z| < 2 h(r) inside the disk's radial range."""
+    zfac[level] times the local scale height, |z| < zfac h(r), inside the disk's radial
+    range (the last entry of zfac holds for deeper levels)."""
     d0 = 2.0 * half_size / n_base
 
     def refine(level, lo, hi):
@@ -476,7 +478,8 @@ def disk_refine_fn(n_base: int, half_size: float, r_in: float, r_out: float):
         zmin = np.where((lo_cm[:, 2] <= 0) & (hi_cm[:, 2] >= 0), 0.0,
                         np.minimum(np.abs(lo_cm[:, 2]), np.abs(hi_cm[:, 2])))
         near_star = np.hypot(rmin, zmin) < 2.0 * r_in
-        in_disk = (zmin < 2.0 * _disk_scale_height(rmax, r_in)) & (rmin <= r_out) & \
+        c = zfac[level] if level < len(zfac) else zfac[-1]
+        in_disk = (zmin < c * _disk_scale_height(rmax, r_in)) & (rmin <= r_out) & \
                   (rmax >= r_in)
         return near_star | in_disk
 
@@ -486,8 +489,8 @@ def disk_refine_fn(n_base: int, half_size: float, r_in: float, r_out: float):
 def disk_model(n_base: int = 128, max_level: int = 2, n_bins: int = 200,
                tau_v_mid: float = 1.0e3, half_size_au: float = 100.0,
                perturbed: bool = False, species: Optional[List[Species]] = None,
-               fractions: Optional[Sequence[float]] = None, n_sed_dirs: int = 1
-               ) -> Model:
+               fractions: Optional[Sequence[float]] = None, n_sed_dirs: int = 1,
+               refine_zfac: Sequence[float] = (2.0,)) -> Model:
     """Flared disk rho ~ r^-1 exp(-z^2/2h^2), h = 0.05 r_in (r/r_in)^1.125 over
     0.1-100 AU, in a cube of half-size ``half_size_au`` with ``max_level`` levels of
     2x2x2 refinement near the inner rim and the midplane; the density is scaled so that
@@ -499,7 +502,7 @@ def disk_model(n_base: int = 128, max_level: int = 2, n_bins: int = 200,
     sp = species if species is not None else two_species(nu)
     fr = fractions if fractions is not None else (MASS_FRACTION if len(sp) == 2 else
                                                   np.full(len(sp), 1.0 / len(sp)))
-    tree = build_tree(n_base, max_level, disk_refine_fn(n_base, H, r_in, r_out))
+    tree = build_tree(n_base, max_level, disk_refine_fn(n_base, H, r_in, r_out, refine_zfac))
     lo, hi = leaf_bounds_cm(tree, H)
     dens = _disk_cell_average(lo, hi, r_in, r_out, perturbed)
     rho = _split_species(dens, fr)
@@ -510,7 +513,8 @@ def disk_model(n_base: int = 128, max_level: int = 2, n_bins: int = 200,
                              tau_v_mid=tau_v_mid, half_size_au=half_size_au,
                              r_in_au=DISK_R_IN_AU, r_out_au=DISK_R_OUT_AU,
                              h0_over_rin=DISK_H0_OVER_RIN, flare=DISK_FLARE,
-                             perturbed=perturbed, fractions=list(map(float, fr))))
+                             perturbed=perturbed, fractions=list(map(float, fr)),
+                             refine_zfac=list(map(float, refine_zfac))))
 
 
 PAH_MASS_FRACTION = 0.05   # of the dust mass, split equally between the two PAH sizes
@@ -518,7 +522,8 @@ PAH_MASS_FRACTION = 0.05   # of the dust mass, split equally between the two PAH
 
 def disk_pah_model(n_base: int = 128, max_level: int = 2, n_bins: int = 200,
                    tau_v_mid: float = 1.0e3, perturbed: bool = True,
-                   pah_sizes: Sequence[int] = (30, 200)) -> Model:
+                   pah_sizes: Sequence[int] = (30, 200),
+                   refine_zfac: Sequence[float] = (2.0,)) -> Model:
     """The disk with the planet's gap and spiral and four species: silicate, amorphous
     carbon and two PAH sizes (30 and 200 C atoms) carrying PAH_MASS_FRACTION of the
     dust mass."""
@@ -527,10 +532,19 @@ def disk_pah_model(n_base: int = 128, max_level: int = 2, n_bins: int = 200,
     fr = list(MASS_FRACTION * (1.0 - PAH_MASS_FRACTION)) + \
         [PAH_MASS_FRACTION / len(pah_sizes)] * len(pah_sizes)
     m = disk_model(n_base=n_base, max_level=max_level, n_bins=n_bins, tau_v_mid=tau_v_mid,
-                   perturbed=perturbed, species=sp, fractions=fr)
+                   perturbed=perturbed, species=sp, fractions=fr, refine_zfac=refine_zfac)
     m.name = "disk_pah"
     m.recipe["pah_mass_fraction"] = PAH_MASS_FRACTION
     m.recipe["pah_sizes"] = list(pah_sizes)
+    return m
+
+
+def large_disk_model() -> Model:
+    """The large disk: gap, spiral and the four species of disk_pah_model on 256^3 base
+    cubes with three levels of refinement (|z| below 1, 0.5 and 0.25 scale heights for
+    the first, second and third split; 1.73e8 leaves) and 400 frequency bins."""
+    m = disk_pah_model(n_base=256, max_level=3, n_bins=400, refine_zfac=(1.0, 0.5, 0.25))
+    m.name = "large_disk"
     return m
 
 
