@@ -202,7 +202,7 @@ def run_reference(args):
 
 # DRAM traffic of the pool kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 2e6-package launch on the disk, scaled per package),
-# valid only for the kernel source it was measured on.
+# valid only for that workload and the kernel source it was measured on.
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
            "sha256": "e4701bbb50d62c83254828a7e02534f3a8c2981fd49a5167a77473a02d8c823e",
@@ -356,7 +356,8 @@ def run_ours(args):
     achieved = bytes_launch / kmean / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm,
-            "traffic": None if images else traffic_per_launch(n), "peak_source": src,
+            "traffic": traffic_per_launch(n) if args.workload == "disk" else None,
+            "peak_source": src,
             "kernel": "k_transport_pool" + (" (peel-off variant)" if images else ""),
             "kernel_ms": 1e3 * kmean,
             "algorithmic_bytes_per_launch": bytes_launch}
