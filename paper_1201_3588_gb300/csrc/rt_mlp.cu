@@ -1,6 +1,8 @@
 // rt_mlp.cu -- the multilayer perceptron of the PAH emission surrogate: forward
 // pass, mean-squared-error gradients and Adam, on tensor cores in BF16 with FP32
-// accumulation (WMMA m16n16k16 tiles).
+// accumulation. Inference runs the whole network per 128-row tile in one kernel on
+// the 5th-generation tensor cores (tcgen05.mma into tensor memory); training runs
+// layer by layer on WMMA m16n16k16 tiles.
 //
 // Network: a_0 = x; z_l = a_{l-1} W_l^T + b_l; a_l = silu(z_l) for the hidden layers,
 // linear output. Loss = mean over rows and outputs of (y - t)^2. Master weights,
@@ -51,6 +53,9 @@ struct rt_mlp {
   float* d_m = nullptr;
   float* d_v = nullptr;
   bf16* d_wbf = nullptr;     // padded BF16 weights
+  bf16* d_wpk = nullptr;     // the same weights in the tensor-core operand layout
+  bool pk_stale = true;      // d_wpk lags behind d_wbf
+  unsigned* d_err = nullptr; // fused forward: nonzero after a wait ran out
   float* d_loss = nullptr;
   long long step = 0;
   float x_lo = -1e30f, x_hi = 1e30f;  // admissible range of the second-to-last input
@@ -240,6 +245,281 @@ __global__ void k_unpack_output(const float* z, long long M, int n_out, int out_
   y[idx] = z[r * out_p + c];
 }
 
+
+// ---------------------------------------------------------------- fused forward
+// The whole forward pass of a 128-row tile in one CTA on the 5th-generation tensor
+// cores: per layer, the activations (BF16, shared memory) times the layer's weights
+// (BF16, shared memory) accumulate in FP32 in tensor memory (tcgen05.mma, issued by
+// one thread), then four warps read the accumulators back (tcgen05.ld), add the
+// bias, apply silu and write the next layer's activations. Every padded width must
+// be at most 256 (one MMA of M = 128, N = width per 16-wide K step).
+//
+// Operand layout in shared memory (no swizzle, K-major): 8-row x 16-byte core
+// matrices; the core holding (row r, column k) starts at (r/8)*SBO + (k/8)*128 bytes,
+// with SBO = (K/8)*128; inside it row r%8 is 16 bytes at (r%8)*16.
+constexpr int kTcRows = 128;
+constexpr int kTcMaxWidth = 256;
+constexpr unsigned long long kTcWaitNs = 2000000000ull;  // give up a wait after 2 s
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// element offset of (r, k) in a [rows][K] operand in the core-matrix layout
+__device__ __forceinline__ int core_off(int r, int k, int K) {
+  return (r >> 3) * (K << 3) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// shared-memory matrix descriptor: start, LBO (K direction) and SBO (row direction)
+// in 16-byte units, the fixed 0b001 at bits 46-48, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__device__ __forceinline__ uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ unsigned long long tc_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = tc_now_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity));
+    if (done) return true;
+    if (tc_now_ns() - t0 > kTcWaitNs) return false;
+  }
+}
+
+// one thread: the next phase of `bar` completes once `bytes` have arrived from the
+// bulk copy of [src, src + bytes) into shared memory at dst (16-byte aligned, size a
+// multiple of 16)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(
+          bar),
+      "r"(bytes)
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+      "[%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct TcNet {
+  int n_layers, n_in, n_out;
+  int in_p[kMaxLayers], out_p[kMaxLayers], n_valid[kMaxLayers];
+  const bf16* w[kMaxLayers];    // packed weights of each layer
+  const float* b[kMaxLayers];   // padded biases
+};
+
+// weights [out_p][in_p] row-major -> the core-matrix layout (one thread per element)
+__global__ void k_pack_weights(const bf16* w, int out_p, int in_p, bf16* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)out_p * in_p) return;
+  const int r = (int)(i / in_p), k = (int)(i % in_p);
+  out[core_off(r, k, in_p)] = w[i];
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(const __grid_constant__ TcNet net,
+                                                           const float* x, long long M,
+                                                           float* y, unsigned* err) {
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  bf16* sA = reinterpret_cast<bf16*>(tc_smem);                       // [128][256]
+  bf16* sB = sA + kTcRows * kTcMaxWidth;                             // [256][256]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + kTcMaxWidth * kTcMaxWidth);  // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(kTcMaxWidth));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar + 1)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t bar_a = smem_addr(bar);      // MMAs done
+  const uint32_t bar_w = smem_addr(bar + 1);  // weights arrived
+  uint32_t parity = 0, wparity = 0;
+  bool ok = true;
+  const long long n_tiles = (M + kTcRows - 1) / kTcRows;
+  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const long long r0 = tile * kTcRows;
+    // the first layer's weights stream in while the input is converted
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0)
+      bulk_load(smem_addr(sB), net.w[0], (uint32_t)(net.out_p[0] * net.in_p[0] * 2), bar_w);
+    // input rows -> BF16 activations: the tile's rows are contiguous in x, read
+    // coalesced; zero beyond the valid rows and in the padding columns
+    {
+      const int K = net.in_p[0], F = net.n_in;
+      const long long valid = M - r0 < kTcRows ? M - r0 : kTcRows;
+      const float* xt = x + r0 * F;
+      const int total = kTcRows * F, step = blockDim.x;
+      for (int i0 = tid; i0 < total; i0 += 8 * step) {
+        float v[8];  // eight loads in flight before the stores
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * step;
+          v[u] = (i < total && i / F < valid) ? __ldg(&xt[i]) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * step;
+          if (i < total) {
+            const int r = i / F, k = i - r * F;
+            sA[core_off(r, k, K)] = __float2bfloat16(v[u]);
+          }
+        }
+      }
+      for (int i = tid; i < kTcRows * (K - F); i += blockDim.x) {
+        const int r = i / (K - F), k = F + i % (K - F);
+        sA[core_off(r, k, K)] = __float2bfloat16(0.0f);
+      }
+    }
+    for (int l = 0; l < net.n_layers && ok; ++l) {
+      const int K = net.in_p[l], N = net.out_p[l];
+      // this layer's weights (bulk copy issued earlier)
+      const bool got_w = mbar_wait(bar_w, wparity);
+      if (!__syncthreads_and(got_w)) {
+        if (tid == 0) atomicOr(err, 1u);
+        ok = false;
+        const long long gr = r0 + tid;
+        if (gr < M)
+          for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
+        break;
+      }
+      wparity ^= 1u;
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t idesc = tc_idesc(kTcRows, N);
+        const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+        const uint32_t sbo = (uint32_t)K * 16u;  // (K/8) cores of 128 bytes
+        for (int kk = 0; kk < K / 16; ++kk)
+          tc_mma(tmem, tc_desc(a0 + kk * 256u, 128u, sbo), tc_desc(b0 + kk * 256u, 128u, sbo),
+                 idesc, kk > 0 ? 1u : 0u);
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                bar_a)
+            : "memory");
+      }
+      const bool waited = mbar_wait(bar_a, parity);
+      if (!__syncthreads_and(waited)) {  // the MMAs never signalled completion
+        if (tid == 0) atomicOr(err, 1u);
+        ok = false;
+        const long long gr = r0 + tid;
+        if (gr < M)
+          for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
+        break;
+      }
+      parity ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      // accumulators of this warp's 32 rows: bias, activation, next operand or output
+      const bool hidden = l < net.n_layers - 1;
+      // the weight buffer is free: the next layer's weights stream in meanwhile
+      if (hidden && tid == 0)
+        bulk_load(smem_addr(sB), net.w[l + 1], (uint32_t)(net.out_p[l + 1] * net.in_p[l + 1] * 2),
+                  bar_w);
+      const int row = warp * 32 + (tid & 31);
+      const float* bias = net.b[l];
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (hidden) {
+          __align__(16) bf16 h[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = c0 + j;
+            const float z = c < net.n_valid[l] ? v[j] + __ldg(&bias[c]) : 0.0f;
+            h[j] = __float2bfloat16(z / (1.0f + __expf(-z)));
+          }
+          // columns c0..c0+15 of this row: two 16-byte pieces of the next operand
+          *reinterpret_cast<uint4*>(&sA[core_off(row, c0, N)]) = *reinterpret_cast<uint4*>(&h[0]);
+          *reinterpret_cast<uint4*>(&sA[core_off(row, c0 + 8, N)]) =
+              *reinterpret_cast<uint4*>(&h[8]);
+        } else {
+          // outputs staged in the weight buffer (its MMA is done), written out below
+          float* so = reinterpret_cast<float*>(sB);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = c0 + j;
+            if (c < net.n_out) so[row * net.n_out + c] = v[j] + __ldg(&bias[c]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      if (!hidden) {  // the tile's output rows are contiguous in y: coalesced copy
+        const long long valid = M - r0 < kTcRows ? M - r0 : kTcRows;
+        const float* so = reinterpret_cast<const float*>(sB);
+        float* yt = y + r0 * net.n_out;
+        for (long long i = tid; i < valid * net.n_out; i += blockDim.x) yt[i] = so[i];
+        __syncthreads();
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTcMaxWidth));
+  }
+}
+
+size_t tc_smem_bytes() {
+  return sizeof(bf16) * (size_t)(kTcRows + kTcMaxWidth) * kTcMaxWidth + 32;
+}
+
+inline unsigned nb(long long n, int t);
+
 inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // ---------------------------------------------------------------- host helpers
@@ -313,6 +593,50 @@ rt_status ensure_rows(rt_mlp* m, long long Mp) {
 
 rt_status refresh_bf16(rt_mlp* m, cudaStream_t s) {
   k_to_bf16<<<nb((long long)m->n_padded, 256), 256, 0, s>>>(m->d_param, m->d_wbf, m->n_padded);
+  m->pk_stale = true;
+  return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ERR_CUDA;
+}
+
+// Every padded width fits one tensor-core MMA (N <= 256): the fused forward applies.
+bool tc_eligible(const rt_mlp* m) {
+  for (int l = 0; l < m->n_layers_total; ++l)
+    if (m->layer[l].in_p > kTcMaxWidth || m->layer[l].out_p > kTcMaxWidth) return false;
+  return true;
+}
+
+// forward of M rows with the fused tensor-core kernel (weights repacked when stale)
+rt_status forward_tc(rt_mlp* m, const float* x, float* y, long long M, cudaStream_t s) {
+  if (m->pk_stale) {
+    for (int l = 0; l < m->n_layers_total; ++l) {
+      const Layer& ly = m->layer[l];
+      k_pack_weights<<<nb((long long)ly.out_p * ly.in_p, 256), 256, 0, s>>>(
+          m->d_wbf + ly.w_off, ly.out_p, ly.in_p, m->d_wpk + ly.w_off);
+    }
+    if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
+    m->pk_stale = false;
+  }
+  TcNet net{};
+  net.n_layers = m->n_layers_total;
+  net.n_in = m->n_in;
+  net.n_out = m->n_out;
+  for (int l = 0; l < m->n_layers_total; ++l) {
+    const Layer& ly = m->layer[l];
+    net.in_p[l] = ly.in_p;
+    net.out_p[l] = ly.out_p;
+    net.n_valid[l] = ly.n_out;
+    net.w[l] = m->d_wpk + ly.w_off;
+    net.b[l] = m->d_param + ly.b_off;
+  }
+  const size_t smem = tc_smem_bytes();
+  if (cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return RT_ERR_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->dev) != cudaSuccess)
+    return RT_ERR_CUDA;
+  const long long tiles = (M + kTcRows - 1) / kTcRows;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+  k_mlp_forward_tc<<<grid, 128, smem, s>>>(net, x, M, y, m->d_err);
   return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ERR_CUDA;
 }
 
@@ -373,7 +697,8 @@ rt_status rt_mlp_create(int n_in, int n_hidden, int n_layers, int n_out, uint64_
   rt_status st;
   if ((st = alloc(&m->d_param, off)) != RT_OK || (st = alloc(&m->d_grad, off)) != RT_OK ||
       (st = alloc(&m->d_m, off)) != RT_OK || (st = alloc(&m->d_v, off)) != RT_OK ||
-      (st = alloc(&m->d_wbf, off)) != RT_OK || (st = alloc(&m->d_loss, 1)) != RT_OK) {
+      (st = alloc(&m->d_wbf, off)) != RT_OK || (st = alloc(&m->d_wpk, off)) != RT_OK ||
+      (st = alloc(&m->d_err, 1)) != RT_OK || (st = alloc(&m->d_loss, 1)) != RT_OK) {
     rt_mlp_destroy(m);
     return st;
   }
@@ -393,6 +718,7 @@ rt_status rt_mlp_create(int n_in, int n_hidden, int n_layers, int n_out, uint64_
   if (e == cudaSuccess) e = cudaMemset(m->d_m, 0, sizeof(float) * off);
   if (e == cudaSuccess) e = cudaMemset(m->d_v, 0, sizeof(float) * off);
   if (e == cudaSuccess) e = cudaMemset(m->d_grad, 0, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(unsigned));
   if (e != cudaSuccess || refresh_bf16(m, nullptr) != RT_OK) {
     rt_mlp_destroy(m);
     return RT_ERR_CUDA;
@@ -410,6 +736,8 @@ rt_status rt_mlp_destroy(rt_mlp* m) {
   release(m->d_m);
   release(m->d_v);
   release(m->d_wbf);
+  release(m->d_wpk);
+  release(m->d_err);
   release(m->d_loss);
   delete m;
   return RT_OK;
@@ -461,7 +789,11 @@ rt_status rt_mlp_get_params(rt_mlp* m, float* out) {
   if (!m || !out) return RT_ERR_ARG;
   if (cudaSetDevice(m->dev) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return RT_ERR_CUDA;
-  return copy_params(m, out, m->d_param);
+  unsigned err = 0;
+  if (cudaMemcpy(&err, m->d_err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RT_ERR_CUDA;
+  rt_status st = copy_params(m, out, m->d_param);
+  return st != RT_OK ? st : (err ? RT_ERR_TIMEOUT : RT_OK);
 }
 
 rt_status rt_mlp_set_params(rt_mlp* m, const float* in) {
@@ -486,6 +818,7 @@ rt_status rt_mlp_forward(rt_mlp* m, const float* x, float* y, int64_t M, void* s
   if (M == 0) return RT_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(m->dev) != cudaSuccess) return RT_ERR_CUDA;
+  if (tc_eligible(m)) return forward_tc(m, x, y, M, s);
   const long long chunk = 1ll << 18;
   for (long long r0 = 0; r0 < M; r0 += chunk) {
     long long Mc = M - r0 < chunk ? M - r0 : chunk;
