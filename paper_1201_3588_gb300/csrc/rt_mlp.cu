@@ -258,6 +258,8 @@ __global__ void k_unpack_output(const float* z, long long M, int n_out, int out_
 // matrices; the core holding (row r, column k) starts at (r/8)*SBO + (k/8)*128 bytes,
 // with SBO = (K/8)*128; inside it row r%8 is 16 bytes at (r%8)*16.
 constexpr int kTcRows = 128;
+constexpr int kTcThreads = 512;  // 16 warps: each reads its lane quarter of the
+                                 // accumulators, the column chunks shared by 4 warps
 constexpr int kTcMaxWidth = 256;
 constexpr unsigned long long kTcWaitNs = 2000000000ull;  // give up a wait after 2 s
 
@@ -357,7 +359,7 @@ __global__ void k_pack_weights(const bf16* w, int out_p, int in_p, bf16* out) {
   out[core_off(r, k, in_p)] = w[i];
 }
 
-__global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(const __grid_constant__ TcNet net,
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_constant__ TcNet net,
                                                            const float* x, long long M,
                                                            float* y, unsigned* err) {
   extern __shared__ __align__(128) unsigned char tc_smem[];
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(const __grid_constant
         if (tid == 0) atomicOr(err, 1u);
         ok = false;
         const long long gr = r0 + tid;
-        if (gr < M)
+        if (tid < kTcRows && gr < M)
           for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
         break;
       }
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(const __grid_constant
         if (tid == 0) atomicOr(err, 1u);
         ok = false;
         const long long gr = r0 + tid;
-        if (gr < M)
+        if (tid < kTcRows && gr < M)
           for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
         break;
       }
@@ -467,11 +469,13 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(const __grid_constant
       if (hidden && tid == 0)
         bulk_load(smem_addr(sB), net.w[l + 1], (uint32_t)(net.out_p[l + 1] * net.in_p[l + 1] * 2),
                   bar_w);
-      const int row = warp * 32 + (tid & 31);
+      const int quarter = warp & 3;                 // lanes 32 quarter .. of the accumulators
+      const int row = quarter * 32 + (tid & 31);
+      const int group = warp >> 2, n_groups = kTcThreads / 128;
       const float* bias = net.b[l];
-      for (int c0 = 0; c0 < N; c0 += 16) {
+      for (int c0 = 16 * group; c0 < N; c0 += 16 * n_groups) {
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
         if (hidden) {
           __align__(16) bf16 h[16];
 #pragma unroll
@@ -636,7 +640,7 @@ rt_status forward_tc(rt_mlp* m, const float* x, float* y, long long M, cudaStrea
     return RT_ERR_CUDA;
   const long long tiles = (M + kTcRows - 1) / kTcRows;
   const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-  k_mlp_forward_tc<<<grid, 128, smem, s>>>(net, x, M, y, m->d_err);
+  k_mlp_forward_tc<<<grid, kTcThreads, smem, s>>>(net, x, M, y, m->d_err);
   return cudaGetLastError() == cudaSuccess ? RT_OK : RT_ERR_CUDA;
 }
 
