@@ -152,6 +152,22 @@ __global__ void k_pack_input(const float* x, long long M, int n_in, long long Mp
   a0[idx] = __float2bfloat16(v);
 }
 
+// logistic sigmoid as 1/2 + tanh(z/2)/2, with the hardware tanh approximation
+// (relative error about 2^-11, below the BF16 rounding of the activations); both the
+// layer-by-layer path and the fused forward use it, so their activations agree
+__device__ __forceinline__ float sigmoid_fast(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+  return fmaf(0.5f, t, 0.5f);
+}
+
+__device__ __forceinline__ float silu_fast(float z) {
+  const float h = 0.5f * z;
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+  return fmaf(h, t, h);
+}
+
 // z += b; a = silu(z) (hidden) or copy (output); padded columns forced to zero
 __global__ void k_bias_act(float* z, const float* b, long long Mp, int out_p, int n_out,
                            int hidden, bf16* a) {
@@ -161,7 +177,7 @@ __global__ void k_bias_act(float* z, const float* b, long long Mp, int out_p, in
   float v = c < n_out ? z[idx] + b[c] : 0.0f;
   z[idx] = v;
   if (a) {
-    float y = hidden ? v / (1.0f + __expf(-v)) : v;
+    float y = hidden ? silu_fast(v) : v;
     a[idx] = __float2bfloat16(y);
   }
 }
@@ -195,7 +211,7 @@ __global__ void k_act_back(float* dz, const float* z, long long Mp, int p, int n
   float v = 0.0f;
   if (c < n_valid) {
     float zz = z[idx];
-    float s = 1.0f / (1.0f + __expf(-zz));
+    float s = sigmoid_fast(zz);
     v = dz[idx] * s * (1.0f + zz * (1.0f - s));
   }
   dz[idx] = v;
@@ -250,7 +266,7 @@ __global__ void k_unpack_output(const float* z, long long M, int n_out, int out_
 // The whole forward pass of a 128-row tile in one CTA on the 5th-generation tensor
 // cores: per layer, the activations (BF16, shared memory) times the layer's weights
 // (BF16, shared memory) accumulate in FP32 in tensor memory (tcgen05.mma, issued by
-// one thread), then four warps read the accumulators back (tcgen05.ld), add the
+// one thread), then 32 warps read the accumulators back (tcgen05.ld), add the
 // bias, apply silu and write the next layer's activations. Every padded width must
 // be at most 256 (one MMA of M = 128, N = width per 16-wide K step).
 //
@@ -258,8 +274,8 @@ __global__ void k_unpack_output(const float* z, long long M, int n_out, int out_
 // matrices; the core holding (row r, column k) starts at (r/8)*SBO + (k/8)*128 bytes,
 // with SBO = (K/8)*128; inside it row r%8 is 16 bytes at (r%8)*16.
 constexpr int kTcRows = 128;
-constexpr int kTcThreads = 512;  // 16 warps: each reads its lane quarter of the
-                                 // accumulators, the column chunks shared by 4 warps
+constexpr int kTcThreads = 1024;  // 32 warps: each reads its lane quarter of the
+                                  // accumulators, the column chunks shared by 8 warps
 constexpr int kTcMaxWidth = 256;
 constexpr unsigned long long kTcWaitNs = 2000000000ull;  // give up a wait after 2 s
 
@@ -365,9 +381,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
   extern __shared__ __align__(128) unsigned char tc_smem[];
   bf16* sA = reinterpret_cast<bf16*>(tc_smem);                       // [128][256]
   bf16* sB = sA + kTcRows * kTcMaxWidth;                             // [256][256]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + kTcMaxWidth * kTcMaxWidth);  // [2]
+  float* sBias = reinterpret_cast<float*>(sB + kTcMaxWidth * kTcMaxWidth);  // [layers][256]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sBias + kMaxLayers * kTcMaxWidth);  // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // biases of every layer, zero in the padding columns
+  for (int i = tid; i < net.n_layers * kTcMaxWidth; i += kTcThreads) {
+    const int l = i / kTcMaxWidth, c = i % kTcMaxWidth;
+    sBias[i] = c < net.n_valid[l] ? net.b[l][c] : 0.0f;
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_addr(tmem_slot)),
@@ -401,27 +423,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
       const int K = net.in_p[0], F = net.n_in;
       const long long valid = M - r0 < kTcRows ? M - r0 : kTcRows;
       const float* xt = x + r0 * F;
-      const int total = kTcRows * F, step = blockDim.x;
-      for (int i0 = tid; i0 < total; i0 += 8 * step) {
-        float v[8];  // eight loads in flight before the stores
+      const int total = kTcRows * F, n_ok = (int)valid * F;
+      // row of element i: (i + 1/2)/F lies at least 1/(2F) >= 2^-9 from an integer
+      // and i < 2^15, so the FP32 product truncates to floor(i/F) exactly
+      const float inv_f = 1.0f / (float)F;
+      for (int i0 = tid; i0 < total; i0 += 4 * kTcThreads) {
+        float v[4];  // four loads in flight before the stores
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = i0 + u * step;
-          v[u] = (i < total && i / F < valid) ? __ldg(&xt[i]) : 0.0f;
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * kTcThreads;
+          v[u] = i < n_ok ? __ldg(&xt[i]) : 0.0f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = i0 + u * step;
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * kTcThreads;
           if (i < total) {
-            const int r = i / F, k = i - r * F;
+            const int r = (int)(((float)i + 0.5f) * inv_f), k = i - r * F;
             sA[core_off(r, k, K)] = __float2bfloat16(v[u]);
           }
         }
       }
-      for (int i = tid; i < kTcRows * (K - F); i += blockDim.x) {
-        const int r = i / (K - F), k = F + i % (K - F);
-        sA[core_off(r, k, K)] = __float2bfloat16(0.0f);
-      }
+      if (tid < kTcRows)
+        for (int k = F; k < K; ++k) sA[core_off(tid, k, K)] = __float2bfloat16(0.0f);
     }
     for (int l = 0; l < net.n_layers && ok; ++l) {
       const int K = net.in_p[l], N = net.out_p[l];
@@ -470,41 +493,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
         bulk_load(smem_addr(sB), net.w[l + 1], (uint32_t)(net.out_p[l + 1] * net.in_p[l + 1] * 2),
                   bar_w);
       const int quarter = warp & 3;                 // lanes 32 quarter .. of the accumulators
-      const int row = quarter * 32 + (tid & 31);
+      const int row = quarter * 32 + lane;
       const int group = warp >> 2, n_groups = kTcThreads / 128;
-      const float* bias = net.b[l];
+      const float* bias = sBias + l * kTcMaxWidth;
+      // outputs are staged over both operand buffers (the last MMA is done) with an odd
+      // row stride, so that the 32 rows a warp stores hit 32 different banks
+      const int o_stride = net.n_out | 1;
+      float* so = reinterpret_cast<float*>(sA);
       for (int c0 = 16 * group; c0 < N; c0 += 16 * n_groups) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-        if (hidden) {
-          __align__(16) bf16 h[16];
+        float bv[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int c = c0 + j;
-            const float z = c < net.n_valid[l] ? v[j] + __ldg(&bias[c]) : 0.0f;
-            h[j] = __float2bfloat16(z / (1.0f + __expf(-z)));
+        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(&bv[j]) =
+            *reinterpret_cast<const float4*>(&bias[c0 + j]);
+        if (hidden) {
+          uint32_t h[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat162 p =
+                __floats2bfloat162_rn(silu_fast(v[2 * j] + bv[2 * j]),
+                                      silu_fast(v[2 * j + 1] + bv[2 * j + 1]));
+            h[j] = *reinterpret_cast<const uint32_t*>(&p);
           }
           // columns c0..c0+15 of this row: two 16-byte pieces of the next operand
-          *reinterpret_cast<uint4*>(&sA[core_off(row, c0, N)]) = *reinterpret_cast<uint4*>(&h[0]);
+          *reinterpret_cast<uint4*>(&sA[core_off(row, c0, N)]) = make_uint4(h[0], h[1], h[2], h[3]);
           *reinterpret_cast<uint4*>(&sA[core_off(row, c0 + 8, N)]) =
-              *reinterpret_cast<uint4*>(&h[8]);
+              make_uint4(h[4], h[5], h[6], h[7]);
         } else {
-          // outputs staged in the weight buffer (its MMA is done), written out below
-          float* so = reinterpret_cast<float*>(sB);
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int c = c0 + j;
-            if (c < net.n_out) so[row * net.n_out + c] = v[j] + __ldg(&bias[c]);
+            if (c < net.n_out) so[row * o_stride + c] = v[j] + bv[j];
           }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncthreads();
-      if (!hidden) {  // the tile's output rows are contiguous in y: coalesced copy
+      if (!hidden) {  // the tile's output rows are contiguous in y: coalesced copy by rows
         const long long valid = M - r0 < kTcRows ? M - r0 : kTcRows;
-        const float* so = reinterpret_cast<const float*>(sB);
         float* yt = y + r0 * net.n_out;
-        for (long long i = tid; i < valid * net.n_out; i += blockDim.x) yt[i] = so[i];
+        for (int r = warp; r < (int)valid; r += kTcThreads / 32)
+          for (int c = lane; c < net.n_out; c += 32) yt[(long long)r * net.n_out + c] = so[r * o_stride + c];
         __syncthreads();
       }
     }
@@ -519,7 +549,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
 }
 
 size_t tc_smem_bytes() {
-  return sizeof(bf16) * (size_t)(kTcRows + kTcMaxWidth) * kTcMaxWidth + 32;
+  return sizeof(bf16) * (size_t)(kTcRows + kTcMaxWidth) * kTcMaxWidth +
+         sizeof(float) * kMaxLayers * kTcMaxWidth + 32;
 }
 
 inline unsigned nb(long long n, int t);
