@@ -59,6 +59,8 @@ struct rt_grid {
   double* d_pah_ek = nullptr;
   int* d_pah_qk = nullptr;
   double* d_pah_wk = nullptr;
+  float* d_pah_cf = nullptr;
+  float* d_pah_wf = nullptr;
   float* d_pah_cdf = nullptr;
   float* d_pah_cell_cdf = nullptr;  // [n_pah][N][B] per-cell re-emission spectra
   unsigned* d_pahabs = nullptr;
@@ -157,6 +159,8 @@ void free_tables(rt_grid* g) {
   dfree(g->d_pah_ek);
   dfree(g->d_pah_qk);
   dfree(g->d_pah_wk);
+  dfree(g->d_pah_cf);
+  dfree(g->d_pah_wf);
   dfree(g->d_pah_cdf);
   g->tables_ready = false;
 }
@@ -237,6 +241,8 @@ rt_status build_pah_tables(rt_grid* g, cudaStream_t s) {
   if ((st = dalloc(&g->d_pah_ek, (size_t)K)) != RT_OK) return st;
   if ((st = dalloc(&g->d_pah_qk, (size_t)P * K)) != RT_OK) return st;
   if ((st = dalloc(&g->d_pah_wk, (size_t)P * K)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_pah_cf, (size_t)P * M)) != RT_OK) return st;
+  if ((st = dalloc(&g->d_pah_wf, (size_t)P * K)) != RT_OK) return st;
   if ((st = dalloc(&g->d_pah_cdf, (size_t)P * B)) != RT_OK) return st;
   if (!g->d_pahabs) {
     if ((st = dalloc(&g->d_pahabs, (size_t)P * g->desc.n_leaves * K)) != RT_OK) return st;
@@ -275,11 +281,15 @@ rt_status build_pah_tables(rt_grid* g, cudaStream_t s) {
   pb.q_k = g->d_pah_qk;
   pb.w_k = g->d_pah_wk;
   pb.template_cdf = g->d_pah_cdf;
+  pb.c_f = g->d_pah_cf;
+  pb.w_f = g->d_pah_wf;
   pt.s = g->d_pah_s;
   pt.L = g->d_pah_L;
   pt.e_k = g->d_pah_ek;
   pt.q_k = g->d_pah_qk;
   pt.w_k = g->d_pah_wk;
+  pt.c_f = g->d_pah_cf;
+  pt.w_f = g->d_pah_wf;
   RT_CUDA(launch_pah_tables(pb, pt, s));
   RT_CUDA(cudaStreamSynchronize(s));
   g->tab.pah_cdf = g->d_pah_cdf;

@@ -220,6 +220,8 @@ struct PahBuild {
   int* q_k;                  // [n_pah][K] floor(e_k / dE)
   double* w_k;               // [n_pah][K] e_k / dE - q_k
   float* template_cdf;       // [n_pah][B]
+  float* c_f;                // [n_pah][M] downward rate L_f / dE, 1/s (FP32 copy)
+  float* w_f;                // [n_pah][K] w_k (FP32 copy)
 };
 
 struct PahTables {
@@ -229,6 +231,8 @@ struct PahTables {
   const double* e_k;
   const int* q_k;
   const double* w_k;
+  const float* c_f;          // [n_pah][M] L_f / dE in FP32
+  const float* w_f;          // [n_pah][K] w_k in FP32
   double dE[kMaxPah];
   double mol_mass[kMaxPah];  // g per molecule
   int species[kMaxPah];      // species index of each PAH

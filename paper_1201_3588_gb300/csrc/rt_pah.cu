@@ -79,6 +79,13 @@ __global__ void k_pah_coarse(PahBuild pb) {
   pb.w_k[idx] = x - q;
 }
 
+// FP32 copies for the per-cell solution: c_f = L_f / dE and w_k
+__global__ void k_pah_f32(PahBuild pb) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < pb.n_pah * pb.M) pb.c_f[idx] = (float)(pb.L[idx] / pb.dE[idx / pb.M]);
+  if (idx < pb.n_pah * pb.K) pb.w_f[idx] = (float)pb.w_k[idx];
+}
+
 // Level populations of PAH p for absorption rates R[k] (smem, per molecule per
 // second), one warp; P and D are this warp's shared-memory arrays of M doubles.
 // Returns the emitted power sum_f P_f L_f of the normalised populations in P.
@@ -202,17 +209,90 @@ __global__ void k_pah_template(PahTables t, PahBuild pb) {
   if (lane == 0) cdf[pb.B - 1] = 1.0f;
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The same steady state in FP32, for the per-cell solutions (one warp; R, P, D in
+// this warp's shared memory, K rates and M levels). The upward flux across the
+// boundary below level f is summed afresh from the arrivals D_j, j >= f, of the
+// levels already solved, instead of being carried from level to level with the
+// arrivals at f subtracted: a sum of positive terms, with no cancellation, so
+// FP32 keeps about 1e-7 relative accuracy on every level that matters (the carried
+// difference lost several digits in FP32). Populations are kept below 1e20 by
+// rescaling (the normalised result is unchanged). Leaves the unnormalised
+// populations in P and returns their sum.
+__device__ float solve_levels_f32(const PahTables& t, int p, const float* R, float* P, float* D) {
+  const int lane = threadIdx.x & 31;
+  const int M = t.M, K = t.K;
+  const int* q = t.q_k + p * K;
+  const float* wf = t.w_f + p * K;
+  const float* cf = t.c_f + (size_t)p * M;
+  for (int i = lane; i < M; i += 32) {
+    D[i] = 0.0f;
+    P[i] = 0.0f;
+  }
+  // the highest level an absorption reaches above its start
+  int qmax = 0;
+  for (int k = lane; k < K; k += 32)
+    if (R[k] > 0.0f) qmax = max(qmax, q[k] + 1);
+  for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+  __syncwarp();
+  auto scatter = [&](int i, float Pi) {
+    for (int k = lane; k < K; k += 32) {
+      const float r = R[k];
+      if (!(r > 0.0f)) continue;
+      int f = i + q[k];
+      float wk = wf[k];
+      if (f >= M - 1) {
+        f = M - 1;
+        wk = 0.0f;
+      }
+      if (f > i) atomicAdd(&D[f], Pi * (r * (1.0f - wk)));
+      if (wk > 0.0f && f + 1 < M) atomicAdd(&D[f + 1], Pi * (r * wk));
+    }
+  };
+  if (lane == 0) P[0] = 1.0f;
+  scatter(0, 1.0f);
+  for (int f = 1; f < M; ++f) {
+    __syncwarp();
+    const int hi = min(M - 1, f - 1 + qmax);  // arrivals so far lie at or below hi
+    float F = 0.0f;
+    for (int j = f + lane; j <= hi; j += 32) F += D[j];
+    F = warp_sum_f(F);
+    const float C = cf[f];
+    float Pf = C > 0.0f ? F / C : 0.0f;
+    if (!(Pf <= 1e20f)) {  // rescale everything so far so that P_f = 1e20
+      const float sc = (1e20f * C) / F;
+      __syncwarp();
+      for (int j = lane; j < f; j += 32) P[j] *= sc;
+      for (int j = f + lane; j < M; j += 32) D[j] *= sc;
+      __syncwarp();
+      Pf = 1e20f;
+    }
+    if (lane == 0) P[f] = Pf;
+    scatter(f, Pf);
+  }
+  __syncwarp();
+  float tot = 0.0f;
+  for (int i = lane; i < M; i += 32) tot += P[i];
+  return warp_sum_f(tot);
+}
+
 // Exact emission of cells [first, first + n): one warp per cell, all PAH species;
-// j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin).
+// j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin), with the
+// populations from the FP32 level solution above. N_mol and the final scaling stay
+// in FP64 (N_mol can exceed the FP32 range).
 __global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, double eps,
                             double d0, long long first, long long n, float* j_out,
                             const unsigned char* want, int pah_only, const int* list) {
-  extern __shared__ double sm[];
+  extern __shared__ float smf[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_warp = t.K + 2 * t.M;
-  double* R = sm + (size_t)warp * per_warp;
-  double* P = R + t.K;
-  double* D = P + t.M;
+  float* R = smf + (size_t)warp * per_warp;
+  float* P = R + t.K;
+  float* D = P + t.M;
   const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
   if (i >= n) return;
   if (want && !want[i]) return;
@@ -228,20 +308,24 @@ __global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, doub
     const int s = t.species[p];
     const double rho = (double)g.rho[cell * g.S + s] / d0;
     const double n_mol = rho * V / t.mol_mass[p];
+    // absorption rate per molecule: count * eps / (e_k N_mol)
+    const float scale = n_mol > 0.0 ? (float)(eps / n_mol) : 0.0f;
     unsigned any = 0;
     for (int k = lane; k < t.K; k += 32) {
-      unsigned v = cnt[k];
+      const unsigned v = cnt[k];
       any |= v;
-      R[k] = n_mol > 0.0 ? (double)v * eps / (t.e_k[k] * n_mol) : 0.0;
+      R[k] = (float)v * scale / (float)t.e_k[k];
     }
-    if (!__any_sync(0xffffffffu, any != 0)) continue;
+    if (!__any_sync(0xffffffffu, any != 0) || !(n_mol > 0.0)) continue;
     __syncwarp();
-    solve_levels(t, p, R, P, D);
+    const float tot = solve_levels_f32(t, p, R, P, D);
+    const double norm = n_mol / (double)tot;
     for (int b = lane; b < g.B; b += 32) {
-      double j = 0.0;
+      float j = 0.0f;
       const float* sp = t.s + (size_t)p * t.M * g.B + b;
-      for (int f = 0; f < t.M; ++f) j += P[f] * (double)sp[(size_t)f * g.B];
-      out[b] += (float)(n_mol * j);
+#pragma unroll 8
+      for (int f = 0; f < t.M; ++f) j = fmaf(P[f], sp[(size_t)f * g.B], j);
+      out[b] += (float)(norm * (double)j);
     }
     __syncwarp();
   }
@@ -261,20 +345,22 @@ __global__ void k_pah_features(DevGrid g, PahTables t, const unsigned* pahabs, d
   const int F = t.K + 2;
   const unsigned* cnt = pahabs + ((size_t)p * g.n_leaves + cell) * t.K;
   float* x = X + (size_t)c * F;
-  double tot = 0.0;
-  for (int k = 0; k < t.K; ++k) tot += (double)cnt[k];
+  unsigned long long tot = 0;
+  for (int k = 0; k < t.K; ++k) tot += cnt[k];
   const int s = t.species[p];
   const double rho = (double)g.rho[cell * g.S + s] / d0;
   const int lev = g.level[cell];
   const double V = d0 * d0 * d0 / (double)(1ll << (3 * lev));
   const double n_mol = rho * V / t.mol_mass[p];
-  if (!(tot > 0.0) || !(n_mol > 0.0)) {
+  if (tot == 0 || !(n_mol > 0.0)) {
     for (int k = 0; k < F; ++k) x[k] = 0.0f;
     p_abs[c] = 0.0f;
     return;
   }
-  for (int k = 0; k < t.K; ++k) x[k] = (float)(log((double)cnt[k] / tot + 1e-4) / 4.6 + 1.0);
-  const double pw = tot * eps;
+  // the shape features in FP32 (they enter a BF16 network)
+  const float inv_tot = 1.0f / (float)tot;
+  for (int k = 0; k < t.K; ++k) x[k] = logf((float)cnt[k] * inv_tot + 1e-4f) * (1.0f / 4.6f) + 1.0f;
+  const double pw = (double)tot * eps;
   x[t.K] = (float)((log10(pw / n_mol) + 12.0) / 4.0);
   x[t.K + 1] = (float)(log10(t.n_carbon[p]) - 2.0);
   p_abs[c] = (float)pw;
@@ -287,7 +373,12 @@ __global__ void k_pah_encode(const float* J, const float* p_abs, long long n, in
   if (idx >= n * B) return;
   long long c = idx / B;
   float pa = p_abs[c];
-  Y[idx] = pa > 0.0f ? (float)(log((double)J[idx] / pa + 1e-6) / 7.0 + 1.0) : 0.0f;
+  Y[idx] = pa > 0.0f ? logf(J[idx] / pa + 1e-6f) * (1.0f / 7.0f) + 1.0f : 0.0f;
+}
+
+// decoded surrogate output of one bin: q = max(exp(7 (y - 1)) - 1e-6, 0), FP32
+__device__ __forceinline__ float decode_q(float y) {
+  return fmaxf(expf(7.0f * (y - 1.0f)) - 1e-6f, 0.0f);
 }
 
 // Decoded surrogate emission: q_b = max(exp(7 (y_b - 1)) - 1e-6, 0); the energy
@@ -300,12 +391,12 @@ __global__ void k_surrogate_check(const float* Y, const float* X, const float* p
   const int lane = threadIdx.x & 31;
   if (c >= n) return;
   if (!(p_abs[c] > 0.0f)) return;
-  double sum = 0.0;
-  for (int b = lane; b < B; b += 32) sum += fmax(exp(7.0 * ((double)Y[c * B + b] - 1.0)) - 1e-6, 0.0);
+  float sum = 0.0f;
+  for (int b = lane; b < B; b += 32) sum += decode_q(Y[c * B + b]);
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lane == 0) {
     const float xp = X[c * F + F - 2];
-    if (!(fabs(sum - 1.0) <= (double)tol) || xp < x_lo || xp > x_hi) flag[c] = 1;
+    if (!(fabsf(sum - 1.0f) <= tol) || xp < x_lo || xp > x_hi) flag[c] = 1;
   }
 }
 
@@ -317,15 +408,13 @@ __global__ void k_surrogate_add(const float* Y, const float* p_abs, long long n,
   if (c >= n) return;
   const float pa = p_abs[c];
   if (!(pa > 0.0f) || (flag && flag[c])) return;
-  double sum = 0.0;
-  for (int b = lane; b < B; b += 32) sum += fmax(exp(7.0 * ((double)Y[c * B + b] - 1.0)) - 1e-6, 0.0);
+  float sum = 0.0f;
+  for (int b = lane; b < B; b += 32) sum += decode_q(Y[c * B + b]);
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if (!(sum > 0.0)) return;
+  if (!(sum > 0.0f)) return;
   const long long row = list ? (long long)list[c] : c;
-  for (int b = lane; b < B; b += 32) {
-    double q = fmax(exp(7.0 * ((double)Y[c * B + b] - 1.0)) - 1e-6, 0.0);
-    j_out[row * B + b] += (float)((double)pa * q / sum);
-  }
+  const float f = pa / sum;
+  for (int b = lane; b < B; b += 32) j_out[row * B + b] += f * decode_q(Y[c * B + b]);
 }
 
 // Compaction: rows i < n with sel(i) true are appended to out (order not kept);
@@ -372,6 +461,8 @@ cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream
   k_pah_levels<<<(n + 63) / 64, 64, 0, s>>>(pb);
   int nk = pb.n_pah * pb.K;
   k_pah_coarse<<<(nk + 63) / 64, 64, 0, s>>>(pb);
+  const int nf = n > nk ? n : nk;
+  k_pah_f32<<<(nf + 63) / 64, 64, 0, s>>>(pb);
   size_t smem = sizeof(double) * (t.K + 2 * t.M);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_pah_template,
@@ -388,7 +479,7 @@ cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigne
                              cudaStream_t s, const int* list) {
   if (n <= 0) return cudaSuccess;
   const int warps = 4;
-  size_t smem = sizeof(double) * (size_t)warps * (t.K + 2 * t.M);
+  size_t smem = sizeof(float) * (size_t)warps * (t.K + 2 * t.M);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_pah_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
