@@ -269,7 +269,8 @@ def run_ours(args):
         img_dev = torch.empty((2, 256, 256), dtype=torch.float64, device=dev)
         prof_dev = torch.empty(256, dtype=torch.float64, device=dev)
     net, pah_info = None, {}
-    pah_chunk = 1 << 20
+    # cells per PAH-emission call: the output buffer held at <= 16 GiB
+    pah_chunk = max(1, min(N, (16 << 30) // (4 * B)))
     j_dev = torch.empty((min(pah_chunk, N), B), dtype=torch.float32, device=dev) if pah else None
 
     def pah_emission(mode=rt.PAH_AUTO, count=False):
@@ -421,13 +422,12 @@ def run_ours(args):
 
 
 def pah_launches(N, chunk, n_pah=2):
-    """Kernels of one surrogate pass over N cells, per chunk: the compaction of
-    PAH-active cells; per PAH features, network (input packing, a GEMM and a
-    bias/activation kernel per layer, output unpacking) and check; per PAH the add;
-    the compaction of failed cells and their exact solution."""
+    """Kernels of one surrogate pass over N cells, per call (chunk of cells): the
+    compaction of PAH-active cells; per batch of at most 2^20 of them (one batch on
+    these disks) and per PAH the features, the fused network and the check, per PAH
+    the add, and the compaction of failed cells; then their exact solution."""
     chunks = (N + chunk - 1) // chunk
-    per_pah = 1 + (1 + 4 * 2 + 1) + 1 + 1
-    return chunks * (n_pah * per_pah + 3)
+    return chunks * (1 + (3 * n_pah + n_pah + 1) + 1)
 
 
 def plain_rates(g, model, n_prefix, stream, c_pool, n_full):

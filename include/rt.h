@@ -301,8 +301,9 @@ rt_status rt_pah_absorbed(rt_grid *g, uint32_t *out, int mem, void *stream);
  * number `pah` when pah >= 0). Exact (RT_PAH_EXACT): for each cell and PAH, the
  * thermal-discrete steady state under the photon absorption rates its absorbed
  * spectrum implies (count * eps / (h nu_k N_molecules)), then N_molecules
- * sum_f P_f 4 pi sigma_b P_b(T_f), one warp per cell with FP64 populations; emitted
- * power equals absorbed power. RT_PAH_SURROGATE: the network `surrogate` (an rt_mlp
+ * sum_f P_f 4 pi sigma_b P_b(T_f), one warp per cell with FP32 populations (the
+ * upward flux across each level boundary summed afresh from the arrivals above it,
+ * so no cancellation); emitted power equals absorbed power. RT_PAH_SURROGATE: the network `surrogate` (an rt_mlp
  * with n_in = n_coarse + 2, n_out = n_bins, trained on rt_pah_training_pairs)
  * predicts each PAH's emission relative to its absorbed power (decoded as
  * q_b = exp(7 (y_b - 1)) - 1e-6, floored at 0); the prediction is rescaled to
@@ -310,7 +311,10 @@ rt_status rt_pah_absorbed(rt_grid *g, uint32_t *out, int mem, void *stream);
  * exact solution when for any PAH the prediction's energy residual |sum_b q_b - 1|
  * before rescaling exceeds `tol`, or its absorbed power per molecule lies outside
  * the range set with rt_mlp_set_range. *n_fallback_out (may be NULL) receives the
- * number of such cells. Synchronises only for a host output or a fallback count. */
+ * number of such cells. The PAH-active cells of the range are listed first; the
+ * surrogate runs over them in batches of up to 2^20 and the cells sent to the exact
+ * solution are solved in one launch at the end. Synchronises the stream to size that
+ * work (after listing the active cells and after the checks) and for a host output. */
 typedef struct rt_mlp rt_mlp;
 rt_status rt_pah_emission(rt_grid *g, int64_t first_cell, int64_t n_cells, int pah, int mode,
                           const rt_mlp *surrogate, float tol, float *j_out, int mem,

@@ -78,15 +78,15 @@ struct rt_grid {
   bool images = false;
   float* d_jscratch = nullptr;
   size_t jscratch_n = 0;
-  // surrogate scratch (cells per chunk)
-  long long sur_cap = 0;
-  float* d_sx = nullptr;       // [chunk][K+2]
-  float* d_sy = nullptr;       // [n_pah][chunk][B]
-  float* d_spabs = nullptr;    // [n_pah][chunk]
-  unsigned char* d_sflag = nullptr;
+  // surrogate scratch (rows per batch of active cells) and cell lists (per call)
+  long long sur_cap = 0, list_cap = 0;
+  float* d_sx = nullptr;       // [batch][K+2]
+  float* d_sy = nullptr;       // [n_pah][batch][B]
+  float* d_spabs = nullptr;    // [n_pah][batch]
+  unsigned char* d_sflag = nullptr;  // [batch]
   unsigned long long* d_scount = nullptr;
-  int* d_list = nullptr;       // [chunk] PAH-active cells of a chunk
-  int* d_list2 = nullptr;      // [chunk] cells sent to the exact solution
+  int* d_list = nullptr;       // [cells] PAH-active cells of the call
+  int* d_list2 = nullptr;      // [cells] cells sent to the exact solution
   unsigned* d_ucount = nullptr;  // [2]
   // host state
   std::vector<double> nu, kabs, ksca, ghg;   // [S][B]
@@ -1231,28 +1231,30 @@ rt_status rt_pah_temperature_distribution(const rt_pah_pt_case* cases, int n_cas
   return st;
 }
 
-// Work arrays of rt_pah_emission for `chunk` cells: cell lists always, the
-// network's inputs and outputs only when a surrogate is used.
-static rt_status surrogate_scratch(rt_grid* g, long long chunk, bool with_net) {
+// Work arrays of rt_pah_emission: cell lists for `cells` cells; the network's
+// inputs, outputs and flags for `batch` rows only when a surrogate is used.
+static rt_status surrogate_scratch(rt_grid* g, long long cells, long long batch, bool with_net) {
   const int K = g->tab.n_coarse, B = g->desc.n_bins, P = g->n_pah;
   rt_status st;
-  if (chunk > g->sur_cap) {
+  if (cells > g->list_cap) {
+    dfree(g->d_list);
+    dfree(g->d_list2);
+    g->list_cap = 0;
+    if ((st = dalloc(&g->d_list, (size_t)cells)) != RT_OK) return st;
+    if ((st = dalloc(&g->d_list2, (size_t)cells)) != RT_OK) return st;
+    g->list_cap = cells;
+  }
+  if (with_net && batch > g->sur_cap) {
     dfree(g->d_sx);
     dfree(g->d_sy);
     dfree(g->d_spabs);
     dfree(g->d_sflag);
-    dfree(g->d_list);
-    dfree(g->d_list2);
     g->sur_cap = 0;
-    if ((st = dalloc(&g->d_sflag, (size_t)chunk)) != RT_OK) return st;
-    if ((st = dalloc(&g->d_list, (size_t)chunk)) != RT_OK) return st;
-    if ((st = dalloc(&g->d_list2, (size_t)chunk)) != RT_OK) return st;
-    g->sur_cap = chunk;
-  }
-  if (with_net && !g->d_sx) {
-    if ((st = dalloc(&g->d_sx, (size_t)g->sur_cap * (K + 2))) != RT_OK) return st;
-    if ((st = dalloc(&g->d_sy, (size_t)P * g->sur_cap * B)) != RT_OK) return st;
-    if ((st = dalloc(&g->d_spabs, (size_t)P * g->sur_cap)) != RT_OK) return st;
+    if ((st = dalloc(&g->d_sflag, (size_t)batch)) != RT_OK) return st;
+    if ((st = dalloc(&g->d_sx, (size_t)batch * (K + 2))) != RT_OK) return st;
+    if ((st = dalloc(&g->d_sy, (size_t)P * batch * B)) != RT_OK) return st;
+    if ((st = dalloc(&g->d_spabs, (size_t)P * batch)) != RT_OK) return st;
+    g->sur_cap = batch;
   }
   if (!g->d_scount && (st = dalloc(&g->d_scount, 1)) != RT_OK) return st;
   if (!g->d_ucount && (st = dalloc(&g->d_ucount, 2)) != RT_OK) return st;
@@ -1301,53 +1303,54 @@ rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int p
   rt_mlp* m = const_cast<rt_mlp*>(surrogate);
   float x_lo = -1e30f, x_hi = 1e30f;
   if (m) rt_mlp_get_range(m, &x_lo, &x_hi);
-  const long long chunk = n_cells < (1ll << 20) ? n_cells : (1ll << 20);
-  if ((st = surrogate_scratch(g, chunk, mode != RT_PAH_EXACT)) != RT_OK) return st;
+  if ((st = surrogate_scratch(g, n_cells, 0, false)) != RT_OK) return st;
   const float t = mode == RT_PAH_AUTO ? tol : 1e30f;
   unsigned long long n_fallback = 0;
-  for (long long c0 = 0; c0 < n_cells; c0 += chunk) {
-    const long long nc = n_cells - c0 < chunk ? n_cells - c0 : chunk;
-    float* out = dst + (size_t)c0 * B;
-    RT_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * nc * B, s));
-    // the cells of this chunk where a PAH absorbed anything
-    RT_CUDA(cudaMemsetAsync(g->d_ucount, 0, 2 * sizeof(unsigned), s));
-    RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell + c0, nc,
-                           nullptr, nullptr, g->d_list, g->d_ucount, s));
-    unsigned na = 0;
-    RT_CUDA(cudaMemcpyAsync(&na, g->d_ucount, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
-    if (na == 0) continue;
-    if (mode == RT_PAH_EXACT) {
-      RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell + c0, na,
-                               out, nullptr, pah, s, g->d_list));
-      continue;
+  RT_CUDA(cudaMemsetAsync(dst, 0, sizeof(float) * n, s));
+  // the cells where a PAH absorbed anything, in one list for the whole range
+  RT_CUDA(cudaMemsetAsync(g->d_ucount, 0, 2 * sizeof(unsigned), s));
+  RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell, n_cells,
+                         nullptr, nullptr, g->d_list, g->d_ucount, s));
+  unsigned na = 0;
+  RT_CUDA(cudaMemcpyAsync(&na, g->d_ucount, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  RT_CUDA(cudaStreamSynchronize(s));
+  if (na > 0 && mode == RT_PAH_EXACT)
+    RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, na, dst,
+                             nullptr, pah, s, g->d_list));
+  if (na > 0 && mode != RT_PAH_EXACT) {
+    // the surrogate over batches of active cells; cells whose prediction fails its
+    // checks are appended to one fallback list, solved exactly in one launch
+    const long long batch = na < (1u << 20) ? (long long)na : (1ll << 20);
+    if ((st = surrogate_scratch(g, n_cells, batch, true)) != RT_OK) return st;
+    for (long long b0 = 0; b0 < (long long)na; b0 += batch) {
+      const long long nb = (long long)na - b0 < batch ? (long long)na - b0 : batch;
+      const int* lst = g->d_list + b0;
+      RT_CUDA(cudaMemsetAsync(g->d_sflag, 0, (size_t)nb, s));
+      for (int p = 0; p < g->n_pah; ++p) {
+        if (pah >= 0 && p != pah) continue;
+        float* Y = g->d_sy + (size_t)p * batch * B;
+        float* pa = g->d_spabs + (size_t)p * batch;
+        RT_CUDA(launch_pah_features(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, p, first_cell,
+                                    nb, g->d_sx, pa, s, lst));
+        if ((st = rt_mlp_forward(m, g->d_sx, Y, nb, s)) != RT_OK) return st;
+        RT_CUDA(launch_surrogate_check(Y, g->d_sx, pa, nb, B, F, t, x_lo, x_hi, g->d_sflag, s));
+      }
+      for (int p = 0; p < g->n_pah; ++p) {
+        if (pah >= 0 && p != pah) continue;
+        RT_CUDA(launch_surrogate_add(g->d_sy + (size_t)p * batch * B,
+                                     g->d_spabs + (size_t)p * batch, nb, B,
+                                     mode == RT_PAH_AUTO ? g->d_sflag : nullptr, dst, s, lst));
+      }
+      RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell, nb,
+                             g->d_sflag, lst, g->d_list2, g->d_ucount + 1, s));
     }
-    RT_CUDA(cudaMemsetAsync(g->d_sflag, 0, (size_t)na, s));
-    for (int p = 0; p < g->n_pah; ++p) {
-      if (pah >= 0 && p != pah) continue;
-      float* Y = g->d_sy + (size_t)p * chunk * B;
-      float* pa = g->d_spabs + (size_t)p * chunk;
-      RT_CUDA(launch_pah_features(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, p, first_cell + c0,
-                                  na, g->d_sx, pa, s, g->d_list));
-      if ((st = rt_mlp_forward(m, g->d_sx, Y, na, s)) != RT_OK) return st;
-      RT_CUDA(launch_surrogate_check(Y, g->d_sx, pa, na, B, F, t, x_lo, x_hi, g->d_sflag, s));
-    }
-    for (int p = 0; p < g->n_pah; ++p) {
-      if (pah >= 0 && p != pah) continue;
-      RT_CUDA(launch_surrogate_add(g->d_sy + (size_t)p * chunk * B, g->d_spabs + (size_t)p * chunk,
-                                   na, B, mode == RT_PAH_AUTO ? g->d_sflag : nullptr, out, s,
-                                   g->d_list));
-    }
-    // cells whose prediction failed its checks
-    RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell + c0, na,
-                           g->d_sflag, g->d_list, g->d_list2, g->d_ucount + 1, s));
     unsigned nf = 0;
     RT_CUDA(cudaMemcpyAsync(&nf, g->d_ucount + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     RT_CUDA(cudaStreamSynchronize(s));
-    n_fallback += nf;
+    n_fallback = nf;
     if (mode == RT_PAH_AUTO && nf > 0)
-      RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell + c0, nf,
-                               out, nullptr, pah, s, g->d_list2));
+      RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, nf, dst,
+                               nullptr, pah, s, g->d_list2));
   }
   if (n_fallback_out) *n_fallback_out = n_fallback;
   if (mem != RT_MEM_DEVICE) {
