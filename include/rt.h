@@ -396,10 +396,12 @@ rt_status rt_mlp_get_range(const rt_mlp *m, float *lo, float *hi);
 rt_status rt_mlp_get_params(rt_mlp *m, float *out);
 rt_status rt_mlp_set_params(rt_mlp *m, const float *in);  /* host [n_params] */
 
-/* y [M][n_out] = network(x [M][n_in]); device FP32 buffers; asynchronous. When every
- * padded layer width is at most 256 the whole network runs per 128-row tile in one
- * kernel on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulators in tensor
- * memory, BF16 operands in shared memory); otherwise layer by layer (WMMA). */
+/* y [M][n_out] = network(x [M][n_in]); device FP32 buffers; asynchronous. When the
+ * padded input and hidden widths are at most 256 (and the output width at most 4096)
+ * the whole network runs per 128-row tile in one kernel on the 5th-generation tensor
+ * cores (tcgen05.mma, FP32 accumulators in tensor memory, BF16 operands in shared
+ * memory; an output layer wider than 256 in chunks of 256 columns); otherwise layer
+ * by layer (WMMA). */
 rt_status rt_mlp_forward(rt_mlp *m, const float *x, float *y, int64_t M, void *stream);
 
 /* Loss and gradients of a batch (device x [M][n_in], targets t [M][n_out]) into the

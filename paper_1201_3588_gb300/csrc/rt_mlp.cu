@@ -267,8 +267,10 @@ __global__ void k_unpack_output(const float* z, long long M, int n_out, int out_
 // cores: per layer, the activations (BF16, shared memory) times the layer's weights
 // (BF16, shared memory) accumulate in FP32 in tensor memory (tcgen05.mma, issued by
 // one thread), then 32 warps read the accumulators back (tcgen05.ld), add the
-// bias, apply silu and write the next layer's activations. Every padded width must
-// be at most 256 (one MMA of M = 128, N = width per 16-wide K step).
+// bias, apply silu and write the next layer's activations. Every padded input and
+// hidden width must be at most 256 (one MMA of M = 128, N = width per 16-wide K
+// step); a wider output layer runs in chunks of 256 output columns, each its own
+// weight copy, MMAs and epilogue.
 //
 // Operand layout in shared memory (no swizzle, K-major): 8-row x 16-byte core
 // matrices; the core holding (row r, column k) starts at (r/8)*SBO + (k/8)*128 bytes,
@@ -277,6 +279,7 @@ constexpr int kTcRows = 128;
 constexpr int kTcThreads = 1024;  // 32 warps: each reads its lane quarter of the
                                   // accumulators, the column chunks shared by 8 warps
 constexpr int kTcMaxWidth = 256;
+constexpr int kTcMaxOut = 4096;  // output layer: up to 16 chunks of 256 columns
 constexpr unsigned long long kTcWaitNs = 2000000000ull;  // give up a wait after 2 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -415,8 +418,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
     // the first layer's weights stream in while the input is converted
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    if (tid == 0)
-      bulk_load(smem_addr(sB), net.w[0], (uint32_t)(net.out_p[0] * net.in_p[0] * 2), bar_w);
+    if (tid == 0) {
+      const int n0 = net.out_p[0] < kTcMaxWidth ? net.out_p[0] : kTcMaxWidth;
+      bulk_load(smem_addr(sB), net.w[0], (uint32_t)(n0 * net.in_p[0] * 2), bar_w);
+    }
     // input rows -> BF16 activations: the tile's rows are contiguous in x, read
     // coalesced; zero beyond the valid rows and in the padding columns
     {
@@ -446,96 +451,137 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
       if (tid < kTcRows)
         for (int k = F; k < K; ++k) sA[core_off(tid, k, K)] = __float2bfloat16(0.0f);
     }
+    // stages: (layer, chunk of at most 256 output columns); only the output layer
+    // may have more than one chunk (its packed weight rows are contiguous per chunk)
     for (int l = 0; l < net.n_layers && ok; ++l) {
-      const int K = net.in_p[l], N = net.out_p[l];
-      // this layer's weights (bulk copy issued earlier)
-      const bool got_w = mbar_wait(bar_w, wparity);
-      if (!__syncthreads_and(got_w)) {
-        if (tid == 0) atomicOr(err, 1u);
-        ok = false;
-        const long long gr = r0 + tid;
-        if (tid < kTcRows && gr < M)
-          for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
-        break;
-      }
-      wparity ^= 1u;
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t idesc = tc_idesc(kTcRows, N);
-        const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
-        const uint32_t sbo = (uint32_t)K * 16u;  // (K/8) cores of 128 bytes
-        for (int kk = 0; kk < K / 16; ++kk)
-          tc_mma(tmem, tc_desc(a0 + kk * 256u, 128u, sbo), tc_desc(b0 + kk * 256u, 128u, sbo),
-                 idesc, kk > 0 ? 1u : 0u);
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                bar_a)
-            : "memory");
-      }
-      const bool waited = mbar_wait(bar_a, parity);
-      if (!__syncthreads_and(waited)) {  // the MMAs never signalled completion
-        if (tid == 0) atomicOr(err, 1u);
-        ok = false;
-        const long long gr = r0 + tid;
-        if (tid < kTcRows && gr < M)
-          for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
-        break;
-      }
-      parity ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      // accumulators of this warp's 32 rows: bias, activation, next operand or output
+      const int K = net.in_p[l], Np = net.out_p[l];
       const bool hidden = l < net.n_layers - 1;
-      // the weight buffer is free: the next layer's weights stream in meanwhile
-      if (hidden && tid == 0)
-        bulk_load(smem_addr(sB), net.w[l + 1], (uint32_t)(net.out_p[l + 1] * net.in_p[l + 1] * 2),
-                  bar_w);
-      const int quarter = warp & 3;                 // lanes 32 quarter .. of the accumulators
-      const int row = quarter * 32 + lane;
-      const int group = warp >> 2, n_groups = kTcThreads / 128;
-      const float* bias = sBias + l * kTcMaxWidth;
-      // outputs are staged over both operand buffers (the last MMA is done) with an odd
-      // row stride, so that the 32 rows a warp stores hit 32 different banks
-      const int o_stride = net.n_out | 1;
-      float* so = reinterpret_cast<float*>(sA);
-      for (int c0 = 16 * group; c0 < N; c0 += 16 * n_groups) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-        float bv[16];
-#pragma unroll
-        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(&bv[j]) =
-            *reinterpret_cast<const float4*>(&bias[c0 + j]);
-        if (hidden) {
-          uint32_t h[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const __nv_bfloat162 p =
-                __floats2bfloat162_rn(silu_fast(v[2 * j] + bv[2 * j]),
-                                      silu_fast(v[2 * j + 1] + bv[2 * j + 1]));
-            h[j] = *reinterpret_cast<const uint32_t*>(&p);
-          }
-          // columns c0..c0+15 of this row: two 16-byte pieces of the next operand
-          *reinterpret_cast<uint4*>(&sA[core_off(row, c0, N)]) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(&sA[core_off(row, c0 + 8, N)]) =
-              make_uint4(h[4], h[5], h[6], h[7]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int c = c0 + j;
-            if (c < net.n_out) so[row * o_stride + c] = v[j] + bv[j];
+      const int n_chunks = (Np + kTcMaxWidth - 1) / kTcMaxWidth;
+      for (int ch = 0; ch < n_chunks && ok; ++ch) {
+        const int col0 = ch * kTcMaxWidth;                    // first output column
+        const int N = Np - col0 < kTcMaxWidth ? Np - col0 : kTcMaxWidth;
+        // this stage's weights (bulk copy issued earlier)
+        const bool got_w = mbar_wait(bar_w, wparity);
+        if (!__syncthreads_and(got_w)) {
+          if (tid == 0) atomicOr(err, 1u);
+          ok = false;
+          const long long gr = r0 + tid;
+          if (tid < kTcRows && gr < M)
+            for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
+          break;
+        }
+        wparity ^= 1u;
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t idesc = tc_idesc(kTcRows, N);
+          const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+          const uint32_t sbo = (uint32_t)K * 16u;  // (K/8) cores of 128 bytes
+          for (int kk = 0; kk < K / 16; ++kk)
+            tc_mma(tmem, tc_desc(a0 + kk * 256u, 128u, sbo), tc_desc(b0 + kk * 256u, 128u, sbo),
+                   idesc, kk > 0 ? 1u : 0u);
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                  bar_a)
+              : "memory");
+        }
+        const bool waited = mbar_wait(bar_a, parity);
+        if (!__syncthreads_and(waited)) {  // the MMAs never signalled completion
+          if (tid == 0) atomicOr(err, 1u);
+          ok = false;
+          const long long gr = r0 + tid;
+          if (tid < kTcRows && gr < M)
+            for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
+          break;
+        }
+        parity ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // the weight buffer is free: the next stage's weights stream in meanwhile
+        // (after a single-chunk output layer the buffer stages the outputs instead)
+        if (tid == 0) {
+          if (ch + 1 < n_chunks) {
+            const int n1 = Np - col0 - kTcMaxWidth < kTcMaxWidth ? Np - col0 - kTcMaxWidth
+                                                                : kTcMaxWidth;
+            bulk_load(smem_addr(sB), net.w[l] + (size_t)(col0 + kTcMaxWidth) * K,
+                      (uint32_t)(n1 * K * 2), bar_w);
+          } else if (hidden) {
+            const int n1 = net.out_p[l + 1] < kTcMaxWidth ? net.out_p[l + 1] : kTcMaxWidth;
+            bulk_load(smem_addr(sB), net.w[l + 1], (uint32_t)(n1 * net.in_p[l + 1] * 2), bar_w);
           }
         }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncthreads();
-      if (!hidden) {  // the tile's output rows are contiguous in y: coalesced copy by rows
-        const long long valid = M - r0 < kTcRows ? M - r0 : kTcRows;
-        float* yt = y + r0 * net.n_out;
-        for (int r = warp; r < (int)valid; r += kTcThreads / 32)
-          for (int c = lane; c < net.n_out; c += 32) yt[(long long)r * net.n_out + c] = so[r * o_stride + c];
+        // accumulators of this warp's 32 rows: bias, activation, next operand or output
+        const int quarter = warp & 3;                 // lanes 32 quarter .. of the accumulators
+        const int row = quarter * 32 + lane;
+        const int group = warp >> 2, n_groups = kTcThreads / 128;
+        const float* bias = sBias + l * kTcMaxWidth;
+        // a single-chunk output layer is staged over both operand buffers (the last MMA
+        // is done) with an odd row stride, so that the 32 rows a warp stores hit 32
+        // different banks; wider output layers are stored from registers per chunk
+        const int o_stride = net.n_out | 1;
+        float* so = reinterpret_cast<float*>(sA);
+        const long long grow = r0 + row;
+        const bool vec4 = (net.n_out & 3) == 0;
+        for (int c0 = 16 * group; c0 < N; c0 += 16 * n_groups) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+          float bv[16];
+          if (n_chunks == 1) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(&bv[j]) =
+                *reinterpret_cast<const float4*>(&bias[c0 + j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int c = col0 + c0 + j;
+              bv[j] = c < net.n_valid[l] ? __ldg(&net.b[l][c]) : 0.0f;
+            }
+          }
+          if (hidden) {
+            uint32_t h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const __nv_bfloat162 p =
+                  __floats2bfloat162_rn(silu_fast(v[2 * j] + bv[2 * j]),
+                                        silu_fast(v[2 * j + 1] + bv[2 * j + 1]));
+              h[j] = *reinterpret_cast<const uint32_t*>(&p);
+            }
+            // columns c0..c0+15 of this row: two 16-byte pieces of the next operand
+            *reinterpret_cast<uint4*>(&sA[core_off(row, c0, N)]) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(&sA[core_off(row, c0 + 8, N)]) =
+                make_uint4(h[4], h[5], h[6], h[7]);
+          } else if (n_chunks == 1) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int c = c0 + j;
+              if (c < net.n_out) so[row * o_stride + c] = v[j] + bv[j];
+            }
+          } else if (grow < M) {
+            float* yr = y + grow * net.n_out + col0 + c0;
+            if (vec4 && col0 + c0 + 16 <= net.n_out) {
+#pragma unroll
+              for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4*>(&yr[j]) =
+                    make_float4(v[j] + bv[j], v[j + 1] + bv[j + 1], v[j + 2] + bv[j + 2],
+                                v[j + 3] + bv[j + 3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (col0 + c0 + j < net.n_out) yr[j] = v[j] + bv[j];
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
+        if (!hidden && n_chunks == 1) {  // the tile's output rows are contiguous in y
+          const long long valid = M - r0 < kTcRows ? M - r0 : kTcRows;
+          float* yt = y + r0 * net.n_out;
+          for (int r = warp; r < (int)valid; r += kTcThreads / 32)
+            for (int c = lane; c < net.n_out; c += 32)
+              yt[(long long)r * net.n_out + c] = so[r * o_stride + c];
+          __syncthreads();
+        }
       }
     }
   }
@@ -634,8 +680,12 @@ rt_status refresh_bf16(rt_mlp* m, cudaStream_t s) {
 
 // Every padded width fits one tensor-core MMA (N <= 256): the fused forward applies.
 bool tc_eligible(const rt_mlp* m) {
-  for (int l = 0; l < m->n_layers_total; ++l)
-    if (m->layer[l].in_p > kTcMaxWidth || m->layer[l].out_p > kTcMaxWidth) return false;
+  const int L = m->n_layers_total;
+  for (int l = 0; l < L; ++l) {
+    if (m->layer[l].in_p > kTcMaxWidth) return false;
+    // hidden widths are one MMA; the output layer runs in chunks of 256 columns
+    if (m->layer[l].out_p > (l + 1 < L ? kTcMaxWidth : kTcMaxOut)) return false;
+  }
   return true;
 }
 

@@ -1,8 +1,9 @@
 """The fused tensor-core forward pass (tcgen05.mma into tensor memory) of the
 surrogate network: against the FP64 oracle within BF16 error, against the
 layer-by-layer WMMA forward of the training path (the same BF16 weights, so nearly
-identical), for ragged row counts, after the weights change, and with a layer too
-wide for it (the layer-by-layer path takes over)."""
+identical), for ragged row counts, after the weights change, with an output layer
+wider than one MMA (run in chunks of 256 columns), and with a hidden layer too wide
+for it (the layer-by-layer path takes over)."""
 import numpy as np
 import pytest
 
@@ -61,6 +62,22 @@ def test_fused_forward_follows_weight_updates():
     torch.cuda.synchronize()
     assert not torch.equal(y0, y1)
     _check_against_oracle(net, shapes, x, y1)
+
+
+@pytest.mark.parametrize("n_out,M", [(400, 1000), (400, 70_001), (258, 333), (514, 129)])
+def test_wide_output_layer_in_chunks(n_out, M):
+    # 400 bins (the large disk), and widths that leave a ragged last chunk (16 and 2
+    # columns past a multiple of 256; 258 and 514 are not multiples of 4)
+    net = rt.MLP(66, 256, 3, n_out, seed=11)
+    shapes = omlp.layer_shapes(66, 256, 3, n_out)
+    rng = np.random.default_rng(n_out + M)
+    x = rng.normal(size=(M, 66)).astype(np.float32)
+    y = torch.full((M, n_out), float("nan"), device="cuda")
+    net.forward(_dev(x), y)
+    torch.cuda.synchronize()
+    got = _check_against_oracle(net, shapes, x, y)
+    loss, _ = net.loss_grad(_dev(x), y.contiguous(), want_loss=True)
+    assert loss < 1e-6 * float((got ** 2).mean()), loss
 
 
 def test_too_wide_layers_use_the_layer_path():
