@@ -214,120 +214,159 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// The same steady state in FP32, for the per-cell solutions (one warp; R, P, D in
-// this warp's shared memory, K rates and M levels). The upward flux across the
-// boundary below level f is summed afresh from the arrivals D_j, j >= f, of the
-// levels already solved, instead of being carried from level to level with the
-// arrivals at f subtracted: a sum of positive terms, with no cancellation, so
-// FP32 keeps about 1e-7 relative accuracy on every level that matters (the carried
-// difference lost several digits in FP32). Populations are kept below 1e20 by
-// rescaling (the normalised result is unchanged). Leaves the unnormalised
-// populations in P and returns their sum.
-__device__ float solve_levels_f32(const PahTables& t, int p, const float* R, float* P, float* D) {
+// The same steady state in FP32, for the per-cell solutions (one warp; R, P, G in
+// this warp's shared memory, K rates and M levels). The levels are uniform, so the
+// rate from level i to the levels at or above f depends on f - i alone:
+// G(d) = sum over coarse bins of the rate landing d or more levels up (an absorption
+// split between i + q_k and i + q_k + 1, or cut at the top level, counts alike for
+// every f <= M - 1). The upward flux across the boundary below f is then
+// F_f = sum_{d >= 1} G(d) P_{f-d} -- the same quantity the carried recursion forms,
+// here as a dot product of positive terms, with no cancellation in FP32 (about 1e-7
+// relative on every level that matters) and no scatter. P_f = F_f / C_f. Populations
+// are kept below 1e20 by rescaling (the normalised result is unchanged). Leaves the
+// unnormalised populations in P and returns their sum.
+__device__ float solve_levels_f32(const PahTables& t, int p, const float* R, float* P, float* G) {
   const int lane = threadIdx.x & 31;
   const int M = t.M, K = t.K;
   const int* q = t.q_k + p * K;
   const float* wf = t.w_f + p * K;
   const float* cf = t.c_f + (size_t)p * M;
   for (int i = lane; i < M; i += 32) {
-    D[i] = 0.0f;
+    G[i] = 0.0f;
     P[i] = 0.0f;
   }
-  // the highest level an absorption reaches above its start
-  int qmax = 0;
-  for (int k = lane; k < K; k += 32)
-    if (R[k] > 0.0f) qmax = max(qmax, q[k] + 1);
-  for (int o = 16; o > 0; o >>= 1) qmax = max(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
   __syncwarp();
-  auto scatter = [&](int i, float Pi) {
-    for (int k = lane; k < K; k += 32) {
-      const float r = R[k];
-      if (!(r > 0.0f)) continue;
-      int f = i + q[k];
-      float wk = wf[k];
-      if (f >= M - 1) {
-        f = M - 1;
-        wk = 0.0f;
-      }
-      if (f > i) atomicAdd(&D[f], Pi * (r * (1.0f - wk)));
-      if (wk > 0.0f && f + 1 < M) atomicAdd(&D[f + 1], Pi * (r * wk));
+  // rate landing exactly d levels up, then its suffix sums G(d), d = 1 .. dmax
+  int dmax = 0;
+  for (int k = lane; k < K; k += 32) {
+    const float r = R[k];
+    if (!(r > 0.0f)) continue;
+    const int qq = min(q[k], M - 1);
+    const float w = wf[k];
+    if (qq >= 1) atomicAdd(&G[qq], r * (1.0f - w));
+    if (w > 0.0f) atomicAdd(&G[min(qq + 1, M - 1)], r * w);
+    dmax = max(dmax, min(qq + 1, M - 1));
+  }
+  for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  __syncwarp();
+  float carry = 0.0f;
+  for (int base = dmax & ~31; base >= 0; base -= 32) {
+    const int d = base + lane;
+    float v = (d >= 1 && d <= dmax) ? G[d] : 0.0f;
+    for (int o = 1; o < 32; o <<= 1) {  // suffix sums within the 32 entries
+      const float y = __shfl_down_sync(0xffffffffu, v, o);
+      if (lane + o < 32) v += y;
     }
-  };
+    v += carry;
+    carry = __shfl_sync(0xffffffffu, v, 0);
+    if (d >= 1 && d <= dmax) G[d] = v;
+  }
   if (lane == 0) P[0] = 1.0f;
-  scatter(0, 1.0f);
+  __syncwarp();
   for (int f = 1; f < M; ++f) {
-    __syncwarp();
-    const int hi = min(M - 1, f - 1 + qmax);  // arrivals so far lie at or below hi
+    const int hi = min(f, dmax);
     float F = 0.0f;
-    for (int j = f + lane; j <= hi; j += 32) F += D[j];
+    for (int d = 1 + lane; d <= hi; d += 32) F = fmaf(G[d], P[f - d], F);
     F = warp_sum_f(F);
     const float C = cf[f];
     float Pf = C > 0.0f ? F / C : 0.0f;
-    if (!(Pf <= 1e20f)) {  // rescale everything so far so that P_f = 1e20
+    if (!(Pf <= 1e20f)) {  // rescale the levels so far so that P_f = 1e20
       const float sc = (1e20f * C) / F;
-      __syncwarp();
       for (int j = lane; j < f; j += 32) P[j] *= sc;
-      for (int j = f + lane; j < M; j += 32) D[j] *= sc;
-      __syncwarp();
       Pf = 1e20f;
     }
     if (lane == 0) P[f] = Pf;
-    scatter(f, Pf);
+    __syncwarp();
   }
-  __syncwarp();
   float tot = 0.0f;
   for (int i = lane; i < M; i += 32) tot += P[i];
   return warp_sum_f(tot);
 }
 
-// Exact emission of cells [first, first + n): one warp per cell, all PAH species;
-// j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin), with the
-// populations from the FP32 level solution above. N_mol and the final scaling stay
-// in FP64 (N_mol can exceed the FP32 range).
-__global__ void k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, double eps,
-                            double d0, long long first, long long n, float* j_out,
-                            const unsigned char* want, int pah_only, const int* list) {
-  extern __shared__ float smf[];
+// Exact emission of cells [first, first + n): one warp per cell solves the level
+// populations (all PAH species in turn); the block's 8 warps then form the emission
+// of their 8 cells together, J_wb = sum_f P_wf s_fb, one thread per bin, so that each
+// row of the level table s (read from L2) serves 8 cells.
+// j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin). N_mol and the
+// final scaling stay in FP64 (N_mol can exceed the FP32 range).
+constexpr int kExactWarps = 8;
+
+__global__ void __launch_bounds__(32 * kExactWarps, 4)
+    k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, double eps, double d0,
+                long long first, long long n, float* j_out, const unsigned char* want,
+                int pah_only, const int* list) {
+  extern __shared__ __align__(16) float smf[];
+  __shared__ double s_norm[kExactWarps];   // N_mol / sum_f P_f, 0 without a solution
+  __shared__ long long s_row[kExactWarps];  // row of j_out
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per_warp = t.K + 2 * t.M;
+  const int Kp = (t.K + 3) & ~3, Mp = (t.M + 3) & ~3;  // 16-byte aligned arrays
+  const int per_warp = Kp + 2 * Mp;
   float* R = smf + (size_t)warp * per_warp;
-  float* P = R + t.K;
-  float* D = P + t.M;
-  const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (i >= n) return;
-  if (want && !want[i]) return;
-  const long long c = list ? (long long)list[i] : i;  // row of j_out (cell - first)
+  float* P = R + Kp;
+  float* G = P + Mp;
+  const long long i = (long long)blockIdx.x * kExactWarps + warp;
+  const bool active = i < n && !(want && !want[i]);
+  const long long c = active ? (list ? (long long)list[i] : i) : -1;  // cell - first
   const long long cell = first + c;
-  float* out = j_out + (size_t)c * g.B;
-  for (int b = lane; b < g.B; b += 32) out[b] = 0.0f;
-  const int lev = g.level[cell];
-  const double V = d0 * d0 * d0 / (double)(1ll << (3 * lev));
+  if (lane == 0) s_row[warp] = c;
+  if (active)
+    for (int b = lane; b < g.B; b += 32) j_out[(size_t)c * g.B + b] = 0.0f;
+  const double V = active ? d0 * d0 * d0 / (double)(1ll << (3 * g.level[cell])) : 0.0;
   for (int p = 0; p < t.n_pah; ++p) {
     if (pah_only >= 0 && p != pah_only) continue;
-    const unsigned* cnt = pahabs + ((size_t)p * g.n_leaves + cell) * t.K;
-    const int s = t.species[p];
-    const double rho = (double)g.rho[cell * g.S + s] / d0;
-    const double n_mol = rho * V / t.mol_mass[p];
-    // absorption rate per molecule: count * eps / (e_k N_mol)
-    const float scale = n_mol > 0.0 ? (float)(eps / n_mol) : 0.0f;
-    unsigned any = 0;
-    for (int k = lane; k < t.K; k += 32) {
-      const unsigned v = cnt[k];
-      any |= v;
-      R[k] = (float)v * scale / (float)t.e_k[k];
+    double norm = 0.0;
+    if (active) {
+      const unsigned* cnt = pahabs + ((size_t)p * g.n_leaves + cell) * t.K;
+      const int s = t.species[p];
+      const double rho = (double)g.rho[cell * g.S + s] / d0;
+      const double n_mol = rho * V / t.mol_mass[p];
+      // absorption rate per molecule: count * eps / (e_k N_mol)
+      const float scale = n_mol > 0.0 ? (float)(eps / n_mol) : 0.0f;
+      unsigned any = 0;
+      for (int k = lane; k < t.K; k += 32) {
+        const unsigned v = cnt[k];
+        any |= v;
+        R[k] = (float)v * scale / (float)t.e_k[k];
+      }
+      if (__any_sync(0xffffffffu, any != 0) && n_mol > 0.0) {
+        __syncwarp();
+        const float tot = solve_levels_f32(t, p, R, P, G);
+        norm = n_mol / (double)tot;
+      }
     }
-    if (!__any_sync(0xffffffffu, any != 0) || !(n_mol > 0.0)) continue;
-    __syncwarp();
-    const float tot = solve_levels_f32(t, p, R, P, D);
-    const double norm = n_mol / (double)tot;
-    for (int b = lane; b < g.B; b += 32) {
-      float j = 0.0f;
-      const float* sp = t.s + (size_t)p * t.M * g.B + b;
-#pragma unroll 8
-      for (int f = 0; f < t.M; ++f) j = fmaf(P[f], sp[(size_t)f * g.B], j);
-      out[b] += (float)(norm * (double)j);
+    if (lane == 0) s_norm[warp] = norm;
+    __syncthreads();
+    bool some = false;
+#pragma unroll
+    for (int w = 0; w < kExactWarps; ++w) some |= s_norm[w] > 0.0;
+    if (some) {
+      const float* Pw = smf + Kp;  // P of warp w at Pw + w * per_warp
+      for (int b = threadIdx.x; b < g.B; b += blockDim.x) {
+        float j[kExactWarps];
+#pragma unroll
+        for (int w = 0; w < kExactWarps; ++w) j[w] = 0.0f;
+        const float* sp = t.s + (size_t)p * t.M * g.B + b;
+        int f = 0;
+        for (; f + 2 <= t.M; f += 2) {
+          const float s0 = __ldg(sp + (size_t)f * g.B), s1 = __ldg(sp + (size_t)(f + 1) * g.B);
+#pragma unroll
+          for (int w = 0; w < kExactWarps; ++w) {
+            const float2 q = *reinterpret_cast<const float2*>(Pw + (size_t)w * per_warp + f);
+            j[w] = fmaf(q.x, s0, j[w]);
+            j[w] = fmaf(q.y, s1, j[w]);
+          }
+        }
+        for (; f < t.M; ++f) {
+          const float sf = __ldg(sp + (size_t)f * g.B);
+#pragma unroll
+          for (int w = 0; w < kExactWarps; ++w) j[w] = fmaf(Pw[(size_t)w * per_warp + f], sf, j[w]);
+        }
+#pragma unroll
+        for (int w = 0; w < kExactWarps; ++w)
+          if (s_norm[w] > 0.0) j_out[(size_t)s_row[w] * g.B + b] += (float)(s_norm[w] * (double)j[w]);
+      }
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -478,8 +517,8 @@ cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigne
                              float* j_out, const unsigned char* want, int pah_only,
                              cudaStream_t s, const int* list) {
   if (n <= 0) return cudaSuccess;
-  const int warps = 4;
-  size_t smem = sizeof(float) * (size_t)warps * (t.K + 2 * t.M);
+  const int warps = kExactWarps;
+  size_t smem = sizeof(float) * (size_t)warps * (((t.K + 3) & ~3) + 2 * ((t.M + 3) & ~3));
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_pah_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
