@@ -205,8 +205,8 @@ def run_reference(args):
 # valid only for that workload and the kernel source it was measured on.
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": "e4701bbb50d62c83254828a7e02534f3a8c2981fd49a5167a77473a02d8c823e",
-           "dram_bytes_per_package": 1080.7}
+           "sha256": "33f8421c15c0737709ce4225c18afb74753b779aee332e41b8845c8f9ff5e3e6",
+           "dram_bytes_per_package": 1083.2}
 
 
 def traffic_per_launch(n_packages):

@@ -412,6 +412,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
   const uint32_t bar_w = smem_addr(bar + 1);  // weights arrived
   uint32_t parity = 0, wparity = 0;
   bool ok = true;
+  uint32_t pend = 0;  // after a wait ran out: the barrier still owed a completion
   const long long n_tiles = (M + kTcRows - 1) / kTcRows;
   for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const long long r0 = tile * kTcRows;
@@ -465,6 +466,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
         if (!__syncthreads_and(got_w)) {
           if (tid == 0) atomicOr(err, 1u);
           ok = false;
+          pend = bar_w;
           const long long gr = r0 + tid;
           if (tid < kTcRows && gr < M)
             for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
@@ -491,6 +493,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
         if (!__syncthreads_and(waited)) {  // the MMAs never signalled completion
           if (tid == 0) atomicOr(err, 1u);
           ok = false;
+          pend = bar_a;
           const long long gr = r0 + tid;
           if (tid < kTcRows && gr < M)
             for (int c = 0; c < net.n_out; ++c) y[gr * net.n_out + c] = __int_as_float(0x7fc00000);
@@ -585,6 +588,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(const __grid_c
       }
     }
   }
+  // after a wait that ran out: let the weight copy or the MMAs still in flight land
+  // (again with a time limit) before the shared and tensor memory are released
+  if (pend != 0 && warp == 0) mbar_wait(pend, pend == bar_w ? wparity : parity);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
