@@ -193,7 +193,7 @@ __device__ __forceinline__ int locate(const DevGrid& g, const R p[3], const R d[
 template <typename R>
 struct Pkg {
   R p[3], d[3];
-  R inv[3];  // 1/d (unused where d == 0)
+  R inv[3];  // 1/d; +inf where d == 0 (of either sign)
   R tau;
   int bin;
   unsigned event;
@@ -215,7 +215,7 @@ enum Adv { kCrossed = 0, kInteract = 1, kEscaped = 2, kError = 3 };
 template <typename R>
 __device__ __forceinline__ void set_inverse(Pkg<R>& k) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) k.inv[a] = (R)1 / k.d[a];
+  for (int a = 0; a < 3; ++a) k.inv[a] = k.d[a] == (R)0 ? (R)INFINITY : (R)1 / k.d[a];
 }
 
 template <typename R>
@@ -297,17 +297,30 @@ __device__ __forceinline__ int advance(Pkg<R>& k, const DevGrid& g, const Kappa*
 }
 
 // ---------------------------------------------------------------- linked walk
-// The leaf a package is in, with its level and integer corner (at that level).
+// The leaf a package is in, with its level, its lower corner and its edge (base-cube
+// units; both exact in FP32: multiples of 2^-level below 2^13).
 struct Cell {
-  int leaf, level;
-  int I[3];
+  int leaf;
+  float lo[3];
+  float sz;  // 2^-level
+  __device__ __forceinline__ int level() const { return 127 - (__float_as_int(sz) >> 23); }
 };
+
+__device__ __forceinline__ void set_corner(Cell& c, const int I[3], int level) {
+  c.sz = __int_as_float((127 - level) << 23);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) c.lo[a] = (float)I[a] * c.sz;
+}
 
 // Enter the grid at the package's position (full descent from the base cube).
 __device__ __forceinline__ int enter(const Pkg<float>& k, const DevGrid& g, Cell& c,
                                      unsigned& child_reads) {
-  int rc = locate<float>(g, k.p, k.d, c.leaf, c.level, c.I);
-  if (rc == 0) child_reads += c.level;
+  int I[3], level;
+  int rc = locate<float>(g, k.p, k.d, c.leaf, level, I);
+  if (rc == 0) {
+    child_reads += level;
+    set_corner(c, I, level);
+  }
   return rc;
 }
 
@@ -322,30 +335,19 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
                                               unsigned& child_reads, float* pathabs,
                                               float* tau_los = nullptr) {
   // every array below is indexed with constants only, so it stays in registers
-  const float sz = __int_as_float((127 - c.level) << 23);  // 2^-level
-  const float lo0 = (float)c.I[0] * sz, lo1 = (float)c.I[1] * sz, lo2 = (float)c.I[2] * sz;
+  const float sz = c.sz;
+  const float lo0 = c.lo[0], lo1 = c.lo[1], lo2 = c.lo[2];
   const float hi0 = lo0 + sz, hi1 = lo1 + sz, hi2 = lo2 + sz;
   const float d0 = k.d[0], d1 = k.d[1], d2 = k.d[2];
-  const float t0 = d0 > 0.f ? (hi0 - k.p[0]) * k.inv[0]
-                            : (d0 < 0.f ? (lo0 - k.p[0]) * k.inv[0] : INFINITY);
-  const float t1 = d1 > 0.f ? (hi1 - k.p[1]) * k.inv[1]
-                            : (d1 < 0.f ? (lo1 - k.p[1]) * k.inv[1] : INFINITY);
-  const float t2 = d2 > 0.f ? (hi2 - k.p[2]) * k.inv[2]
-                            : (d2 < 0.f ? (lo2 - k.p[2]) * k.inv[2] : INFINITY);
+  // distance to the face ahead on each axis; an axis with d == 0 has inv = +inf and
+  // gives +inf, or NaN on its upper face, which the minimum below never picks
+  const float t0 = ((k.inv[0] > 0.f ? hi0 : lo0) - k.p[0]) * k.inv[0];
+  const float t1 = ((k.inv[1] > 0.f ? hi1 : lo1) - k.p[1]) * k.inv[1];
+  const float t2 = ((k.inv[2] > 0.f ? hi2 : lo2) - k.p[2]) * k.inv[2];
   // exit axis: the nearest face, the lowest axis on ties
-  int ax;
-  float tex;
-  if (t0 <= t1 && t0 <= t2) {
-    ax = 0;
-    tex = t0;
-  } else if (t1 <= t2) {
-    ax = 1;
-    tex = t1;
-  } else {
-    ax = 2;
-    tex = t2;
-  }
-  tex = fmaxf(tex, 0.f);
+  const float tmin = fminf(fminf(t0, t1), t2);
+  const int ax = t0 == tmin ? 0 : (t1 == tmin ? 1 : 2);
+  const float tex = fmaxf(tmin, 0.f);
   const float dax = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
   const bool up = dax > 0.f;
   const int* rec = g.links + (size_t)c.leaf * 8;
@@ -389,23 +391,33 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
   k.p[1] = ax == 1 ? f1 : fminf(hi1, fmaxf(lo1, k.p[1] + tex * d1));
   k.p[2] = ax == 2 ? f2 : fminf(hi2, fmaxf(lo2, k.p[2] + tex * d2));
   if (link == kLinkEscape) return kEscaped;
-  const int step = up ? 1 : -1;
-  int J0 = c.I[0] + (ax == 0 ? step : 0);
-  int J1 = c.I[1] + (ax == 1 ? step : 0);
-  int J2 = c.I[2] + (ax == 2 ? step : 0);
+  // the same-size neighbour's corner
+  const float step = up ? sz : -sz;
+  const float n0 = ax == 0 ? lo0 + step : lo0;
+  const float n1 = ax == 1 ? lo1 + step : lo1;
+  const float n2 = ax == 2 ? lo2 + step : lo2;
   if (link >= 0) {
     const int nl = link >> 28;
-    const int sh = c.level - nl;
+    const float nsz = __int_as_float((127 - nl) << 23);
     c.leaf = link & kLinkLeafMask;
-    c.level = nl;
-    c.I[0] = J0 >> sh;
-    c.I[1] = J1 >> sh;
-    c.I[2] = J2 >> sh;
+    if (nsz == sz) {
+      c.lo[0] = n0;
+      c.lo[1] = n1;
+      c.lo[2] = n2;
+    } else {  // a coarser leaf: round the corner down to its edge (exact)
+      c.sz = nsz;
+      const float isz = __int_as_float((127 + nl) << 23);
+      c.lo[0] = floorf(n0 * isz) * c.sz;
+      c.lo[1] = floorf(n1 * isz) * c.sz;
+      c.lo[2] = floorf(n2 * isz) * c.sz;
+    }
     return kCrossed;
   }
   // the same-size neighbour is split: descend, staying inside that node
+  int lev = c.level();
+  const float iz = __int_as_float((127 + lev) << 23);  // 2^level
+  int J0 = (int)(n0 * iz), J1 = (int)(n1 * iz), J2 = (int)(n2 * iz);
   long long blk = -(long long)link - 1;
-  int lev = c.level;
   for (;;) {
     if (blk >= g.n_blocks || lev >= g.max_level) return kError;
     ++lev;
@@ -422,10 +434,8 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
     if (node >= 0) {
       if ((long long)node >= g.n_leaves) return kError;
       c.leaf = node;
-      c.level = lev;
-      c.I[0] = J0;
-      c.I[1] = J1;
-      c.I[2] = J2;
+      const int I[3] = {J0, J1, J2};
+      set_corner(c, I, lev);
       return kCrossed;
     }
     blk = -(long long)node - 1;
@@ -611,7 +621,9 @@ __device__ __forceinline__ bool sight_line(const DevGrid& g, const Kappa* kap,
   Cell c;
   unsigned lv = 0;
   float tau = 0.f;
-  const int rc = locate<float>(g, k.p, k.d, c.leaf, c.level, c.I);
+  int I0[3], lev0;
+  const int rc = locate<float>(g, k.p, k.d, c.leaf, lev0, I0);
+  if (rc == 0) set_corner(c, I0, lev0);
   if (rc < 0) {
     atomicOr(status, kStatusTree);
     return false;
@@ -796,7 +808,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
   k.id = 0;
   bool alive = false;
   bool pending = false;  // reached an interaction point, waiting for the batch
-  Cell cell{0, 0, {0, 0, 0}};
+  Cell cell{0, {0.f, 0.f, 0.f}, 1.f};
   const int K = r.refill_period > 0 ? r.refill_period : 32;
   const int batch = r.interaction_batch > 0 ? r.interaction_batch : 8;
 
@@ -898,7 +910,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
         if (t.pah_of[sp] >= 0)
           pah_absorb<float>(k, g, t, r, t.pah_of[sp], cell.leaf, w1);
         else
-          reemit<float>(k, g, t, r, sp, cell.leaf, cell.level, old + __popc(peers & lt_mask),
+          reemit<float>(k, g, t, r, sp, cell.leaf, cell.level(), old + __popc(peers & lt_mask),
                         w1, tl);
         ++tl.absorptions;
       }
@@ -1012,7 +1024,7 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
   long long rec[9] = {0, 0, 0, 0, 0, 0, 0, 0, -1};
   const unsigned long long t0 = global_ns();
   unsigned steps = 0;
-  Cell c{0, 0, {0, 0, 0}};
+  Cell c{0, {0.f, 0.f, 0.f}, 1.f};
   int rc = enter(k, g, c, tl.levels);
   if (rc == 1) rec[4] = 1;
   if (rc < 0) atomicOr(r.status, kStatusTree);
@@ -1034,7 +1046,7 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
     if (t.pah_of[s] >= 0) {
       pah_bin(k, g, t, t.pah_of[s], c.leaf, w1);  // replay does not tally
     } else {
-      reemit<float>(k, g, t, r, s, c.leaf, c.level, 0ull, w1, tl);
+      reemit<float>(k, g, t, r, s, c.leaf, c.level(), 0ull, w1, tl);
     }
     ++rec[1];
   }
