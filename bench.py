@@ -205,8 +205,8 @@ def run_reference(args):
 # valid only for that workload and the kernel source it was measured on.
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": "33f8421c15c0737709ce4225c18afb74753b779aee332e41b8845c8f9ff5e3e6",
-           "dram_bytes_per_package": 1083.2}
+           "sha256": "f3d3dd13c506e8d1d474eb4950c08cc19d9a3582a324965646cdf01c0b970fd3",
+           "dram_bytes_per_package": 1080.8}
 
 
 def traffic_per_launch(n_packages):

@@ -1390,6 +1390,7 @@ struct rt_batch {
   unsigned long long* d_next = nullptr;
   long long n_chunks = 0;
   int blocks_per_sm = 0;
+  int s_fixed = 0;  // the species count every model shares (walk compiled for it), else 0
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -1467,6 +1468,9 @@ rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packag
   }
   b->n_chunks = (long long)chunks.size();
   b->blocks_per_sm = o ? o->blocks_per_sm : 0;
+  b->s_fixed = grids[0]->desc.n_species;
+  for (int m = 1; m < n; ++m)
+    if (grids[m]->desc.n_species != b->s_fixed) b->s_fixed = 0;
   if ((st = dalloc(&b->d_models, (size_t)n)) != RT_OK ||
       (st = dalloc(&b->d_chunks, chunks.size())) != RT_OK ||
       (st = dalloc(&b->d_next, 1)) != RT_OK) {
@@ -1498,7 +1502,7 @@ rt_status rt_batch_run(rt_batch* b, int reset, int temperatures, void* stream) {
   RT_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), s));
   if (b->n_chunks > 0)
     RT_CUDA(launch_transport_batch(b->d_models, b->d_chunks, b->n_chunks, b->d_next,
-                                   b->blocks_per_sm, s));
+                                   b->blocks_per_sm, b->s_fixed, s));
   if (temperatures)
     for (rt_grid* g : b->grids)
       RT_CUDA(launch_temperatures(g->g, g->tab, g->d_count, g->d_Tscratch, g->d_counters, s));

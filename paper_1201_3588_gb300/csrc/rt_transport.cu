@@ -329,7 +329,7 @@ __device__ __forceinline__ int enter(const Pkg<float>& k, const DevGrid& g, Cell
 // the next leaf is the linked one (same size or coarser), or is found by a short
 // descent when the neighbouring region is finer. kLos: a sight line, which never
 // interacts and adds the cell's optical depth to *tau_los instead.
-template <bool kLos = false>
+template <bool kLos = false, int kS = 0>
 __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevGrid& g,
                                               const Kappa* kap,
                                               unsigned& child_reads, float* pathabs,
@@ -352,11 +352,13 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
   const bool up = dax > 0.f;
   const int* rec = g.links + (size_t)c.leaf * 8;
   const int link = __ldg(rec + 2 * ax + (up ? 1 : 0));
-  const Kappa* kb = kap + k.bin * g.S;
+  // kS: the species count when fixed at compile time (2: both densities in the
+  // record), 0 when read from the grid
+  const Kappa* kb = kap + k.bin * (kS > 0 ? kS : g.S);
   float kx;
-  if (g.S <= 2) {
+  if (kS == 2 || (kS == 0 && g.S <= 2)) {
     kx = __int_as_float(__ldg(rec + 6)) * kb[0].kext;
-    if (g.S == 2) kx += __int_as_float(__ldg(rec + 7)) * kb[1].kext;
+    if (kS == 2 || g.S == 2) kx += __int_as_float(__ldg(rec + 7)) * kb[1].kext;
   } else {
     const float* rho = g.rho + (size_t)c.leaf * g.S;
     kx = 0.f;
@@ -794,7 +796,7 @@ struct RangeIds {
 // kPeel: scatterings and re-emissions at image bins are recorded (position, w,
 // bin) in the peel-off event buffer, one slot range per warp and phase; point-source
 // emissions are counted per bin in s_nemit.
-template <bool kPeel, class Ids>
+template <bool kPeel, class Ids, int kS = 0>
 __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, const DevRun& r,
                                           const Kappa* kap, const float* star_cdf,
                                           unsigned long long* sed, unsigned long long n_end,
@@ -853,7 +855,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
     for (int step = 0; step < K; ++step) {
       // walk phase: lanes not waiting for an interaction cross one cell
       if (alive && !pending) {
-        const int a = advance_linked(k, cell, g, kap, tl.levels, r.pathabs);
+        const int a = advance_linked<false, kS>(k, cell, g, kap, tl.levels, r.pathabs);
         if (a == kCrossed) {
           ++tl.crossings;
         } else if (a == kEscaped) {
@@ -941,7 +943,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
 // Persistent packet pool over one model: all warps draw package indices from one
 // global counter; the opacity table, the stellar CDF and (when it fits) the
 // escaped-spectrum histogram live in shared memory.
-template <int kMinBlocks, bool kPeel>
+template <int kMinBlocks, bool kPeel, int kS = 0>
 __global__ void __launch_bounds__(256, kMinBlocks)
     k_transport_pool(DevGrid g, DevTables t, DevRun r, const __grid_constant__ DevPeel pe) {
   extern __shared__ unsigned long long smem_u64[];
@@ -965,7 +967,7 @@ __global__ void __launch_bounds__(256, kMinBlocks)
   __syncthreads();
   Tally tl = {};
   GlobalIds ids{r.next};
-  pool_warp<kPeel>(g, t, r, s_kap, s_cdf, s_sed, r.n_packages, ids, tl, global_ns(), &pe,
+  pool_warp<kPeel, GlobalIds, kS>(g, t, r, s_kap, s_cdf, s_sed, r.n_packages, ids, tl, global_ns(), &pe,
                    s_nemit);
   flush_tally(tl, r.counters);
   if (sed_local || kPeel) __syncthreads();
@@ -984,6 +986,7 @@ __global__ void __launch_bounds__(256, kMinBlocks)
 // from a global queue, stage that model's descriptor in shared memory and run the
 // pool loop over the chunk (tables in global memory / L2, spectrum by global
 // atomics). Counters are flushed to the chunk's model when the chunk ends.
+template <int kS>
 __global__ void __launch_bounds__(256) k_transport_batch(const ModelDesc* models,
                                                          const BatchChunk* chunks,
                                                          long long n_chunks,
@@ -1004,8 +1007,8 @@ __global__ void __launch_bounds__(256) k_transport_batch(const ModelDesc* models
     const ModelDesc& md = sdesc[warp];
     Tally tl = {};
     RangeIds ids{ch.first};
-    pool_warp<false>(md.g, md.t, md.r, md.t.kap, md.t.star_cdf, md.r.sed, ch.first + ch.count,
-                     ids, tl, t0);
+    pool_warp<false, RangeIds, kS>(md.g, md.t, md.r, md.t.kap, md.t.star_cdf, md.r.sed,
+                                    ch.first + ch.count, ids, tl, t0);
     flush_tally(tl, md.r.counters);
     __syncwarp();
   }
@@ -1115,7 +1118,7 @@ static size_t sed_smem(const DevGrid& g) {
 
 static size_t peel_smem(const DevGrid& g) { return 16 + sizeof(unsigned long long) * g.B; }
 
-template <int kMinBlocks, bool kPeel>
+template <int kMinBlocks, bool kPeel, int kS = 0>
 static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, const DevRun& r,
                                        const DevPeel& pe, int blocks_per_sm, int threads,
                                        int sms, cudaStream_t s) {
@@ -1125,17 +1128,17 @@ static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, con
   size_t sm = table_smem(g) + extra + (rr.sed_in_smem ? sed_smem(g) : 0);
   cudaError_t e;
   if (sm > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_transport_pool<kMinBlocks, kPeel>,
+    e = cudaFuncSetAttribute(k_transport_pool<kMinBlocks, kPeel, kS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_pool<kMinBlocks, kPeel>,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_pool<kMinBlocks, kPeel, kS>,
                                                     threads, sm);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   int bps = blocks_per_sm > 0 ? (blocks_per_sm < occ ? blocks_per_sm : occ) : occ;
-  k_transport_pool<kMinBlocks, kPeel><<<sms * bps, threads, sm, s>>>(g, t, rr, pe);
+  k_transport_pool<kMinBlocks, kPeel, kS><<<sms * bps, threads, sm, s>>>(g, t, rr, pe);
   return cudaGetLastError();
 }
 
@@ -1151,12 +1154,17 @@ cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const De
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  if (peel && g.S == 2)
+    return launch_pool_variant<4, true, 2>(g, t, r, *peel, blocks_per_sm, threads, sms, s);
   if (peel) return launch_pool_variant<4, true>(g, t, r, *peel, blocks_per_sm, threads, sms, s);
   const DevPeel none{};
   if (threads == 256 && blocks_per_sm == 6)
     return launch_pool_variant<6, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
   if (threads == 256 && blocks_per_sm == 5)
     return launch_pool_variant<5, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
+  // two species: a walk compiled for the densities in the face-link record (a
+  // variant for four species reading them as one 16-byte load measured 4 % slower)
+  if (g.S == 2) return launch_pool_variant<4, false, 2>(g, t, r, none, blocks_per_sm, threads, sms, s);
   return launch_pool_variant<4, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
 }
 
@@ -1206,21 +1214,30 @@ cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const D
   return cudaGetLastError();
 }
 
-cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* chunks,
-                                   long long n_chunks, unsigned long long* next_chunk,
-                                   int blocks_per_sm, cudaStream_t s) {
+template <int kS>
+static cudaError_t launch_batch_variant(const ModelDesc* models, const BatchChunk* chunks,
+                                        long long n_chunks, unsigned long long* next_chunk,
+                                        int blocks_per_sm, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_batch, 256, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_batch<kS>, 256, 0);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
-  k_transport_batch<<<sms * bps, 256, 0, s>>>(models, chunks, n_chunks, next_chunk);
+  k_transport_batch<kS><<<sms * bps, 256, 0, s>>>(models, chunks, n_chunks, next_chunk);
   return cudaGetLastError();
+}
+
+cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* chunks,
+                                   long long n_chunks, unsigned long long* next_chunk,
+                                   int blocks_per_sm, int s_fixed, cudaStream_t s) {
+  if (s_fixed == 2)
+    return launch_batch_variant<2>(models, chunks, n_chunks, next_chunk, blocks_per_sm, s);
+  return launch_batch_variant<0>(models, chunks, n_chunks, next_chunk, blocks_per_sm, s);
 }
 
 cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
