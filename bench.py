@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--plain-packages", type=float, default=1e7)
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-one-thread", action="store_true",
+                   help="time the oracle on one host thread instead of one process per core")
     return p.parse_args()
 
 
@@ -154,23 +156,66 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(model, n_total, seconds, mode=0):
-    """Oracle packages/s on the host (one thread): packages 0, 1, 2 ... of the same
-    workload, in chunks, until `seconds` of CPU work have been spent."""
+def _oracle_prefix(model, first, n_total, seconds, mode=0):
+    """The oracle on one host thread: packages first, first + 1, ... of the workload,
+    in chunks, until `seconds` have passed. Returns (packages, seconds)."""
     import oracle
     om = oracle.OracleModel(model)
     tally = oracle.new_tally(om)
     done, chunk = 0, 4
     t0 = time.perf_counter()
     while True:
-        oracle.transport(om, chunk, seed=1000, first_id=done, n_total=n_total, mode=mode,
-                         tally=tally)
+        oracle.transport(om, chunk, seed=1000, first_id=first + done, n_total=n_total,
+                         mode=mode, tally=tally)
         done += chunk
         el = time.perf_counter() - t0
         if el >= seconds:
             break
         chunk = max(1, min(chunk * 2, int(done / el * (seconds - el)) + 1))
-    return done / el, done, el
+    return done, el
+
+
+_POOL_MODEL = None
+
+
+def _oracle_worker(job):
+    first, n_total, seconds, mode = job
+    return _oracle_prefix(_POOL_MODEL, first, n_total, seconds, mode)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool(model):
+    """One oracle process per host core, forked while the process has not touched
+    CUDA (they share the model's pages; none of them uses the GPU)."""
+    global _POOL_MODEL
+    _POOL_MODEL = model
+    import multiprocessing as mp
+    n = host_cores()
+    pool = mp.get_context("fork").Pool(n)
+    pool.n_workers = n
+    return pool
+
+
+def cpu_oracle_rate(model, n_total, seconds, mode=0, pool=None):
+    """Oracle packages/s on the host cores: with a pool, every process follows its
+    own range of package ids (disjoint, spread over the workload) for `seconds`;
+    packages of all processes / the longest wall time. Returns (rate, packages,
+    seconds, processes)."""
+    if pool is None:
+        done, el = _oracle_prefix(model, 0, n_total, seconds, mode)
+        return done / el, done, el, 1
+    w = pool.n_workers
+    stride = max(1, n_total // w)
+    res = pool.map(_oracle_worker, [(i * stride, n_total, seconds, mode) for i in range(w)])
+    done = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return done / el, done, el, w
 
 
 def run_reference(args):
@@ -178,14 +223,18 @@ def run_reference(args):
     if rank != 0:
         return
     model, desc = build_model(args.workload)
+    pool = oracle_pool(model) if not args.cpu_one_thread else None
     n_total = int(args.packages)
     per_step = max(1.0, args.cpu_seconds / 3.0)
     times, counts = [], []
     for i in range(args.warmup + args.steps):
-        rate, n, el = cpu_oracle_rate(model, n_total, per_step)
+        rate, n, el, cores = cpu_oracle_rate(model, n_total, per_step, pool=pool)
         if i >= args.warmup:
             times.append(el)
             counts.append(n)
+    if pool is not None:
+        pool.close()
+        pool.join()
     value = sum(counts) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -193,8 +242,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "packages_per_step": sum(counts) // len(counts),
                        "sample": "oracle prefix of the same workload"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{sum(counts)} packages over {args.steps} steps"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sum(counts)} packages over {args.steps} steps, "
+                                       f"{cores} processes on disjoint package ranges"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -240,11 +290,14 @@ def run_ours(args):
     from paper_1201_3588_gb300 import rt
 
     rank, world, local = dist_env()
+    model, desc = build_model(args.workload)
+    # the host-core oracle processes are forked before this process touches CUDA
+    pool = oracle_pool(model) if rank == 0 and args.cpu_seconds > 0 \
+        and not args.cpu_one_thread else None
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    model, desc = build_model(args.workload)
     n = int(args.packages)
     S, N, B = model.n_species, model.tree.n_leaves, model.n_bins
     stream = torch.cuda.Stream(device=dev)
@@ -390,7 +443,11 @@ def run_ours(args):
     e2e = e2e_rate(model, n, world, first, args.e2e_steps) \
         if args.e2e_steps > 0 and not pah and not images else None
     if rank == 0:
-        cpu_rate, cpu_n, cpu_s = cpu_oracle_rate(model, n * world, args.cpu_seconds)
+        cpu_rate, cpu_n, cpu_s, cpu_cores = cpu_oracle_rate(model, n * world, args.cpu_seconds,
+                                                            pool=pool)
+        if pool is not None:
+            pool.close()
+            pool.join()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -402,9 +459,11 @@ def run_ours(args):
                        "l2": f"inputs larger than L2: grid + counts "
                              f"{(4 * N * S + N + 8 * N * S) / 2**20:.0f} MiB > 129 MiB"},
             "roofline": roof,
-            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {cpu_n} packages of the same workload "
-                                       f"(BW mode, one thread, {cpu_s:.1f} s)"},
+            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_cores,
+                             "kind": "oracle",
+                             "sample": f"{cpu_n} packages of the same workload (BW mode, "
+                                       f"{cpu_cores} processes on disjoint package ranges, "
+                                       f"{cpu_s:.1f} s)"},
             "e2e": e2e,
             "gpu_launches": (2 + (pah_launches(N, pah_chunk) if pah else 0)
                              + (4 if images else 0)) * args.steps,
