@@ -209,36 +209,39 @@ __global__ void k_pah_template(PahTables t, PahBuild pb) {
   if (lane == 0) cdf[pb.B - 1] = 1.0f;
 }
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// Sum over the 4 lanes of a quad (lanes 4q .. 4q+3 of the warp).
+__device__ __forceinline__ float quad_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v + __shfl_xor_sync(0xffffffffu, v, 2);
 }
 
-// The same steady state in FP32, for the per-cell solutions (one warp; R, P, G in
-// this warp's shared memory, K rates and M levels). The levels are uniform, so the
-// rate from level i to the levels at or above f depends on f - i alone:
-// G(d) = sum over coarse bins of the rate landing d or more levels up (an absorption
-// split between i + q_k and i + q_k + 1, or cut at the top level, counts alike for
-// every f <= M - 1). The upward flux across the boundary below f is then
-// F_f = sum_{d >= 1} G(d) P_{f-d} -- the same quantity the carried recursion forms,
-// here as a dot product of positive terms, with no cancellation in FP32 (about 1e-7
-// relative on every level that matters) and no scatter. P_f = F_f / C_f. Populations
-// are kept below 1e20 by rescaling (the normalised result is unchanged). Leaves the
-// unnormalised populations in P and returns their sum.
+// The same steady state in FP32, for the per-cell solutions: one quad of 4 lanes
+// per cell (the 8 quads of a warp run in lockstep; a quad without a cell solves a
+// zero rate vector). R, P, G are the cell's shared-memory arrays (K rates, M
+// levels). The levels are uniform, so the rate from level i to the levels at or
+// above f depends on f - i alone: G(d) = sum over coarse bins of the rate landing d
+// or more levels up (an absorption split between i + q_k and i + q_k + 1, or cut at
+// the top level, counts alike for every f <= M - 1). The upward flux across the
+// boundary below f is then F_f = sum_{d >= 1} G(d) P_{f-d} -- the quantity the
+// carried recursion forms, here as a dot product of positive terms, with no
+// cancellation in FP32 (about 1e-7 relative on every level that matters) and no
+// scatter. P_f = F_f / C_f. Populations are kept below 1e20 by rescaling (the
+// normalised result is unchanged). Leaves the unnormalised populations in P and
+// returns their sum (in every lane of the quad).
 __device__ float solve_levels_f32(const PahTables& t, int p, const float* R, float* P, float* G) {
-  const int lane = threadIdx.x & 31;
+  const int j = threadIdx.x & 3;  // lane within the quad
   const int M = t.M, K = t.K;
   const int* q = t.q_k + p * K;
   const float* wf = t.w_f + p * K;
   const float* cf = t.c_f + (size_t)p * M;
-  for (int i = lane; i < M; i += 32) {
+  for (int i = j; i < M; i += 4) {
     G[i] = 0.0f;
     P[i] = 0.0f;
   }
   __syncwarp();
   // rate landing exactly d levels up, then its suffix sums G(d), d = 1 .. dmax
   int dmax = 0;
-  for (int k = lane; k < K; k += 32) {
+  for (int k = j; k < K; k += 4) {
     const float r = R[k];
     if (!(r > 0.0f)) continue;
     const int qq = min(q[k], M - 1);
@@ -247,123 +250,139 @@ __device__ float solve_levels_f32(const PahTables& t, int p, const float* R, flo
     if (w > 0.0f) atomicAdd(&G[min(qq + 1, M - 1)], r * w);
     dmax = max(dmax, min(qq + 1, M - 1));
   }
-  for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, 1));
+  dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, 2));
   __syncwarp();
-  float carry = 0.0f;
-  for (int base = dmax & ~31; base >= 0; base -= 32) {
-    const int d = base + lane;
-    float v = (d >= 1 && d <= dmax) ? G[d] : 0.0f;
-    for (int o = 1; o < 32; o <<= 1) {  // suffix sums within the 32 entries
-      const float y = __shfl_down_sync(0xffffffffu, v, o);
-      if (lane + o < 32) v += y;
+  {  // suffix sums over d = 1 .. dmax: four contiguous chunks, one per lane
+    const int len = (dmax + 3) >> 2;
+    const int lo = 1 + j * len, hi = min(dmax, lo + len - 1);
+    float part = 0.0f;
+    for (int d = lo; d <= hi; ++d) part += G[d];
+    // the sum of the chunks above this lane's
+    const float p1 = __shfl_down_sync(0xffffffffu, part, 1);
+    const float p2 = __shfl_down_sync(0xffffffffu, part, 2);
+    const float p3 = __shfl_down_sync(0xffffffffu, part, 3);
+    float above = (j < 3 ? p1 : 0.0f) + (j < 2 ? p2 : 0.0f) + (j < 1 ? p3 : 0.0f);
+    __syncwarp();
+    for (int d = hi; d >= lo; --d) {
+      above += G[d];
+      G[d] = above;
     }
-    v += carry;
-    carry = __shfl_sync(0xffffffffu, v, 0);
-    if (d >= 1 && d <= dmax) G[d] = v;
   }
-  if (lane == 0) P[0] = 1.0f;
+  if (j == 0) P[0] = 1.0f;
   __syncwarp();
   for (int f = 1; f < M; ++f) {
     const int hi = min(f, dmax);
-    float F = 0.0f;
-    for (int d = 1 + lane; d <= hi; d += 32) F = fmaf(G[d], P[f - d], F);
-    F = warp_sum_f(F);
+    float F0 = 0.0f, F1 = 0.0f;  // two chains
+    int d = 1 + j;
+    for (; d + 4 <= hi; d += 8) {
+      F0 = fmaf(G[d], P[f - d], F0);
+      F1 = fmaf(G[d + 4], P[f - d - 4], F1);
+    }
+    if (d <= hi) F0 = fmaf(G[d], P[f - d], F0);
+    const float F = quad_sum(F0 + F1);
     const float C = cf[f];
     float Pf = C > 0.0f ? F / C : 0.0f;
     if (!(Pf <= 1e20f)) {  // rescale the levels so far so that P_f = 1e20
       const float sc = (1e20f * C) / F;
-      for (int j = lane; j < f; j += 32) P[j] *= sc;
+      for (int i = j; i < f; i += 4) P[i] *= sc;
       Pf = 1e20f;
     }
-    if (lane == 0) P[f] = Pf;
+    if (j == 0) P[f] = Pf;
     __syncwarp();
   }
   float tot = 0.0f;
-  for (int i = lane; i < M; i += 32) tot += P[i];
-  return warp_sum_f(tot);
+  for (int i = j; i < M; i += 4) tot += P[i];
+  return quad_sum(tot);
 }
 
-// Exact emission of cells [first, first + n): one warp per cell solves the level
-// populations (all PAH species in turn); the block's 8 warps then form the emission
-// of their 8 cells together, J_wb = sum_f P_wf s_fb, one thread per bin, so that each
-// row of the level table s (read from L2) serves 8 cells.
-// j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin). N_mol and the
-// final scaling stay in FP64 (N_mol can exceed the FP32 range).
-constexpr int kExactWarps = 8;
+// Exact emission of cells [first, first + n): a quad of 4 lanes per cell solves
+// the level populations (all PAH species in turn); the block's cells (8 per warp)
+// then form their emission together, J_cb = sum_f P_cf s_fb, one thread per bin,
+// so that each row of the level table s (read from L2) serves every cell of the
+// block. j_out[c][b] = sum over PAH of N_mol sum_f P_f s_fb (erg/s per bin). N_mol
+// and the final scaling stay in FP64 (N_mol can exceed the FP32 range).
+constexpr int kExactCellsMax = 16;  // two warps of 8 quads
 
-__global__ void __launch_bounds__(32 * kExactWarps, 4)
+__device__ __forceinline__ int exact_cell_stride(int K, int M) {
+  // 16-byte aligned arrays, and a stride of 4 (mod 32) words: the 8 quads of a warp
+  // reading the same offset in their own arrays hit 8 different groups of 4 banks
+  const int w = ((K + 3) & ~3) + 2 * ((M + 3) & ~3);
+  return ((w + 31) & ~31) + 4;
+}
+
+__global__ void __launch_bounds__(32 * kExactCellsMax / 8)
     k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, double eps, double d0,
                 long long first, long long n, float* j_out, const unsigned char* want,
                 int pah_only, const int* list) {
   extern __shared__ __align__(16) float smf[];
-  __shared__ double s_norm[kExactWarps];   // N_mol / sum_f P_f, 0 without a solution
-  __shared__ long long s_row[kExactWarps];  // row of j_out
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int Kp = (t.K + 3) & ~3, Mp = (t.M + 3) & ~3;  // 16-byte aligned arrays
-  const int per_warp = Kp + 2 * Mp;
-  float* R = smf + (size_t)warp * per_warp;
+  __shared__ double s_norm[kExactCellsMax];   // N_mol / sum_f P_f, 0 without a solution
+  __shared__ long long s_row[kExactCellsMax];  // row of j_out
+  const int n_cells = blockDim.x >> 2;         // 8 per warp
+  const int slot = threadIdx.x >> 2, j = threadIdx.x & 3;
+  const int Kp = (t.K + 3) & ~3, Mp = (t.M + 3) & ~3;
+  const int CS = exact_cell_stride(t.K, t.M);
+  float* R = smf + (size_t)slot * CS;
   float* P = R + Kp;
   float* G = P + Mp;
-  const long long i = (long long)blockIdx.x * kExactWarps + warp;
+  const long long i = (long long)blockIdx.x * n_cells + slot;
   const bool active = i < n && !(want && !want[i]);
   const long long c = active ? (list ? (long long)list[i] : i) : -1;  // cell - first
   const long long cell = first + c;
-  if (lane == 0) s_row[warp] = c;
+  if (j == 0) s_row[slot] = c;
   if (active)
-    for (int b = lane; b < g.B; b += 32) j_out[(size_t)c * g.B + b] = 0.0f;
+    for (int b = j; b < g.B; b += 4) j_out[(size_t)c * g.B + b] = 0.0f;
   const double V = active ? d0 * d0 * d0 / (double)(1ll << (3 * g.level[cell])) : 0.0;
   for (int p = 0; p < t.n_pah; ++p) {
     if (pah_only >= 0 && p != pah_only) continue;
-    double norm = 0.0;
+    double norm = 0.0, n_mol = 0.0;
+    unsigned any = 0;
     if (active) {
       const unsigned* cnt = pahabs + ((size_t)p * g.n_leaves + cell) * t.K;
       const int s = t.species[p];
       const double rho = (double)g.rho[cell * g.S + s] / d0;
-      const double n_mol = rho * V / t.mol_mass[p];
+      n_mol = rho * V / t.mol_mass[p];
       // absorption rate per molecule: count * eps / (e_k N_mol)
       const float scale = n_mol > 0.0 ? (float)(eps / n_mol) : 0.0f;
-      unsigned any = 0;
-      for (int k = lane; k < t.K; k += 32) {
+      for (int k = j; k < t.K; k += 4) {
         const unsigned v = cnt[k];
         any |= v;
         R[k] = (float)v * scale / (float)t.e_k[k];
       }
-      if (__any_sync(0xffffffffu, any != 0) && n_mol > 0.0) {
-        __syncwarp();
-        const float tot = solve_levels_f32(t, p, R, P, G);
-        norm = n_mol / (double)tot;
-      }
+    } else {
+      for (int k = j; k < t.K; k += 4) R[k] = 0.0f;
     }
-    if (lane == 0) s_norm[warp] = norm;
+    any |= __shfl_xor_sync(0xffffffffu, any, 1);
+    any |= __shfl_xor_sync(0xffffffffu, any, 2);
+    __syncwarp();
+    // every quad of the warp solves (a zero rate vector where there is nothing to
+    // solve), so the warp stays converged for its shuffles
+    const bool work = __any_sync(0xffffffffu, any != 0 && n_mol > 0.0);
+    if (work) {
+      const float tot = solve_levels_f32(t, p, R, P, G);
+      if (any != 0 && n_mol > 0.0) norm = n_mol / (double)tot;
+    }
+    if (j == 0) s_norm[slot] = norm;
     __syncthreads();
     bool some = false;
-#pragma unroll
-    for (int w = 0; w < kExactWarps; ++w) some |= s_norm[w] > 0.0;
+    for (int w = 0; w < n_cells; ++w) some |= s_norm[w] > 0.0;
     if (some) {
-      const float* Pw = smf + Kp;  // P of warp w at Pw + w * per_warp
+      const float* Pc = smf + Kp;  // P of cell w at Pc + w * CS
       for (int b = threadIdx.x; b < g.B; b += blockDim.x) {
-        float j[kExactWarps];
+        float acc[kExactCellsMax];
 #pragma unroll
-        for (int w = 0; w < kExactWarps; ++w) j[w] = 0.0f;
+        for (int w = 0; w < kExactCellsMax; ++w) acc[w] = 0.0f;
         const float* sp = t.s + (size_t)p * t.M * g.B + b;
-        int f = 0;
-        for (; f + 2 <= t.M; f += 2) {
-          const float s0 = __ldg(sp + (size_t)f * g.B), s1 = __ldg(sp + (size_t)(f + 1) * g.B);
-#pragma unroll
-          for (int w = 0; w < kExactWarps; ++w) {
-            const float2 q = *reinterpret_cast<const float2*>(Pw + (size_t)w * per_warp + f);
-            j[w] = fmaf(q.x, s0, j[w]);
-            j[w] = fmaf(q.y, s1, j[w]);
-          }
-        }
-        for (; f < t.M; ++f) {
+        for (int f = 0; f < t.M; ++f) {
           const float sf = __ldg(sp + (size_t)f * g.B);
 #pragma unroll
-          for (int w = 0; w < kExactWarps; ++w) j[w] = fmaf(Pw[(size_t)w * per_warp + f], sf, j[w]);
+          for (int w = 0; w < kExactCellsMax; ++w)
+            if (w < n_cells) acc[w] = fmaf(Pc[(size_t)w * CS + f], sf, acc[w]);
         }
 #pragma unroll
-        for (int w = 0; w < kExactWarps; ++w)
-          if (s_norm[w] > 0.0) j_out[(size_t)s_row[w] * g.B + b] += (float)(s_norm[w] * (double)j[w]);
+        for (int w = 0; w < kExactCellsMax; ++w)
+          if (w < n_cells && s_norm[w] > 0.0)
+            j_out[(size_t)s_row[w] * g.B + b] += (float)(s_norm[w] * (double)acc[w]);
       }
     }
     __syncthreads();
@@ -517,16 +536,19 @@ cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigne
                              float* j_out, const unsigned char* want, int pah_only,
                              cudaStream_t s, const int* list) {
   if (n <= 0) return cudaSuccess;
-  const int warps = kExactWarps;
-  size_t smem = sizeof(float) * (size_t)warps * (((t.K + 3) & ~3) + 2 * ((t.M + 3) & ~3));
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_pah_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  long long blocks = (n + warps - 1) / warps;
-  k_pah_exact<<<(unsigned)blocks, 32 * warps, smem, s>>>(g, t, pahabs, eps, d0, first, n,
-                                                        j_out, want, pah_only, list);
+  const int w = ((t.K + 3) & ~3) + 2 * ((t.M + 3) & ~3);
+  const size_t per_cell = sizeof(float) * (size_t)(((w + 31) & ~31) + 4);
+  // 16 cells (two warps) per block when their arrays fit, else 8
+  int cells = kExactCellsMax;
+  if (per_cell * cells > 200 * 1024) cells = 8;
+  const size_t smem = per_cell * cells;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_pah_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  long long blocks = (n + cells - 1) / cells;
+  k_pah_exact<<<(unsigned)blocks, 4 * cells, smem, s>>>(g, t, pahabs, eps, d0, first, n,
+                                                       j_out, want, pah_only, list);
   return cudaGetLastError();
 }
 
