@@ -1,5 +1,5 @@
 """The learned part: the PAH emission surrogate trained on the GPU by the library's
-own kernels on exact transient-heating solutions of one disk, then judged on another
+own kernels on exact transient-heating solutions of one disk, then evaluated on another
 (held-out) disk against the exact solution: accuracy, energy balance, the fallback
 of flagged cells to the exact solution, and the time it saves."""
 import numpy as np
@@ -69,7 +69,7 @@ def test_surrogate_learns_and_gains():
           f"p90 {np.quantile(err_auto, 0.9):.4f}; fallback {nf} ({nf / n_cells:.3f}); "
           f"time exact {t_ex * 1e3:.1f} ms, surrogate {t_sur * 1e3:.1f} ms, "
           f"auto {t_auto * 1e3:.1f} ms")
-    # judged against the exact computation on held-out cells
+    # evaluated against the exact computation on held-out cells
     assert np.median(err) < 0.05 and np.quantile(err, 0.9) < 0.10
     assert np.quantile(err_auto, 0.9) <= np.quantile(err, 0.9) + 1e-6
     assert nf < 0.05 * n_cells
