@@ -456,30 +456,38 @@ __device__ __forceinline__ float hg_per_sr(float g, float mu) {
 // absorbing species. Returns the species (>= 0) for an absorption, -1 for a scatter.
 // peel_o / peel_w (peel-off): for a scattering, *peel_w receives the phase function
 // per steradian toward the unit vector peel_o, at the direction before the turn.
-template <typename R>
+// kS: the species count when fixed at compile time (2: the densities come from the
+// cell's face-link record, which the walk has just read), 0 when read from the grid.
+template <int kS>
+__device__ __forceinline__ float cell_rho(const DevGrid& g, int leaf, int s) {
+  if (kS == 2) return __int_as_float(__ldg(g.links + (size_t)leaf * 8 + 6 + s));
+  return __ldg(&g.rho[(size_t)leaf * g.S + s]);
+}
+
+template <typename R, int kS = 0>
 __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa* kap,
                                         int leaf, const DevRun& r, uint4& w1,
                                         const float* peel_o = nullptr,
                                         float* peel_w = nullptr) {
   uint4 w0 = draw(r.seed, k.id, k.event, 0u);
   w1 = draw(r.seed, k.id, k.event, 1u);
-  const float* rho = g.rho + (size_t)leaf * g.S;
-  const Kappa* kb = kap + k.bin * g.S;
+  const int S = kS > 0 ? kS : g.S;
+  const Kappa* kb = kap + k.bin * S;
   float ksca = 0.f, kext = 0.f, kabs = 0.f;
-  for (int s = 0; s < g.S; ++s) {
-    const float rs = __ldg(&rho[s]);
+  for (int s = 0; s < S; ++s) {
+    const float rs = cell_rho<kS>(g, leaf, s);
     ksca += rs * kb[s].ksca;
     kext += rs * kb[s].kext;
     kabs += rs * kb[s].kabs;
   }
   k.touched = true;
   const float xs = unit<float>(w0.y);
-  int sp = g.S - 1;
+  int sp = S - 1;
   if (unit<float>(w0.x) * kext < ksca) {
     const float target = xs * ksca;
     float cum = 0.f;
-    for (int s = 0; s < g.S; ++s) {
-      cum += __ldg(&rho[s]) * kb[s].ksca;
+    for (int s = 0; s < S; ++s) {
+      cum += cell_rho<kS>(g, leaf, s) * kb[s].ksca;
       if (cum > target) { sp = s; break; }
     }
     if (peel_w)
@@ -493,8 +501,8 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
   }
   const float target = xs * kabs;
   float cum = 0.f;
-  for (int s = 0; s < g.S; ++s) {
-    cum += __ldg(&rho[s]) * kb[s].kabs;
+  for (int s = 0; s < S; ++s) {
+    cum += cell_rho<kS>(g, leaf, s) * kb[s].kabs;
     if (cum > target) { sp = s; break; }
   }
   isotropic<R>(unit<R>(w0.z), unit<R>(w0.w), k.d);
@@ -505,13 +513,13 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
 
 // Interaction part 2 (absorption): n is this package's place in the cell's
 // absorption count (the count before it); draw the new bin.
-template <typename R>
+template <typename R, int kS = 0>
 __device__ __forceinline__ void reemit(Pkg<R>& k, const DevGrid& g, const DevTables& t,
                                        const DevRun& r, int s, int leaf, int level,
                                        unsigned long long n, const uint4& w1,
                                        Tally& tl) {
   float xu = unit<float>(w1.y), xb = unit<float>(w1.z);
-  float rho = __ldg(&g.rho[(size_t)leaf * g.S + s]);
+  float rho = cell_rho<kS>(g, leaf, s);
   float u;
   if (r.mode == 0) {
     float e = t.eps_d0_over_V[level] / rho;
@@ -889,8 +897,8 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
           ++tl.capped;
           alive = false;
         } else {
-          sp = interact<float>(k, g, kap, cell.leaf, r, w1, kPeel ? pe->o : nullptr,
-                               kPeel ? &wv : nullptr);
+          sp = interact<float, kS>(k, g, kap, cell.leaf, r, w1, kPeel ? pe->o : nullptr,
+                                   kPeel ? &wv : nullptr);
           if (sp < 0) {
             ++tl.scatters;
             scattered = true;
@@ -912,7 +920,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
         if (t.pah_of[sp] >= 0)
           pah_absorb<float>(k, g, t, r, t.pah_of[sp], cell.leaf, w1);
         else
-          reemit<float>(k, g, t, r, sp, cell.leaf, cell.level(), old + __popc(peers & lt_mask),
+          reemit<float, kS>(k, g, t, r, sp, cell.leaf, cell.level(), old + __popc(peers & lt_mask),
                         w1, tl);
         ++tl.absorptions;
       }
