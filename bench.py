@@ -255,8 +255,8 @@ def run_reference(args):
 # valid only for that workload and the kernel source it was measured on.
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": "f3d3dd13c506e8d1d474eb4950c08cc19d9a3582a324965646cdf01c0b970fd3",
-           "dram_bytes_per_package": 1080.8}
+           "sha256": "399e87fed13fa5113207886adb678989fda7c347c8b4dcfde5ae30573de64d14",
+           "dram_bytes_per_package": 1066.5}
 
 
 def traffic_per_launch(n_packages):
