@@ -1469,8 +1469,8 @@ rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packag
   b->n_chunks = (long long)chunks.size();
   b->blocks_per_sm = o ? o->blocks_per_sm : 0;
   b->s_fixed = grids[0]->desc.n_species;
-  for (int m = 1; m < n; ++m)
-    if (grids[m]->desc.n_species != b->s_fixed) b->s_fixed = 0;
+  for (int m = 0; m < n; ++m)  // the fixed-count walk runs without the path-length tally
+    if (grids[m]->desc.n_species != b->s_fixed || desc[(size_t)m].r.pathabs) b->s_fixed = 0;
   if ((st = dalloc(&b->d_models, (size_t)n)) != RT_OK ||
       (st = dalloc(&b->d_chunks, chunks.size())) != RT_OK ||
       (st = dalloc(&b->d_next, 1)) != RT_OK) {

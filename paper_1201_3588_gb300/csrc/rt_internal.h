@@ -134,8 +134,8 @@ struct BatchChunk {
 };
 
 // Kernel launchers (rt_transport.cu, rt_tables.cu).
-// s_fixed: the species count all models share (2 has a walk compiled for it), 0
-// otherwise
+// s_fixed: the species count all models share (2 has a walk compiled for it,
+// without the path-length tally), 0 otherwise
 cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* chunks,
                                    long long n_chunks, unsigned long long* next_chunk,
                                    int blocks_per_sm, int s_fixed, cudaStream_t s);

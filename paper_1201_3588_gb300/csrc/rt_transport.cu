@@ -863,7 +863,9 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
     for (int step = 0; step < K; ++step) {
       // walk phase: lanes not waiting for an interaction cross one cell
       if (alive && !pending) {
-        const int a = advance_linked<false, kS>(k, cell, g, kap, tl.levels, r.pathabs);
+        // the two-species form runs without the path-length tally (launched only then)
+        const int a = advance_linked<false, kS>(k, cell, g, kap, tl.levels,
+                                                kS == 2 ? nullptr : r.pathabs);
         if (a == kCrossed) {
           ++tl.crossings;
         } else if (a == kEscaped) {
@@ -1162,7 +1164,7 @@ cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const De
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  if (peel && g.S == 2)
+  if (peel && g.S == 2 && !r.pathabs)
     return launch_pool_variant<4, true, 2>(g, t, r, *peel, blocks_per_sm, threads, sms, s);
   if (peel) return launch_pool_variant<4, true>(g, t, r, *peel, blocks_per_sm, threads, sms, s);
   const DevPeel none{};
@@ -1172,7 +1174,8 @@ cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const De
     return launch_pool_variant<5, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
   // two species: a walk compiled for the densities in the face-link record (a
   // variant for four species reading them as one 16-byte load measured 4 % slower)
-  if (g.S == 2) return launch_pool_variant<4, false, 2>(g, t, r, none, blocks_per_sm, threads, sms, s);
+  if (g.S == 2 && !r.pathabs)
+    return launch_pool_variant<4, false, 2>(g, t, r, none, blocks_per_sm, threads, sms, s);
   return launch_pool_variant<4, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
 }
 
