@@ -255,8 +255,8 @@ def run_reference(args):
 # valid only for that workload and the kernel source it was measured on.
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": "399e87fed13fa5113207886adb678989fda7c347c8b4dcfde5ae30573de64d14",
-           "dram_bytes_per_package": 1066.5}
+           "sha256": "f8413be4ff53a8103a81e4494461311947f12906897bcd4c32bb0fc20c5cd976",
+           "dram_bytes_per_package": 1035.3}
 
 
 def traffic_per_launch(n_packages):
