@@ -252,22 +252,34 @@ def run_reference(args):
 
 # DRAM traffic of the pool kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum over a 2e6-package launch on the disk, scaled per package),
-# valid only for that workload and the kernel source it was measured on.
+# valid only for that workload and the kernel source it was measured on (the hash
+# covers the code of the sources with comments and blank lines removed).
 TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                        "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": "f8413be4ff53a8103a81e4494461311947f12906897bcd4c32bb0fc20c5cd976",
+           "sha256": "d50f24fa339fca45dfc7626db83c4a47413a6771b8e1acd8f0d2cc88bb82dfe8",
            "dram_bytes_per_package": 1035.3}
 
 
-def traffic_per_launch(n_packages):
+def source_code_hash(paths):
+    """SHA-256 of C/C++ sources with comments, trailing blanks and empty lines
+    removed, so that an edit of a comment does not void a capture."""
     import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in paths:
+        with open(os.path.join(ROOT, f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln).encode())
+    return h.hexdigest()
+
+
+def traffic_per_launch(n_packages):
     if not TRAFFIC["sha256"] or not TRAFFIC["dram_bytes_per_package"]:
         return None
-    h = hashlib.sha256()
-    for f in TRAFFIC["sources"]:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest() != TRAFFIC["sha256"]:
+    if source_code_hash(TRAFFIC["sources"]) != TRAFFIC["sha256"]:
         return None
     return TRAFFIC["dram_bytes_per_package"] * n_packages
 

@@ -1153,9 +1153,10 @@ static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, con
 }
 
 // blocks_per_sm selects the register budget: 5 or 6 resident blocks of 256 threads
-// use variants compiled for that occupancy (fewer registers, some spills); other
-// values use the 4-block variant (no spills), capped at its occupancy.
-// With peel-off images the 4-block variant is used.
+// use variants compiled for that occupancy (fewer registers, more spills); other
+// values use the 4-block variants, capped at their occupancy: the two-species one
+// (no spills; used when the path-length tally is off) or the generic one (8 bytes
+// of spills). With peel-off images the 4-block variants are used.
 cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
                                   int blocks_per_sm, int threads, cudaStream_t s,
                                   const DevPeel* peel) {
