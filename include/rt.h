@@ -301,9 +301,9 @@ rt_status rt_pah_absorbed(rt_grid *g, uint32_t *out, int mem, void *stream);
  * number `pah` when pah >= 0). Exact (RT_PAH_EXACT): for each cell and PAH, the
  * thermal-discrete steady state under the photon absorption rates its absorbed
  * spectrum implies (count * eps / (h nu_k N_molecules)), then N_molecules
- * sum_f P_f 4 pi sigma_b P_b(T_f), one warp per cell with FP32 populations (the
- * upward flux across each level boundary summed afresh from the arrivals above it,
- * so no cancellation); emitted power equals absorbed power. RT_PAH_SURROGATE: the network `surrogate` (an rt_mlp
+ * sum_f P_f 4 pi sigma_b P_b(T_f), a quad of four lanes per cell with FP32
+ * populations (the upward flux across each level boundary summed afresh from the
+ * arrivals above it, so no cancellation); emitted power equals absorbed power. RT_PAH_SURROGATE: the network `surrogate` (an rt_mlp
  * with n_in = n_coarse + 2, n_out = n_bins, trained on rt_pah_training_pairs)
  * predicts each PAH's emission relative to its absorbed power (decoded as
  * q_b = exp(7 (y_b - 1)) - 1e-6, floored at 0); the prediction is rescaled to
@@ -421,10 +421,10 @@ const char *rt_status_string(rt_status s);
  * Who needs it: code that owns all of its device memory and may not call
  * cudaMalloc at the point where temperatures are wanted -- a framework that hands
  * out memory only from its own pool (a stray cudaMalloc would synchronise the
- * device and fragment the pool), or a pipeline being recorded by stream capture,
- * during which allocation is not allowed. Such a caller passes every input and the
- * output as its own device buffers; this entry point then allocates nothing: no
- * cudaMalloc, no cudaFree, no allocating library routine.
+ * device and fragment the pool), or a host process whose memory budget on the
+ * GPU is fixed up front. Such a caller passes every input and the output as its
+ * own device buffers; this entry point then allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
  *
  * It computes what rt_cell_temperatures computes: T from
  * n eps = rho V 4 pi sum_b kappa_abs(b) P_b(T), inverted in FP64, 0 where n = 0 or
@@ -445,9 +445,10 @@ const char *rt_status_string(rt_status s);
  * n_clamped device, one uint64 (may be NULL): cells set to t_max
  * stream  cudaStream_t; the call is asynchronous on it.
  *
- * The first call on a device looks up the array's device address (once per device,
- * with that device current) and may load the library's device code; make that
- * first call before any stream capture. Every call reuses the same array and finds
+ * Every call looks up the array's address in the current context with
+ * cudaGetSymbolAddress (which allocates nothing); the first call in a context may
+ * load the library's device code there, so make that first call before any stream
+ * capture. Every call reuses the same array and finds
  * there whatever the previous call left, so calls whose work overlaps on the GPU
  * (other streams, other threads) race and must be serialised by the caller. */
 rt_status rt_cell_temperatures_noalloc(const uint64_t *count, const double *rho,

@@ -4,8 +4,10 @@
 // The FP64 emission table S_s(T_i) that the temperature inversion needs is built
 // into a fixed file-scope device array instead of memory from cudaMalloc. Host
 // code may not pass that array's name to a kernel (in host code it is only a
-// stand-in object, not a device address); it asks the runtime for the device
-// address once per device with cudaGetSymbolAddress and caches it.
+// stand-in object, not a device address); every call asks the runtime for the
+// array's address in the current context with cudaGetSymbolAddress, which
+// allocates nothing. No address is cached: after cudaDeviceReset, or in another
+// context, the module is loaded again at another address.
 
 #include "../../include/rt.h"
 #include "rt_internal.h"
@@ -14,14 +16,12 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 namespace {
 
 constexpr int kNoAllocMaxSpecies = 8;
 constexpr int kNoAllocMaxRows = 2048;
 constexpr int kNoAllocMaxBins = 1024;
-constexpr int kMaxDevices = 64;
 
 // Layout: [0, 256) clamped counter (uint64) | T grid (double [rows]) |
 // emission table (double [species][rows]).
@@ -32,21 +32,13 @@ constexpr size_t kScratchBytes =
 // 147,712 bytes, held by every GPU that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_scratch_mu;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set up on first use).
-rt_status scratch_on_current_device(unsigned char** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RT_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) return RT_ERR_CUDA;
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_addr[dev];
+// Device address of the scratch array in the current context. The first call in
+// a context may load the library's device code there.
+rt_status scratch_in_current_context(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) return RT_ERR_CUDA;
+  *out = static_cast<unsigned char*>(p);
   return RT_OK;
 }
 
@@ -131,7 +123,7 @@ extern "C" rt_status rt_cell_temperatures_noalloc(
       n_cells * (int64_t)n_species > 0x7fffffffll * 32)
     return RT_ERR_TOO_LARGE;
   unsigned char* base = nullptr;
-  rt_status st = scratch_on_current_device(&base);
+  rt_status st = scratch_in_current_context(&base);
   if (st != RT_OK) return st;
   unsigned long long* clamped = reinterpret_cast<unsigned long long*>(base);
   double* Tgrid = reinterpret_cast<double*>(base + kCounterBytes);

@@ -549,14 +549,39 @@ def cell_temperatures_noalloc(count, rho, volume, kabs, nu_edges, eps: float, T_
                               n_temp: int = 0, stream=None):
     """Temperatures from caller-owned device tensors (counts uint64/int64 [S][N], rho
     float64 [S][N], volume float64 [N], kabs float64 [S][B], nu_edges float64 [B+1],
-    T_out float32 [S][N], n_clamped int64 [1] or None); the library allocates
-    nothing for this call (its table lives in a fixed device array)."""
+    T_out float32 [S][N], n_clamped int64/uint64 [1] or None); the library allocates
+    nothing for this call (its table lives in a fixed device array). Every tensor
+    must be contiguous and on the current CUDA device; ValueError otherwise, before
+    anything is launched."""
+    import torch
+    if count.dim() != 2 or kabs.dim() != 2:
+        raise ValueError("count must be [S][N] and kabs [S][B]")
     S, N = int(count.shape[0]), int(count.shape[1])
     B = int(kabs.shape[1])
-    for name, t in (("count", count), ("rho", rho), ("volume", volume), ("kabs", kabs),
-                    ("nu_edges", nu_edges), ("T_out", T_out)):
-        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
-            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    u64 = getattr(torch, "uint64", None)
+    spec = (("count", count, (torch.int64,) + ((u64,) if u64 is not None else ()), (S, N)),
+            ("rho", rho, (torch.float64,), (S, N)),
+            ("volume", volume, (torch.float64,), (N,)),
+            ("kabs", kabs, (torch.float64,), (S, B)),
+            ("nu_edges", nu_edges, (torch.float64,), (B + 1,)),
+            ("T_out", T_out, (torch.float32,), (S, N)))
+    if n_clamped is not None:
+        spec += (("n_clamped", n_clamped,
+                  (torch.int64,) + ((u64,) if u64 is not None else ()), (1,)),)
+    cur = torch.cuda.current_device()
+    for name, t, dtypes, shape in spec:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
+                             f"cuda:{cur}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} must have dtype {' or '.join(map(str, dtypes))}, "
+                             f"not {t.dtype}")
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}, not {tuple(t.shape)}")
     _check(load().rt_cell_temperatures_noalloc(
         count.data_ptr(), rho.data_ptr(), volume.data_ptr(), kabs.data_ptr(),
         nu_edges.data_ptr(), S, N, B, float(eps), float(t_min), float(t_max), int(n_temp),
