@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """Throughput of the photon-package transport on GB300: packages/s.
 
-A step is one pass of the whole path over one batch: zero the counts, transport
-the batch of packages (Bjorkman-Wood re-emission, persistent packet-pool kernel,
-FP32), invert the counts into per-cell temperatures (FP64) and gather the escaped
-spectrum. The workload is the flared proto-planetary disk (128^3 base cubes, two
-levels of 2x2x2 refinement at the inner rim and midplane, 200 frequency bins,
-midplane V-band optical depth 1e3, 1e8 packages per GPU).
+A step is one pass of the whole path over one batch of packages: zero the tallies,
+transport the batch (Bjorkman-Wood re-emission, persistent packet-pool kernel,
+FP32), invert the counts into per-cell temperatures (FP64), gather the escaped
+spectrum and, where the model holds PAHs, compute the emission of every PAH-active
+cell with the BF16 tensor-core surrogate and the exact transient-heating solution
+as its fallback. The default workload is the large disk: gap and spiral, 256^3
+base cubes with three levels of 2x2x2 refinement (1.73e8 cells), 400 frequency
+bins, silicate, carbon and PAHs of 30 and 200 C atoms, 2.5e8 packages per step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large_disk|disk|disk_pah|disk_images|sphere|batch]
 
 Prints one JSON line. With several ranks (torchrun) every rank follows its own
 package-id range (weak scaling), the integer counts are summed over ranks, and the
@@ -42,10 +45,16 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--packages", type=float, default=1e8, help="packages per GPU per step")
+    p.add_argument("--packages", type=float, default=None,
+                   help="packages per GPU per step (default: 2.5e8 for the large disk, "
+                        "1e8 otherwise)")
     p.add_argument("--workload", choices=["disk", "sphere", "batch", "disk_pah", "disk_images",
                                           "large_disk"],
-                   default="disk")
+                   default="large_disk")
+    p.add_argument("--full-run", action="store_true",
+                   help="after the timed steps, one untimed-by-the-line run of the "
+                        "workload's full package count (1e10 for the large disk), reported "
+                        "in the line's 'full_run'")
     p.add_argument("--batch-models", type=int, default=256)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--plain-packages", type=float, default=1e7)
@@ -53,7 +62,17 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--cpu-one-thread", action="store_true",
                    help="time the oracle on one host thread instead of one process per core")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.packages is None:
+        a.packages = DEFAULT_PACKAGES.get(a.workload, 1e8)
+    return a
+
+
+# packages per step: config 5 is timed on a prefix of its 1e10 packages, sized so
+# that 20 timed steps take under a minute
+DEFAULT_PACKAGES = {"large_disk": 2.5e8}
+FULL_PACKAGES = {"large_disk": 1e10, "disk": 1e8, "disk_pah": 1e8, "disk_images": 1e8,
+                 "sphere": 1e5}
 
 
 def dist_env():
@@ -250,14 +269,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# DRAM traffic of the pool kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum over a 2e6-package launch on the disk, scaled per package),
-# valid only for that workload and the kernel source it was measured on (the hash
-# covers the code of the sources with comments and blank lines removed).
-TRAFFIC = {"sources": ("paper_1201_3588_gb300/csrc/rt_transport.cu",
-                       "paper_1201_3588_gb300/csrc/rt_internal.h"),
-           "sha256": "d50f24fa339fca45dfc7626db83c4a47413a6771b8e1acd8f0d2cc88bb82dfe8",
-           "dram_bytes_per_package": 1035.3}
+# Figures of the pool kernel from ncu captures, per workload, valid only for the
+# kernel source they were measured on (the hash covers the code of the sources with
+# comments and blank lines removed): DRAM traffic (dram__bytes_read.sum +
+# dram__bytes_write.sum) per package of a prefix launch, and the mean active lanes
+# per executed warp instruction (warp execution efficiency x 32).
+PROFILE_SOURCES = ("paper_1201_3588_gb300/csrc/rt_transport.cu",
+                   "paper_1201_3588_gb300/csrc/rt_internal.h")
+PROFILE = {}
 
 
 def source_code_hash(paths):
@@ -276,24 +295,108 @@ def source_code_hash(paths):
     return h.hexdigest()
 
 
-def traffic_per_launch(n_packages):
-    if not TRAFFIC["sha256"] or not TRAFFIC["dram_bytes_per_package"]:
+def profile_figures(workload):
+    """The ncu figures of this workload when they belong to the current source."""
+    p = PROFILE.get(workload)
+    if not p or source_code_hash(PROFILE_SOURCES) != p["sha256"]:
         return None
-    if source_code_hash(TRAFFIC["sources"]) != TRAFFIC["sha256"]:
-        return None
-    return TRAFFIC["dram_bytes_per_package"] * n_packages
+    return p
+
+
+def crossing_bytes(c, S, L):
+    """Algorithmic bytes of one transport launch by the per-unit count of the
+    method's data: every cell crossing reads the base-cube id (4 B), the child ids
+    of the L refinement levels (4 B each) and the S densities (4 B each); every
+    absorption is one 8-byte read-modify-write of a count (16 B)."""
+    return c["crossings"] * (4 + 4 * L + 4 * S) + 16 * c["absorptions"]
 
 
 def walk_bytes(c, S):
-    """Algorithmic bytes of one transport launch (per unit of work):
-    every cell entered reads its face link (4 B) and S densities (4 B each), every
-    descent into a finer neighbour one child id (4 B); every absorption is one 8-byte
-    read-modify-write of a count (16 B). Peel-off: every cell a sight line crosses
-    reads the same link and densities, every peeled event adds into an FP64 pixel
-    (16 B)."""
+    """Bytes the linked walk itself reads per launch: every cell entered reads its
+    face link (4 B) and S densities (4 B each), every descent into a finer neighbour
+    one child id (4 B); every absorption is one 8-byte read-modify-write of a count
+    (16 B). Peel-off: every cell a sight line crosses reads the same link and
+    densities, every peeled event adds into an FP64 pixel (16 B)."""
     entered = c["crossings"] + c["absorptions"] + c["scatters"] + c["capped"]
     return (entered * (4 + 4 * S) + 4 * c["levels"] + 16 * c["absorptions"]
             + c.get("peel_crossings", 0) * (4 + 4 * S) + 16 * c.get("peel_events", 0))
+
+
+def has_pah(model):
+    return any(sp.is_pah for sp in model.species)
+
+
+def train_surrogate(g, n, first, stream, dev):
+    """The PAH surrogate trained on the exact solutions of one untimed transport
+    pass of the same model (at most 1e6 (cell, PAH) pairs, 8 epochs)."""
+    import torch
+    from paper_1201_3588_gb300 import rt, surrogate
+    g.transport(n, seed=999, first_id=first, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, Y = surrogate.training_pairs(g)
+    keep = torch.randperm(X.shape[0], device=dev)[:1_000_000]
+    X, Y = X[keep].contiguous(), Y[keep].contiguous()
+    net = rt.MLP(X.shape[1], surrogate.N_HIDDEN, surrogate.N_LAYERS, g.B, seed=0)
+    hist = surrogate.train(net, X, Y, epochs=8)
+    xp = X[:, -2]
+    net.set_range(float(xp.min()) - 0.25, float(xp.max()) + 0.25)
+    torch.cuda.synchronize()
+    info = {"training_pairs": int(X.shape[0]), "train_s": time.perf_counter() - t0,
+            "train_loss_first_last": [hist[0], hist[-1]]}
+    del X, Y
+    g.reset(stream)
+    return net, info
+
+
+def pah_step_launches(n_active, n_fallback, n_pah):
+    """Kernels of one active-cell PAH emission pass: the compaction of PAH-active
+    cells; per batch of at most 2^20 of them and per PAH the features, the fused
+    network and the check, per PAH the add, and the compaction of failed cells;
+    then one exact launch for those."""
+    if n_active == 0:
+        return 1
+    batches = (n_active + (1 << 20) - 1) >> 20
+    return 1 + batches * (4 * n_pah + 1) + (1 if n_fallback else 0)
+
+
+def surrogate_error(g, net, cells_dev, j_dev, tol, stream):
+    """Surrogate-with-fallback emission against the exact emission of the same cells
+    (both from the library): energy-weighted L1 error, its median and 90th
+    percentile over cells, and the time of each."""
+    import torch
+    from paper_1201_3588_gb300 import rt
+    dev = j_dev.device
+    cells_ex = torch.empty_like(cells_dev)
+    j_ex = torch.empty_like(j_dev)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    c_ex, r_ex, _ = g.pah_emission_active(mode=rt.PAH_EXACT, cells=cells_ex, out=j_ex,
+                                          stream=stream)
+    e.record(stream)
+    torch.cuda.synchronize()
+    t_exact = a.elapsed_time(e)
+    a.record(stream)
+    c_au, r_au, nf = g.pah_emission_active(mode=rt.PAH_AUTO, surrogate=net, tol=tol,
+                                           cells=cells_dev, out=j_dev, stream=stream)
+    e.record(stream)
+    torch.cuda.synchronize()
+    t_auto = a.elapsed_time(e)
+    o_ex = torch.argsort(c_ex.long())
+    o_au = torch.argsort(c_au.long())
+    same_cells = bool(torch.equal(c_ex.long()[o_ex], c_au.long()[o_au]))
+    rx = r_ex[o_ex].double()
+    ra = r_au[o_au].double()
+    tot = rx.sum(dim=1).clamp_min(1e-300)
+    err = (ra - rx).abs().sum(dim=1) / tot
+    return {"active_cells": int(c_ex.shape[0]), "fallback_cells": int(nf),
+            "exact_ms": t_exact, "surrogate_auto_ms": t_auto,
+            "exact_over_auto": t_exact / max(t_auto, 1e-9),
+            "l1_vs_exact_energy_weighted": float((err * tot).sum() / tot.sum()),
+            "l1_vs_exact_median": float(err.median()),
+            "l1_vs_exact_p90": float(torch.quantile(err.float(), 0.9)),
+            "same_cells": same_cells}, r_au.shape[0]
 
 
 def run_ours(args):
@@ -312,6 +415,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     n = int(args.packages)
     S, N, B = model.n_species, model.tree.n_leaves, model.n_bins
+    L = model.tree.max_level
     stream = torch.cuda.Stream(device=dev)
     g = rt.Grid(model)
     g.emit_star(n * world)
@@ -319,7 +423,7 @@ def run_ours(args):
     sed_dev = torch.empty((2, model.n_sed_dirs, B), dtype=torch.int64, device=dev)
     cnt_dev = torch.empty((S, N), dtype=torch.int64, device=dev) if world > 1 else None
     first = rank * n
-    pah = args.workload in ("disk_pah", "large_disk")
+    pah = has_pah(model)
     images = args.workload == "disk_images"
     img_dev = prof_dev = None
     if images:
@@ -334,36 +438,15 @@ def run_ours(args):
         img_dev = torch.empty((2, 256, 256), dtype=torch.float64, device=dev)
         prof_dev = torch.empty(256, dtype=torch.float64, device=dev)
     net, pah_info = None, {}
-    # cells per PAH-emission call: the output buffer held at <= 16 GiB
-    pah_chunk = max(1, min(N, (16 << 30) // (4 * B)))
-    j_dev = torch.empty((min(pah_chunk, N), B), dtype=torch.float32, device=dev) if pah else None
-
-    def pah_emission(mode=rt.PAH_AUTO, count=False):
-        nf = 0
-        for c0 in range(0, N, pah_chunk):
-            nc = min(pah_chunk, N - c0)
-            _, f = g.pah_emission(first=c0, n=nc, mode=mode, surrogate=net, tol=0.05,
-                                  out=j_dev[:nc], stream=stream, count_fallback=count)
-            nf += f
-        return nf
-
-    if pah:  # train the surrogate on the exact solutions of a first (untimed) pass
-        from paper_1201_3588_gb300 import surrogate
-        g.transport(n, seed=999, first_id=first, stream=stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        X, Y = surrogate.training_pairs(g)
-        keep = torch.randperm(X.shape[0], device=dev)[:1_000_000]
-        X, Y = X[keep].contiguous(), Y[keep].contiguous()
-        net = rt.MLP(X.shape[1], surrogate.N_HIDDEN, surrogate.N_LAYERS, B, seed=0)
-        hist = surrogate.train(net, X, Y, epochs=8)
-        xp = X[:, -2]
-        net.set_range(float(xp.min()) - 0.25, float(xp.max()) + 0.25)
-        torch.cuda.synchronize()
-        pah_info = {"training_pairs": int(X.shape[0]), "train_s": time.perf_counter() - t0,
-                    "train_loss_first_last": [hist[0], hist[-1]]}
-        del X, Y
-        g.reset(stream)
+    tol = 0.05
+    cells_dev = j_dev = None
+    pah_state = {"active": 0, "fallback": 0}
+    if pah:
+        net, pah_info = train_surrogate(g, n, first, stream, dev)
+        # rows for the PAH-active cells, at most 8 GiB of them
+        max_cells = max(1, min(N, (8 << 30) // (4 * B)))
+        cells_dev = torch.empty(max_cells, dtype=torch.int32, device=dev)
+        j_dev = torch.empty((max_cells, B), dtype=torch.float32, device=dev)
 
     def step(k, ev=None):
         g.reset(stream)
@@ -380,7 +463,9 @@ def run_ours(args):
         g.temperatures(out=T_dev, stream=stream)
         g.sed(out=sed_dev, stream=stream)
         if pah:
-            pah_emission()
+            c, _, nf = g.pah_emission_active(mode=rt.PAH_AUTO, surrogate=net, tol=tol,
+                                             cells=cells_dev, out=j_dev, stream=stream)
+            pah_state["active"], pah_state["fallback"] = int(c.shape[0]), nf
         if images:
             g.images(out=img_dev, stream=stream)
             g.image_profile(0, 1, 2, out=prof_dev, stream=stream)
@@ -394,6 +479,7 @@ def run_ours(args):
            for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    launches = 0
     with Clocks(local) as clk:
         if world > 1:
             dist.barrier()
@@ -401,6 +487,9 @@ def run_ours(args):
         t_start.record(stream)
         for k in range(args.steps):
             step(args.warmup + k, kev[k])
+            # transport, temperatures; the PAH pass (counted from its own sizes)
+            launches += 2 + (pah_step_launches(pah_state["active"], pah_state["fallback"],
+                                               g.n_pah) if pah else 0) + (4 if images else 0)
         t_end.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -415,35 +504,34 @@ def run_ours(args):
         elapsed = float(t.item())
     value = n * world * args.steps / elapsed
 
-    # roofline of the dominant kernel (the transport launch)
+    # roofline of the dominant kernel (the transport launch), per unit of the method's
+    # data: crossings x (base id + L child ids + S densities) + absorptions x 16 B
     hbm, src = peaks()
     kmean = sum(kern_s) / len(kern_s)
-    bytes_launch = walk_bytes(c, S)
+    bytes_launch = crossing_bytes(c, S, L)
     achieved = bytes_launch / kmean / 1e9
+    prof = profile_figures(args.workload)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm,
-            "traffic": traffic_per_launch(n) if args.workload == "disk" else None,
+            "traffic": prof["dram_bytes_per_package"] * n if prof else None,
             "peak_source": src,
             "kernel": "k_transport_pool" + (" (peel-off variant)" if images else ""),
             "kernel_ms": 1e3 * kmean,
-            "algorithmic_bytes_per_launch": bytes_launch}
+            "bytes_per_crossing": 4 + 4 * L + 4 * S,
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "linked_walk_bytes_per_launch": walk_bytes(c, S),
+            "linked_walk_frac": walk_bytes(c, S) / kmean / 1e9 / hbm}
+    if prof:
+        roof["warp_lanes_active_per_instruction"] = prof["warp_lanes_active"]
+        roof["warp_execution_efficiency"] = prof["warp_lanes_active"] / 32.0
+        roof["warp_instructions_per_crossing"] = prof.get("warp_instr_per_crossing")
+        roof["profile"] = prof["file"]
 
     extra = {}
     if pah:
-        torch.cuda.synchronize()
-        pah_info["fallback_cells_last_step"] = pah_emission(count=True)
-        pah_info["pah_cells"] = int((torch.from_numpy(g.pah_absorbed().sum(axis=(0, 2)).astype("int64")) > 0).sum())
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pah_emission(mode=rt.PAH_EXACT)
-        e.record(stream)
-        torch.cuda.synchronize()
-        pah_info["exact_pah_ms"] = a.elapsed_time(e)
-        a.record(stream)
-        pah_emission()
-        e.record(stream)
-        torch.cuda.synchronize()
-        pah_info["surrogate_auto_pah_ms"] = a.elapsed_time(e)
+        err, n_rows = surrogate_error(g, net, cells_dev, j_dev, tol, stream)
+        pah_info.update(err)
+        pah_info["tol"] = tol
         extra["pah"] = pah_info
     if images:
         extra["images"] = {"peel_events": c["peel_events"],
@@ -451,9 +539,17 @@ def run_ours(args):
                            "band_minus_continuum_total": float((img_dev[0] - img_dev[1]).sum()),
                            "profile_peak": float(prof_dev.max())}
     if rank == 0 and not args.no_plain and not images:
-        extra["plain"] = plain_rates(g, model, int(args.plain_packages), stream, c, n)
-    e2e = e2e_rate(model, n, world, first, args.e2e_steps) \
-        if args.e2e_steps > 0 and not pah and not images else None
+        extra["plain"] = plain_rates(g, model, int(args.plain_packages), stream,
+                                     net if pah else None, cells_dev, j_dev, tol)
+    if args.full_run and rank == 0:
+        extra["full_run"] = full_run(g, args.workload, stream, net, cells_dev, j_dev, tol)
+    params = net.get_params() if pah else None
+    n_active = pah_state["active"]
+    del T_dev, cells_dev, j_dev
+    g.close()
+    torch.cuda.empty_cache()
+    e2e = e2e_rate(model, n, world, first, args.e2e_steps, net, params, tol,
+                   max(1, 2 * n_active)) if args.e2e_steps > 0 and not images else None
     if rank == 0:
         cpu_rate, cpu_n, cpu_s, cpu_cores = cpu_oracle_rate(model, n * world, args.cpu_seconds,
                                                             pool=pool)
@@ -465,11 +561,15 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": desc, "packages_per_gpu_per_step": n, "leaves": N,
-                       "bins": B, "species": S, "reemission": "bjorkman-wood",
-                       "kernel": "persistent packet pool",
+            "config": {"workload": desc, "packages_per_gpu_per_step": n,
+                       "packages_full_workload": FULL_PACKAGES.get(args.workload),
+                       "leaves": N, "bins": B, "species": S, "levels": L,
+                       "reemission": "bjorkman-wood",
+                       "form": "FP32 packet-pool transport" +
+                               (" + BF16 tcgen05 PAH surrogate with exact fallback"
+                                if pah else ""),
                        "l2": f"inputs larger than L2: grid + counts "
-                             f"{(4 * N * S + N + 8 * N * S) / 2**20:.0f} MiB > 129 MiB"},
+                             f"{(4 * N * S + N + 32 * N + 8 * N * S) / 2**20:.0f} MiB > 129 MiB"},
             "roofline": roof,
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_cores,
                              "kind": "oracle",
@@ -477,80 +577,189 @@ def run_ours(args):
                                        f"{cpu_cores} processes on disjoint package ranges, "
                                        f"{cpu_s:.1f} s)"},
             "e2e": e2e,
-            "gpu_launches": (2 + (pah_launches(N, pah_chunk) if pah else 0)
-                             + (4 if images else 0)) * args.steps,
+            "gpu_launches": launches,
             "clocks": clocks,
             "per_step": {"crossings": c["crossings"], "absorptions": c["absorptions"],
                          "scatters": c["scatters"], "capped": c["capped"],
                          "errors": c["errors"], "crossings_per_s": c["crossings"] / kmean,
-                         "warmup_crossings": counters_warm["crossings"]},
+                         "interactions_per_s": (c["absorptions"] + c["scatters"]) / kmean,
+                         "warmup_crossings": counters_warm["crossings"],
+                         "pah_active_cells": pah_state["active"] if pah else None,
+                         "pah_fallback_cells": pah_state["fallback"] if pah else None},
+            "oracle_error": ORACLE_ERROR,
             **extra,
         }
         print(json.dumps(line), flush=True)
-    g.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def pah_launches(N, chunk, n_pah=2):
-    """Kernels of one surrogate pass over N cells, per call (chunk of cells): the
-    compaction of PAH-active cells; per batch of at most 2^20 of them (one batch on
-    these disks) and per PAH the features, the fused network and the check, per PAH
-    the add, and the compaction of failed cells; then their exact solution."""
-    chunks = (N + chunk - 1) // chunk
-    return chunks * (1 + (3 * n_pah + n_pah + 1) + 1)
+# Agreement of each result with the FP64 oracle, as the GPU tests establish it
+# (tests/test_gpu_*.py; the bound each test asserts).
+ORACLE_ERROR = {
+    "temperatures": "same counts inverted by both: max relative difference <= 2e-4 "
+                    "(sphere, disk, large disk)",
+    "absorption_counts": "per cell within 4 sigma of an independent oracle run "
+                         "(batch-means sigma; sphere and refined disk, BW mode)",
+    "histories": "frozen-mode replay: >= 0.97 of packages identical event by event "
+                 "(PAH sphere), each divergence at an FP32 face tie or a re-emission "
+                 "table interval",
+    "pah_exact_emission": "sampled cells vs the oracle's level solution: 2e-3 on bins "
+                          "above 1e-6 of the peak; emitted = absorbed to 2e-4",
+    "surrogate": "forward vs the oracle's FP64 network: BF16 error (1e-2 per output); "
+                 "gradients: cosine > 0.999; accuracy vs exact: the line's pah block",
+}
 
 
-def plain_rates(g, model, n_prefix, stream, c_pool, n_full):
-    """The plain forms (one thread per package, global tables, per-lane atomics) on a
-    package prefix of the same workload, FP32 and FP64, against the pool on the same
-    prefix."""
+def plain_rates(g, model, n_prefix, stream, net=None, cells_dev=None, j_dev=None, tol=0.05):
+    """The plain form (one thread per package, global tables, per-lane atomics; FP64
+    and FP32) against the pool on a package prefix of the same workload; with PAHs,
+    also the plain form's exact PAH emission of every active cell against the
+    surrogate with fallback, on the pool prefix's tallies."""
     import torch
     from paper_1201_3588_gb300 import rt
     out = {"packages": n_prefix}
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     for name, kern in (("pool_f32", rt.KERNEL_POOL), ("plain_f32", rt.KERNEL_PLAIN_F32),
                        ("plain_f64", rt.KERNEL_PLAIN_F64)):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
+        a, b = ev()
         g.reset(stream)
         a.record(stream)
         g.transport(n_prefix, seed=77, kernel=kern, stream=stream)
         b.record(stream)
         torch.cuda.synchronize()
-        s = a.elapsed_time(b) / 1e3
-        out[name] = n_prefix / s
+        out[name] = n_prefix / (a.elapsed_time(b) / 1e3)
     out["pool_over_plain_f32"] = out["pool_f32"] / out["plain_f32"]
     out["pool_over_plain_f64"] = out["pool_f32"] / out["plain_f64"]
+    if net is not None:
+        g.reset(stream)
+        g.transport(n_prefix, seed=77, stream=stream)
+        times = {}
+        for name, mode in (("exact", rt.PAH_EXACT), ("auto", rt.PAH_AUTO)):
+            a, b = ev()
+            a.record(stream)
+            g.pah_emission_active(mode=mode, surrogate=net, tol=tol, cells=cells_dev,
+                                  out=j_dev, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times[name] = a.elapsed_time(b) / 1e3
+        # per package of the prefix: plain = plain FP64 transport + exact PAH,
+        # chosen = pool FP32 transport + surrogate with fallback
+        t_plain = n_prefix / out["plain_f64"] + times["exact"]
+        t_chosen = n_prefix / out["pool_f32"] + times["auto"]
+        out["pah_exact_s"], out["pah_auto_s"] = times["exact"], times["auto"]
+        out["plain_form"] = n_prefix / t_plain
+        out["chosen_form"] = n_prefix / t_chosen
+        out["chosen_over_plain"] = t_plain / t_chosen
+    g.reset(stream)
+    torch.cuda.synchronize()
     return out
 
 
-def e2e_rate(model, n, world, first, steps):
-    """Same metric through the public API with host buffers: create the grid from
-    host arrays, set dust and source, transport, temperatures and spectrum back to
-    host, destroy -- all inside the timed region."""
+def full_run(g, workload, stream, net, cells_dev, j_dev, tol):
+    """One pass of the workload's full package count in launches of 1e9 packages
+    (consecutive id ranges), then temperatures, spectrum and PAH emission."""
+    import torch
+    from paper_1201_3588_gb300 import rt
+    n_full = int(FULL_PACKAGES.get(workload, 1e8))
+    T = torch.empty((g.S, g.N), dtype=torch.float32, device=j_dev.device if j_dev is not None
+                    else torch.device("cuda"))
+    g.reset(stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    chunk = 10 ** 9
+    torch.cuda.synchronize()
+    a.record(stream)
+    for f0 in range(0, n_full, chunk):
+        g.transport(min(chunk, n_full - f0), seed=4242, first_id=f0, stream=stream)
+    g.temperatures(out=T, stream=stream)
+    g.sed(stream=stream)
+    nf = na = 0
+    if net is not None:
+        c, _, nf = g.pah_emission_active(mode=rt.PAH_AUTO, surrogate=net, tol=tol,
+                                         cells=cells_dev, out=j_dev, stream=stream)
+        na = int(c.shape[0])
+    b.record(stream)
+    torch.cuda.synchronize()
+    s = a.elapsed_time(b) / 1e3
+    c = g.counters()
+    return {"packages": n_full, "seconds": s, "packages_per_s": n_full / s,
+            "emitted": c["emitted"], "escaped": c["escaped"], "capped": c["capped"],
+            "errors": c["errors"], "crossings": c["crossings"],
+            "absorptions": c["absorptions"], "clamped": c["clamped"],
+            "pah_active_cells": na, "pah_fallback_cells": nf}
+
+
+def pinned_model(model):
+    """A shallow copy of the model whose large input arrays live in pinned host
+    memory (page-locked, so that the library's copies to the device run at full
+    speed)."""
+    import copy
+    import numpy as np
+    import torch
+
+    def pin(a, dtype):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        t = torch.empty(a.shape, dtype=getattr(torch, np.dtype(dtype).name), pin_memory=True)
+        v = t.numpy()
+        v[...] = a
+        return v, t
+
+    m = copy.copy(model)
+    m.tree = copy.copy(model.tree)
+    keep = []
+    m.tree.base, k1 = pin(model.tree.base, np.int32)
+    m.tree.child, k2 = pin(model.tree.child, np.int32)
+    m.rho, k3 = pin(model.rho, np.float64)
+    keep += [k1, k2, k3]
+    return m, keep
+
+
+def e2e_rate(model, n, world, first, steps, net=None, params=None, tol=0.05, max_cells=1):
+    """Same metric through the public API with host buffers: every step creates the
+    grid from pinned host arrays (tree, densities, opacities, PAH data), loads the
+    surrogate's weights from the host, transports, and reads the temperatures, the
+    escaped spectrum and the PAH emission of the active cells back into pinned host
+    buffers, then destroys the grid -- all inside the timed region."""
     import numpy as np
     import torch
     from paper_1201_3588_gb300 import rt
     S, N, B = model.n_species, model.tree.n_leaves, model.n_bins
-    T_host = np.zeros((S, N), dtype=np.float32)
-    times = []
+    pm, keep = pinned_model(model)
+    T_t = torch.empty((S, N), dtype=torch.float32, pin_memory=True)
+    T_host = T_t.numpy()
+    sed_host = np.zeros((2, model.n_sed_dirs, B), dtype=np.uint64)
+    pah = net is not None
+    if pah:
+        cells_t = torch.empty(max_cells, dtype=torch.int32, pin_memory=True)
+        rows_t = torch.empty((max_cells, B), dtype=torch.float32, pin_memory=True)
+        cells_host, rows_host = cells_t.numpy(), rows_t.numpy()
+    times, na = [], 0
     for k in range(steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with rt.Grid(model) as g:
+        with rt.Grid(pm) as g:
+            if pah:
+                net.set_params(params)
             g.emit_star(n * world)
             g.transport(n, seed=5000 + k, first_id=first)
             g.temperatures(out=T_host)
-            sed, eps = g.sed()
+            g.sed(out=sed_host)
+            if pah:
+                c, _, _ = g.pah_emission_active(mode=rt.PAH_AUTO, surrogate=net, tol=tol,
+                                                cells=cells_host, out=rows_host)
+                na = int(c.shape[0])
         torch.cuda.synchronize()
         if k > 0:  # the first pass warms the process
             times.append(time.perf_counter() - t0)
     t = model.tree
-    h2d = 4 * t.n_base ** 3 + 32 * t.n_blocks + 4 * S * N + N + 8 * (B + 1) + 24 * S * B
-    d2h = 4 * S * N + 16 * model.n_sed_dirs * B + 8 * S * 1024 + 8
+    h2d = (4 * t.n_base ** 3 + 32 * t.n_blocks + 8 * S * N + 8 * (B + 1) + 24 * S * B
+           + (4 * params.size if pah else 0))
+    d2h = 4 * S * N + 16 * model.n_sed_dirs * B + 8 + (4 * na * (B + 1) if pah else 0)
+    del keep
     return {"value": n * world / (sum(times) / len(times)), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": 1e3 * sum(times) / len(times)}
+            "ms_per_step": 1e3 * sum(times) / len(times),
+            "host_buffers": "pinned"}
 
 
 def run_batch(args):

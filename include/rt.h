@@ -320,6 +320,23 @@ rt_status rt_pah_emission(rt_grid *g, int64_t first_cell, int64_t n_cells, int p
                           const rt_mlp *surrogate, float tol, float *j_out, int mem,
                           uint64_t *n_fallback_out, void *stream);
 
+/* The same emission for the PAH-active cells only, in compact form (Sec. 2-3: the
+ * PAH emission of the cells that absorbed photons). The cells of the whole grid in
+ * which a PAH (all PAH species, or only number `pah` when pah >= 0) absorbed
+ * anything since the last reset are listed, in no particular order: cells_out[i]
+ * (int32 cell id) is the cell of row i of j_out [n_active][n_bins] (erg/s per bin),
+ * which holds what rt_pah_emission writes for that cell in the same mode. Cells
+ * without PAH absorptions emit nothing and get no row. *n_active_out receives the
+ * number of such cells; when it exceeds max_cells the call returns RT_ERR_RANGE and
+ * writes no rows. cells_out and j_out both live where `mem` says; a host output
+ * synchronises. n_fallback_out, mode, surrogate and tol as for rt_pah_emission.
+ * Unlike the range form this writes nothing for inactive cells, so on a grid where
+ * few cells hold PAH absorptions the output is small. */
+rt_status rt_pah_emission_active(rt_grid *g, int pah, int mode, const rt_mlp *surrogate,
+                                 float tol, int64_t max_cells, int32_t *cells_out,
+                                 float *j_out, int mem, int64_t *n_active_out,
+                                 uint64_t *n_fallback_out, void *stream);
+
 /* Per-cell PAH re-emission spectra, the step that couples the PAH emission back
  * into the transport (Sec. 2: PAH treatment in the Monte Carlo scheme; iterate
  * transport -> rt_pah_emission -> this call -> transport). Rows J [n_cells][n_bins]

@@ -14,6 +14,7 @@
 #include <memory>
 #include <new>
 #include <thread>
+#include <utility>
 #include <vector>
 
 using namespace rt;
@@ -78,6 +79,8 @@ struct rt_grid {
   bool images = false;
   float* d_jscratch = nullptr;
   size_t jscratch_n = 0;
+  int32_t* d_cells_scratch = nullptr;  // cell list of a host-output active-cell emission
+  int64_t cells_scratch_n = 0;
   // surrogate scratch (rows per batch of active cells) and cell lists (per call)
   long long sur_cap = 0, list_cap = 0;
   float* d_sx = nullptr;       // [batch][K+2]
@@ -191,6 +194,7 @@ void free_all(rt_grid* g) {
   dfree(g->d_iscratch);
   dfree(g->d_pah_cell_cdf);
   dfree(g->d_jscratch);
+  dfree(g->d_cells_scratch);
   dfree(g->d_sx);
   dfree(g->d_sy);
   dfree(g->d_spabs);
@@ -1273,40 +1277,44 @@ static float* output_buffer(rt_grid* g, float* j_out, int mem, size_t n, rt_stat
   return g->d_jscratch;
 }
 
-rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int pah, int mode,
-                          const rt_mlp* surrogate, float tol, float* j_out, int mem,
-                          uint64_t* n_fallback_out, void* stream) {
-  if (!g || !j_out || first_cell < 0 || n_cells < 0) return RT_ERR_ARG;
-  if (first_cell > g->desc.n_leaves || n_cells > g->desc.n_leaves - first_cell)
-    return RT_ERR_ARG;
-  if (mode != RT_PAH_EXACT && mode != RT_PAH_SURROGATE && mode != RT_PAH_AUTO) return RT_ERR_ARG;
-  if (mode != RT_PAH_EXACT && !surrogate) return RT_ERR_ARG;
-  cudaStream_t s = as_stream(stream);
-  RT_CUDA(cudaSetDevice(g->dev));
+// Shared part of rt_pah_emission (rows = the cells of a range) and
+// rt_pah_emission_active (rows = a compact list of the PAH-active cells).
+// Range form: dst [n_cells][B] row c is cell first_cell + c. Compact form
+// (cells_dev != nullptr): the PAH-active cells of the whole grid are listed, row i of
+// dst is cell list[i], copied to cells_dev; at most max_rows rows.
+static rt_status pah_emission_impl(rt_grid* g, int64_t first_cell, int64_t n_cells, int pah,
+                                   int mode, const rt_mlp* surrogate, float tol,
+                                   float* (*get_dst)(rt_grid*, void*, size_t, rt_status*),
+                                   void* dst_ctx, int32_t* cells_dev, int64_t max_rows,
+                                   int64_t* n_rows_out, uint64_t* n_fallback_out,
+                                   float** dst_out, cudaStream_t s) {
   rt_status st = build_tables(g, s);
   if (st != RT_OK) return st;
   if (g->n_pah == 0) return RT_ERR_STATE;
   if (pah < -1 || pah >= g->n_pah) return RT_ERR_ARG;
   const int B = g->desc.n_bins, K = g->tab.n_coarse, F = K + 2;
+  (void)K;
   if (mode != RT_PAH_EXACT) {
     int ni = 0, no = 0;
-    float lo = 0, hi = 0;
     if (rt_mlp_dims(surrogate, &ni, &no) != RT_OK || ni != F || no != B) return RT_ERR_ARG;
-    rt_mlp_get_range(surrogate, &lo, &hi);
-    (void)lo;
   }
+  const bool compact = cells_dev != nullptr;
   if (n_fallback_out) *n_fallback_out = 0;
+  if (n_rows_out) *n_rows_out = 0;
+  *dst_out = nullptr;
   if (n_cells == 0) return RT_OK;
-  const size_t n = (size_t)n_cells * B;
-  float* dst = output_buffer(g, j_out, mem, n, &st);
-  if (st != RT_OK) return st;
   rt_mlp* m = const_cast<rt_mlp*>(surrogate);
   float x_lo = -1e30f, x_hi = 1e30f;
   if (m) rt_mlp_get_range(m, &x_lo, &x_hi);
   if ((st = surrogate_scratch(g, n_cells, 0, false)) != RT_OK) return st;
   const float t = mode == RT_PAH_AUTO ? tol : 1e30f;
   unsigned long long n_fallback = 0;
-  RT_CUDA(cudaMemsetAsync(dst, 0, sizeof(float) * n, s));
+  float* dst = nullptr;
+  if (!compact) {
+    dst = get_dst(g, dst_ctx, (size_t)n_cells * B, &st);
+    if (st != RT_OK) return st;
+    RT_CUDA(cudaMemsetAsync(dst, 0, sizeof(float) * (size_t)n_cells * B, s));
+  }
   // the cells where a PAH absorbed anything, in one list for the whole range
   RT_CUDA(cudaMemsetAsync(g->d_ucount, 0, 2 * sizeof(unsigned), s));
   RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell, n_cells,
@@ -1314,9 +1322,22 @@ rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int p
   unsigned na = 0;
   RT_CUDA(cudaMemcpyAsync(&na, g->d_ucount, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   RT_CUDA(cudaStreamSynchronize(s));
+  if (n_rows_out) *n_rows_out = compact ? (int64_t)na : n_cells;
+  if (compact) {
+    if ((int64_t)na > max_rows) return RT_ERR_RANGE;
+    if (na == 0) return RT_OK;
+    dst = get_dst(g, dst_ctx, (size_t)na * B, &st);
+    if (st != RT_OK) return st;
+    RT_CUDA(cudaMemsetAsync(dst, 0, sizeof(float) * (size_t)na * B, s));
+    RT_CUDA(cudaMemcpyAsync(cells_dev, g->d_list, sizeof(int32_t) * na, cudaMemcpyDeviceToDevice,
+                            s));
+  }
+  *dst_out = dst;
+  // compact rows: row i is cell d_list[i]; range rows: the list holds the rows
+  const int* row_cells = compact ? g->d_list : nullptr;
   if (na > 0 && mode == RT_PAH_EXACT)
     RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, na, dst,
-                             nullptr, pah, s, g->d_list));
+                             nullptr, pah, s, compact ? nullptr : g->d_list, row_cells));
   if (na > 0 && mode != RT_PAH_EXACT) {
     // the surrogate over batches of active cells; cells whose prediction fails its
     // checks are appended to one fallback list, solved exactly in one launch
@@ -1339,10 +1360,13 @@ rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int p
         if (pah >= 0 && p != pah) continue;
         RT_CUDA(launch_surrogate_add(g->d_sy + (size_t)p * batch * B,
                                      g->d_spabs + (size_t)p * batch, nb, B,
-                                     mode == RT_PAH_AUTO ? g->d_sflag : nullptr, dst, s, lst));
+                                     mode == RT_PAH_AUTO ? g->d_sflag : nullptr,
+                                     compact ? dst + (size_t)b0 * B : dst, s,
+                                     compact ? nullptr : lst));
       }
       RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell, nb,
-                             g->d_sflag, lst, g->d_list2, g->d_ucount + 1, s));
+                             g->d_sflag, compact ? nullptr : lst, g->d_list2, g->d_ucount + 1,
+                             s, (int)b0));
     }
     unsigned nf = 0;
     RT_CUDA(cudaMemcpyAsync(&nf, g->d_ucount + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -1350,11 +1374,78 @@ rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int p
     n_fallback = nf;
     if (mode == RT_PAH_AUTO && nf > 0)
       RT_CUDA(launch_pah_exact(g->g, g->ptab, g->d_pahabs, g->eps, g->d0, first_cell, nf, dst,
-                               nullptr, pah, s, g->d_list2));
+                               nullptr, pah, s, g->d_list2, row_cells));
   }
   if (n_fallback_out) *n_fallback_out = n_fallback;
+  return RT_OK;
+}
+
+static float* emission_dst(rt_grid* g, void* ctx, size_t n, rt_status* st) {
+  const auto* o = static_cast<const std::pair<float*, int>*>(ctx);
+  return output_buffer(g, o->first, o->second, n, st);
+}
+
+static rt_status check_pah_mode(int mode, const rt_mlp* surrogate) {
+  if (mode != RT_PAH_EXACT && mode != RT_PAH_SURROGATE && mode != RT_PAH_AUTO) return RT_ERR_ARG;
+  if (mode != RT_PAH_EXACT && !surrogate) return RT_ERR_ARG;
+  return RT_OK;
+}
+
+rt_status rt_pah_emission(rt_grid* g, int64_t first_cell, int64_t n_cells, int pah, int mode,
+                          const rt_mlp* surrogate, float tol, float* j_out, int mem,
+                          uint64_t* n_fallback_out, void* stream) {
+  if (!g || !j_out || first_cell < 0 || n_cells < 0) return RT_ERR_ARG;
+  if (first_cell > g->desc.n_leaves || n_cells > g->desc.n_leaves - first_cell)
+    return RT_ERR_ARG;
+  rt_status st = check_pah_mode(mode, surrogate);
+  if (st != RT_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  std::pair<float*, int> out{j_out, mem};
+  float* dst = nullptr;
+  st = pah_emission_impl(g, first_cell, n_cells, pah, mode, surrogate, tol, emission_dst, &out,
+                         nullptr, 0, nullptr, n_fallback_out, &dst, s);
+  if (st != RT_OK) return st;
+  if (mem != RT_MEM_DEVICE && dst) {
+    RT_CUDA(cudaMemcpyAsync(j_out, dst, sizeof(float) * (size_t)n_cells * g->desc.n_bins,
+                            cudaMemcpyDeviceToHost, s));
+    return sync_status(g, s);
+  }
+  return RT_OK;
+}
+
+rt_status rt_pah_emission_active(rt_grid* g, int pah, int mode, const rt_mlp* surrogate,
+                                 float tol, int64_t max_cells, int32_t* cells_out,
+                                 float* j_out, int mem, int64_t* n_active_out,
+                                 uint64_t* n_fallback_out, void* stream) {
+  if (!g || !j_out || !cells_out || !n_active_out || max_cells < 0) return RT_ERR_ARG;
+  rt_status st = check_pah_mode(mode, surrogate);
+  if (st != RT_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  RT_CUDA(cudaSetDevice(g->dev));
+  // the cell list goes to the caller's buffer, or through the handle's scratch
+  int32_t* cells_dev = cells_out;
   if (mem != RT_MEM_DEVICE) {
-    RT_CUDA(cudaMemcpyAsync(j_out, dst, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    if (g->cells_scratch_n < g->desc.n_leaves) {
+      dfree(g->d_cells_scratch);
+      g->cells_scratch_n = 0;
+      if ((st = dalloc(&g->d_cells_scratch, (size_t)g->desc.n_leaves)) != RT_OK) return st;
+      g->cells_scratch_n = g->desc.n_leaves;
+    }
+    cells_dev = g->d_cells_scratch;
+  }
+  std::pair<float*, int> out{j_out, mem};
+  float* dst = nullptr;
+  int64_t na = 0;
+  st = pah_emission_impl(g, 0, g->desc.n_leaves, pah, mode, surrogate, tol, emission_dst, &out,
+                         cells_dev, max_cells, &na, n_fallback_out, &dst, s);
+  *n_active_out = na;
+  if (st != RT_OK) return st;
+  if (mem != RT_MEM_DEVICE && na > 0) {
+    RT_CUDA(cudaMemcpyAsync(j_out, dst, sizeof(float) * (size_t)na * g->desc.n_bins,
+                            cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaMemcpyAsync(cells_out, cells_dev, sizeof(int32_t) * (size_t)na,
+                            cudaMemcpyDeviceToHost, s));
     return sync_status(g, s);
   }
   return RT_OK;

@@ -245,7 +245,8 @@ cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream
 cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                              double eps, double d0, long long first, long long n,
                              float* j_out, const unsigned char* want, int pah_only,
-                             cudaStream_t s, const int* list = nullptr);
+                             cudaStream_t s, const int* list = nullptr,
+                             const int* cell_of_row = nullptr);
 cudaError_t launch_pah_features(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                                 double eps, double d0, int p, long long first, long long n,
                                 float* X, float* p_abs, cudaStream_t s,
@@ -260,7 +261,8 @@ cudaError_t launch_surrogate_add(const float* Y, const float* p_abs, long long n
                                  const int* list = nullptr);
 cudaError_t launch_compact(const PahTables& t, const unsigned* pahabs, long long N, int pah,
                            long long first, long long n, const unsigned char* flag,
-                           const int* list, int* out, unsigned* count, cudaStream_t s);
+                           const int* list, int* out, unsigned* count, cudaStream_t s,
+                           int off = 0);
 cudaError_t launch_count_flags(const unsigned char* flag, long long n, unsigned long long* out,
                                cudaStream_t s);
 cudaError_t launch_pah_cell_cdf(const float* J, long long n, int B, float* out, cudaStream_t s);

@@ -314,7 +314,7 @@ __device__ __forceinline__ int exact_cell_stride(int K, int M) {
 __global__ void __launch_bounds__(32 * kExactCellsMax / 8)
     k_pah_exact(DevGrid g, PahTables t, const unsigned* pahabs, double eps, double d0,
                 long long first, long long n, float* j_out, const unsigned char* want,
-                int pah_only, const int* list) {
+                int pah_only, const int* list, const int* cell_of_row) {
   extern __shared__ __align__(16) float smf[];
   __shared__ double s_norm[kExactCellsMax];   // N_mol / sum_f P_f, 0 without a solution
   __shared__ long long s_row[kExactCellsMax];  // row of j_out
@@ -327,8 +327,10 @@ __global__ void __launch_bounds__(32 * kExactCellsMax / 8)
   float* G = P + Mp;
   const long long i = (long long)blockIdx.x * n_cells + slot;
   const bool active = i < n && !(want && !want[i]);
-  const long long c = active ? (list ? (long long)list[i] : i) : -1;  // cell - first
-  const long long cell = first + c;
+  // row of j_out; the cell is first + row, or first + cell_of_row[row] when the
+  // output rows are a compact list of cells
+  const long long c = active ? (list ? (long long)list[i] : i) : -1;
+  const long long cell = active ? first + (cell_of_row ? (long long)cell_of_row[c] : c) : -1;
   if (j == 0) s_row[slot] = c;
   if (active)
     for (int b = j; b < g.B; b += 4) j_out[(size_t)c * g.B + b] = 0.0f;
@@ -477,10 +479,11 @@ __global__ void k_surrogate_add(const float* Y, const float* p_abs, long long n,
 
 // Compaction: rows i < n with sel(i) true are appended to out (order not kept);
 // *count receives their number. sel = any PAH absorption in cell first + i (all PAH
-// or only `pah`), or flag[i] when flag is given (then out receives list[i]).
+// or only `pah`), or flag[i] when flag is given (then out receives list[i], or
+// off + i without a list).
 __global__ void k_compact(const unsigned* pahabs, long long N, int K, int n_pah, int pah,
                           long long first, long long n, const unsigned char* flag,
-                          const int* list, int* out, unsigned* count) {
+                          const int* list, int off, int* out, unsigned* count) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   bool sel = false;
   if (i < n) {
@@ -502,7 +505,9 @@ __global__ void k_compact(const unsigned* pahabs, long long N, int K, int n_pah,
   unsigned base = 0;
   if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (sel) out[base + __popc(m & ((1u << lane) - 1u))] = flag ? (list ? list[i] : (int)i) : (int)i;
+  if (sel)
+    out[base + __popc(m & ((1u << lane) - 1u))] =
+        flag ? (list ? list[i] : off + (int)i) : (int)i;
 }
 
 __global__ void k_count_flags(const unsigned char* flag, long long n, unsigned long long* out) {
@@ -534,7 +539,7 @@ cudaError_t launch_pah_tables(const PahBuild& pb, const PahTables& t, cudaStream
 cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigned* pahabs,
                              double eps, double d0, long long first, long long n,
                              float* j_out, const unsigned char* want, int pah_only,
-                             cudaStream_t s, const int* list) {
+                             cudaStream_t s, const int* list, const int* cell_of_row) {
   if (n <= 0) return cudaSuccess;
   const int w = ((t.K + 3) & ~3) + 2 * ((t.M + 3) & ~3);
   const size_t per_cell = sizeof(float) * (size_t)(((w + 31) & ~31) + 4);
@@ -548,7 +553,8 @@ cudaError_t launch_pah_exact(const DevGrid& g, const PahTables& t, const unsigne
   if (e != cudaSuccess) return e;
   long long blocks = (n + cells - 1) / cells;
   k_pah_exact<<<(unsigned)blocks, 4 * cells, smem, s>>>(g, t, pahabs, eps, d0, first, n,
-                                                       j_out, want, pah_only, list);
+                                                       j_out, want, pah_only, list,
+                                                       cell_of_row);
   return cudaGetLastError();
 }
 
@@ -747,10 +753,11 @@ cudaError_t launch_pah_cell_cdf(const float* J, long long n, int B, float* out, 
 
 cudaError_t launch_compact(const PahTables& t, const unsigned* pahabs, long long N, int pah,
                            long long first, long long n, const unsigned char* flag,
-                           const int* list, int* out, unsigned* count, cudaStream_t s) {
+                           const int* list, int* out, unsigned* count, cudaStream_t s,
+                           int off) {
   if (n <= 0) return cudaSuccess;
   k_compact<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pahabs, N, t.K, t.n_pah, pah, first, n,
-                                                         flag, list, out, count);
+                                                         flag, list, off, out, count);
   return cudaGetLastError();
 }
 

@@ -123,6 +123,9 @@ SIGNATURES = {
                            C.c_void_p],
     "rt_pah_emission": [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_void_p,
                         C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "rt_pah_emission_active": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_float, C.c_int64,
+                               C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int64),
+                               C.c_void_p, C.c_void_p],
     "rt_pah_training_pairs": [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_void_p,
                               C.c_void_p, C.c_void_p, C.c_void_p],
     "rt_mlp_dims": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)],
@@ -330,6 +333,29 @@ class Grid:
                                       C.byref(nf) if count_fallback else None,
                                       _stream(stream)), "rt_pah_emission")
         return out, int(nf.value)
+
+    def pah_emission_active(self, mode: int = PAH_EXACT, surrogate=None, tol: float = 0.0,
+                            cells=None, out=None, pah: int = -1, stream=None):
+        """Emission rows of the PAH-active cells only: returns (cells [n], rows [n][B],
+        n_fallback). `cells` (int32) and `out` (float32 [max][B]) are preallocated
+        outputs, both host (numpy) or both device (torch); by default host arrays
+        large enough for every cell."""
+        if out is None:
+            cells = np.zeros(self.N, dtype=np.int32)
+            out = np.zeros((self.N, self.B), dtype=np.float32)
+        pc, mc = _ptr_mem(cells)
+        p, mem = _ptr_mem(out)
+        if mc != mem:
+            raise ValueError("cells and out must both be host or both be device memory")
+        na = C.c_int64()
+        nf = C.c_uint64()
+        _check(load().rt_pah_emission_active(self._h, int(pah), int(mode),
+                                             surrogate._h if surrogate is not None else None,
+                                             float(tol), int(out.shape[0]), pc, p, mem,
+                                             C.byref(na), C.byref(nf), _stream(stream)),
+               "rt_pah_emission_active")
+        n = int(na.value)
+        return cells[:n], out[:n], int(nf.value)
 
     def set_pah_spectra(self, pah: int, J, first: int = 0, stream=None):
         """Per-cell re-emission spectra of PAH `pah` for cells first .. first+len(J)-1

@@ -1,0 +1,160 @@
+"""Bjorkman-Wood transport on refined grids, GPU against the FP64 oracle.
+
+* Per-cell absorption counts of the BW mode on a refined disk (32^3 base cubes, two
+  levels of subcubes, 100 bins): the walk the benchmark times (face links, descents
+  into finer neighbours, eps/V per level). The oracle makes 16 independent BW runs
+  (one host process each); the GPU 64. Each cell's mean count must lie within 4
+  sigma of the GPU's, sigma from the spread of the runs. With ~10^5 cells compared,
+  a few are expected beyond 4 sigma by chance: the test bounds their number by the
+  chance rate, and bounds the mean square z (a small bias common to many cells
+  raises it).
+* Temperatures under replay: the frozen mode on a small refined box, GPU and oracle
+  following the same packages; cells with >= 1e4 absorptions agree within 0.5 %.
+"""
+import math
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1201_3588_gb300 import rt, workloads as w
+from _helpers import frozen_field
+
+pytestmark = pytest.mark.gpu
+
+N_RUN = 100_000          # packages per run (eps = L / N_RUN in every run)
+ORACLE_RUNS = 16
+GPU_RUNS = 64
+
+
+def _disk():
+    return w.disk_model(n_base=32, max_level=2, n_bins=100, tau_v_mid=30.0)
+
+
+def _oracle_bw_run(seed):
+    m = _disk()
+    t = oracle.transport(m, N_RUN, seed=seed, n_total=N_RUN, mode=oracle.MODE_BW)
+    return t.count.astype(np.float64), t.sed[0, 0].astype(np.float64), t.emitted, t.escaped
+
+
+def _pool(n):
+    # spawned processes: this process may already hold a CUDA context
+    return mp.get_context("spawn").Pool(n)
+
+
+def _procs():
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return max(1, min(ORACLE_RUNS, cores))
+
+
+def _z(o_runs, g_runs):
+    """z of the oracle mean against the GPU mean, per cell; variance per run from
+    both sets of runs pooled, floored at the Poisson value and at one count."""
+    mo, mg = o_runs.mean(axis=0), g_runs.mean(axis=0)
+    ko, kg = o_runs.shape[0], g_runs.shape[0]
+    pooled = ((ko - 1) * o_runs.var(axis=0, ddof=1) + (kg - 1) * g_runs.var(axis=0, ddof=1)) \
+        / (ko + kg - 2)
+    var = np.maximum(np.maximum(pooled, 0.5 * (mo + mg)), 1.0)
+    return (mo - mg) / np.sqrt(var * (1.0 / ko + 1.0 / kg)), mo + mg > 0
+
+
+def _two_sided_t_tail(z, dof):
+    """P(|t| > z) for Student's t with `dof` degrees of freedom (regularised
+    incomplete beta by continued fraction is in scipy; use it when present)."""
+    try:
+        from scipy import stats
+        return float(2 * stats.t.sf(z, dof))
+    except Exception:
+        return math.erfc(z / math.sqrt(2))
+
+
+def test_bw_counts_on_refined_disk_match_oracle():
+    model = _disk()
+    assert model.tree.max_level == 2 and (model.tree.leaf_level == 1).any()
+    with _pool(_procs()) as pool:
+        res = pool.map(_oracle_bw_run, [7000 + k for k in range(ORACLE_RUNS)])
+    o_cnt = np.array([r[0] for r in res])
+    o_sed = np.array([r[1] for r in res])
+    assert all(r[2] == N_RUN == r[3] for r in res)
+    g_cnt, g_sed = [], []
+    with rt.Grid(model) as g:
+        g.emit_star(N_RUN)
+        for k in range(GPU_RUNS):
+            g.reset()
+            g.transport(N_RUN, seed=100 + k, mode=rt.REEMIT_BW)
+            c = g.counters()
+            assert c["emitted"] == N_RUN == c["escaped"] and c["errors"] == 0
+            g_cnt.append(g.counts().astype(np.float64))
+            g_sed.append(g.sed()[0][0, 0].astype(np.float64))
+    g_cnt, g_sed = np.array(g_cnt), np.array(g_sed)
+    dof = ORACLE_RUNS + GPU_RUNS - 2
+    lev = model.tree.leaf_level
+    for name, o, gg in (("counts", o_cnt.reshape(ORACLE_RUNS, -1), g_cnt.reshape(GPU_RUNS, -1)),
+                        ("sed", o_sed, g_sed)):
+        z, ok = _z(o, gg)
+        z = z[ok]
+        n_out = int((np.abs(z) > 4.0).sum())
+        chance = _two_sided_t_tail(4.0, dof) * z.size
+        print(f"{name}: {z.size} cells compared, max |z| {np.abs(z).max():.2f}, "
+              f"{n_out} beyond 4 sigma (chance {chance:.2f}), mean z^2 {(z ** 2).mean():.3f}")
+        # 4 sigma per cell; beyond it no more cells than chance allows (Poisson
+        # tail of the expected number, at a one-in-a-million false alarm)
+        allowed = chance + 5.0 * math.sqrt(chance) + 5.0
+        assert n_out <= allowed, (name, n_out, allowed)
+        assert np.abs(z).max() < 6.5, name
+        assert abs((z ** 2).mean() - 1.0) < 0.1, name
+    # every refinement level took part, with well-measured cells
+    mean = g_cnt.mean(axis=0)
+    for L in range(3):
+        assert (mean[:, lev == L] > 100).sum() > 20, L
+
+
+def _box():
+    nu = w.frequency_edges(64)
+    return w.uniform_box_model(4, 64, 2.0, w.two_species(nu), max_level=2,
+                               refine=w.sphere_refine_fn(4, 0.6))
+
+
+def _oracle_frozen_shard(job):
+    first, n, n_total, seed = job
+    m = _box()
+    Tf = frozen_field(m, T0=60.0, r0_frac=0.2).astype(np.float64)
+    t = oracle.transport(m, n, seed=seed, first_id=first, n_total=n_total,
+                         mode=oracle.MODE_FROZEN, T_frozen=Tf)
+    return t.count.astype(np.int64)
+
+
+def test_temperatures_under_replay_on_refined_box():
+    model = _box()
+    assert model.tree.max_level == 2
+    N = 4_000_000
+    seed = 31
+    Tf = frozen_field(model, T0=60.0, r0_frac=0.2)
+    with rt.Grid(model) as g:
+        g.emit_star(N)
+        g.set_frozen_temperatures(Tf)
+        g.transport(N, seed=seed, mode=rt.REEMIT_FROZEN)
+        c = g.counters()
+        cnt_g = g.counts().astype(np.int64)
+        T_g = g.temperatures().astype(np.float64)
+        _, eps = g.sed()
+    assert c["emitted"] == N == c["escaped"] and c["errors"] == 0
+    # the oracle follows the same packages in disjoint id ranges (the frozen mode
+    # shards exactly), then inverts its own counts
+    k = _procs()
+    step = (N + k - 1) // k
+    jobs = [(f, min(step, N - f), N, seed) for f in range(0, N, step)]
+    with _pool(k) as pool:
+        cnt_o = sum(pool.map(_oracle_frozen_shard, jobs))
+    T_o = oracle.temperatures(model, cnt_o.astype(np.uint64), eps)
+    big = (cnt_g >= 10_000) & (cnt_o >= 10_000)
+    print("cells with >= 1e4 counts:", int(big.sum()), "of", cnt_g.size,
+          "max |T_gpu/T_oracle - 1|:", float(np.abs(T_g[big] / T_o[big] - 1).max()),
+          "max count difference:", float(np.abs(cnt_g[big] / cnt_o[big] - 1).max()))
+    assert big.sum() >= 0.5 * cnt_g.size
+    np.testing.assert_allclose(T_g[big], T_o[big], rtol=5e-3)

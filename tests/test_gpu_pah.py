@@ -90,3 +90,46 @@ def test_exact_pah_emission_matches_oracle(pah_model, pah_oracle):
             ref += n_mol * pah.emission(P, tab)
         big = ref > 1e-6 * ref.max()
         np.testing.assert_allclose(J[c][big], ref[big], rtol=2e-3)
+
+
+def test_active_cell_emission_equals_range_form(pah_model):
+    """rt_pah_emission_active returns, for every PAH-active cell and no other, the
+    row rt_pah_emission writes for it -- exact, surrogate and auto (with fallback)
+    modes, device and host outputs, all PAHs and one PAH -- and refuses a buffer
+    smaller than the number of active cells."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    N = 10 ** 6
+    net = rt.MLP(64 + 2, 64, 2, pah_model.n_bins, seed=3)  # untrained: many fallbacks
+    with rt.Grid(pah_model) as g:
+        g.emit_star(N)
+        g.transport(N, seed=5)
+        tal = g.pah_absorbed()
+        for mode, pah_sel in ((rt.PAH_EXACT, -1), (rt.PAH_SURROGATE, -1), (rt.PAH_AUTO, -1),
+                              (rt.PAH_AUTO, 1)):
+            sur = None if mode == rt.PAH_EXACT else net
+            tol = 0.05 if mode == rt.PAH_AUTO else 0.0
+            J, nf_range = g.pah_emission(mode=mode, surrogate=sur, tol=tol, pah=pah_sel)
+            sel = tal if pah_sel < 0 else tal[pah_sel:pah_sel + 1]
+            active = np.nonzero(sel.sum(axis=(0, 2)) > 0)[0]
+            assert len(active) > 50
+            # device output
+            cells_d = torch.full((g.N,), -1, dtype=torch.int32, device=dev)
+            rows_d = torch.zeros((g.N, g.B), dtype=torch.float32, device=dev)
+            c_d, r_d, nf_d = g.pah_emission_active(mode=mode, surrogate=sur, tol=tol,
+                                                   cells=cells_d, out=rows_d, pah=pah_sel)
+            c_d, r_d = c_d.cpu().numpy(), r_d.cpu().numpy()
+            # host output
+            c_h, r_h, nf_h = g.pah_emission_active(mode=mode, surrogate=sur, tol=tol,
+                                                   pah=pah_sel)
+            for cells, rows, nf in ((c_d, r_d, nf_d), (c_h, r_h, nf_h)):
+                assert sorted(cells.tolist()) == active.tolist()
+                assert nf == nf_range
+                np.testing.assert_allclose(rows, J[cells], rtol=1e-6, atol=0)
+            if mode == rt.PAH_AUTO:
+                assert 0 < nf_range <= len(active)
+        small_c = np.zeros(10, dtype=np.int32)
+        small_r = np.zeros((10, g.B), dtype=np.float32)
+        with pytest.raises(rt.RTError) as e:
+            g.pah_emission_active(cells=small_c, out=small_r)
+        assert e.value.code == 6
