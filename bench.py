@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--plain-packages", type=float, default=1e7)
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-pah", action="store_true",
+                   help="leave the PAH emission out of the step (the transport still "
+                        "tallies PAH absorptions); for profiling the transport alone")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--cpu-one-thread", action="store_true",
                    help="time the oracle on one host thread instead of one process per core")
@@ -423,7 +426,7 @@ def run_ours(args):
     sed_dev = torch.empty((2, model.n_sed_dirs, B), dtype=torch.int64, device=dev)
     cnt_dev = torch.empty((S, N), dtype=torch.int64, device=dev) if world > 1 else None
     first = rank * n
-    pah = has_pah(model)
+    pah = has_pah(model) and not args.no_pah
     images = args.workload == "disk_images"
     img_dev = prof_dev = None
     if images:

@@ -270,6 +270,24 @@ rt_status rt_batch_temperatures(rt_batch *b, int model, float *T_out, int mem, v
 rt_status rt_trace(rt_grid *g, const uint64_t *ids, int64_t n, uint64_t seed,
                    uint64_t max_events, int64_t *out);
 
+/* One event of a replayed history: kind 1 scattering, 2 absorption (species: the
+ * absorbing species), 3 escape, 4 capped (species -1); the cell (at an escape: the
+ * last cell), the frequency bin after the event and the position in base-cube units
+ * (0 .. n_base per axis). */
+typedef struct rt_event {
+    int32_t kind, species, leaf, bin;
+    float pos[3];
+    int32_t pad;
+} rt_event;
+
+/* Replay at event level: as rt_trace, and the events of package ids[i] in
+ * out[i * max_out ...] (host; at most max_out each), n_out[i] (host) the number of
+ * events its history has, which may exceed max_out. Diagnostic: compares histories
+ * with an independent implementation event by event. */
+rt_status rt_trace_events(rt_grid *g, const uint64_t *ids, int64_t n, uint64_t seed,
+                          uint64_t max_events, int64_t max_out, rt_event *out,
+                          int64_t *n_out);
+
 /* Philox4x32-10 blocks for counters {id_lo, id_hi, event, block} = (ids[i], event,
  * block) under key = seed, written to out[4*i..4*i+3] (host). Diagnostic. */
 rt_status rt_philox(const uint64_t *ids, int64_t n, uint32_t event, uint32_t block,

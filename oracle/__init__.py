@@ -111,6 +111,9 @@ def lib():
             L.orc_transport.restype = C.c_int
             L.orc_trace.argtypes = [C.POINTER(_Model), C.POINTER(_Run), dp, C.c_int64, dp]
             L.orc_trace.restype = C.c_int
+            L.orc_trace_events.argtypes = [C.POINTER(_Model), C.POINTER(_Run), C.c_uint64,
+                                           C.c_int64, dp, C.POINTER(C.c_int64)]
+            L.orc_trace_events.restype = C.c_int
             L.orc_temperatures.argtypes = [C.POINTER(_Model), dp, d, dp]
             L.orc_temperatures.restype = C.c_int
             L.orc_reemit_bin.argtypes = [C.POINTER(_Model), C.c_int, C.c_int, C.c_uint64, d,
@@ -388,6 +391,28 @@ def trace(model, ids, T_frozen, seed: int = 0, n_total: int = 1,
     if rc != 0:
         raise RuntimeError(f"oracle trace failed ({rc})")
     return out
+
+
+EVENT_DTYPE = np.dtype([("kind", np.int32), ("species", np.int32), ("leaf", np.int64),
+                        ("bin", np.int32), ("pad", np.int32), ("pos", np.float64, (3,))])
+EVENT_SCATTER, EVENT_ABSORB, EVENT_ESCAPE, EVENT_CAPPED = 1, 2, 3, 4
+
+
+def trace_events(model, package_id: int, T_frozen, seed: int = 0, n_total: int = 1,
+                 max_events: int = 10_000_000, t_min: float = T_MIN_DEFAULT,
+                 max_out: int = 1 << 16):
+    """The events of one package in the frozen-temperature mode: every scattering and
+    absorption (kind, species, cell, bin after the event, position in base-cube
+    units), then its escape or cap. Returns (events, total number of events)."""
+    om = as_oracle(model)
+    out = np.zeros(max_out, dtype=EVENT_DTYPE)
+    n = C.c_int64()
+    r, keep = _run(0, seed, 0, n_total, MODE_FROZEN, max_events, t_min, T_frozen)
+    rc = lib().orc_trace_events(C.byref(om.s), C.byref(r), int(package_id), int(max_out),
+                                _ptr(out), C.byref(n))
+    if rc != 0:
+        raise RuntimeError(f"oracle event trace failed ({rc})")
+    return out[:min(n.value, max_out)].copy(), int(n.value)
 
 
 def temperatures(model, count: np.ndarray, eps: float) -> np.ndarray:

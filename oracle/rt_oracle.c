@@ -573,8 +573,30 @@ static void peel(const orc_model *m, const orc_run *r, const ctx_t *c, orc_tally
 /* Follow package `id` until it leaves the grid or reaches the event cap.
  * count may be NULL only in the frozen mode (trajectories then do not depend on
  * the counts). */
+/* Event log of one package (trace): events beyond cap are counted, not stored. */
+typedef struct {
+    orc_event *ev;
+    int64_t cap, n;
+} event_log;
+
+static void log_event(event_log *lg, int kind, int species, int64_t leaf, int bin,
+                      const double p[3])
+{
+    if (!lg) return;
+    if (lg->n < lg->cap) {
+        orc_event *e = &lg->ev[lg->n];
+        e->kind = kind;
+        e->species = species;
+        e->leaf = leaf;
+        e->bin = bin;
+        e->pad = 0;
+        e->pos[0] = p[0]; e->pos[1] = p[1]; e->pos[2] = p[2];
+    }
+    lg->n += 1;
+}
+
 static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uint64_t id,
-                       uint64_t *count, orc_tally *t, orc_trace_rec *rec)
+                       uint64_t *count, orc_tally *t, orc_trace_rec *rec, event_log *lg)
 {
     const int S = m->n_species, B = m->n_bins;
     const int64_t N = m->n_leaves;
@@ -625,7 +647,7 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
             for (int a = 0; a < 3; ++a) p[a] += sdist * d[a];
             clamp3(p, lo, hi);
             ++n_ev;
-            if (n_ev > r->max_events) { capped = 1; break; }
+            if (n_ev > r->max_events) { capped = 1; log_event(lg, 4, -1, leaf, bin, p); break; }
             interacted = 1;
             draw_block(c->key, id, (uint32_t)n_ev, 0, u);
             draw_block(c->key, id, (uint32_t)n_ev, 1, v);
@@ -651,6 +673,7 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
                 double mu = orc_hg_mu(m->g[s * B + bin], u[2]);
                 orc_rotate(d, mu, 2.0 * PI * u[3]);
                 ++n_sca;
+                log_event(lg, 1, s, leaf, bin, p);
             } else {
                 /* 4.+5. absorption: the cell's energy rises by eps; isotropic
                  * re-emission of the same energy at a new frequency */
@@ -677,6 +700,7 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
                         if (tot > 0.0) wrow = cw;
                     }
                     bin = sample_discrete(wrow, B, v[2]);
+                    log_event(lg, 2, s, leaf, bin, p);
                     peel(m, r, c, t, p, bin, 1.0 / (4.0 * PI));
                     isotropic(u[2], u[3], d);
                     ++n_abs;
@@ -692,6 +716,7 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
                 }
                 bin = orc_reemit_bin(m, s, r->mode, n, e, uf, r->t_min, v[1], v[2]);
                 if (bin < 0) { err = 1; break; }
+                log_event(lg, 2, s, leaf, bin, p);
                 peel(m, r, c, t, p, bin, 1.0 / (4.0 * PI));
                 isotropic(u[2], u[3], d);
                 ++n_abs;
@@ -705,6 +730,7 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
             ++n_cross;
         }
     }
+    if (escaped) log_event(lg, 3, -1, last_leaf, bin, p);
     int db = sed_dir_bin(d, m->n_sed_dirs);
     if (t) {
         t->emitted += 1;
@@ -751,7 +777,7 @@ int orc_transport(const orc_model *m, const orc_run *r, orc_tally *t)
     if (ctx_init(m, r, &c)) { ctx_free(&c); return -2; }
     int rc = 0;
     for (uint64_t i = 0; i < r->n_packages; ++i)
-        if (run_package(m, r, &c, r->first_id + i, t->count, t, NULL)) rc = -3;
+        if (run_package(m, r, &c, r->first_id + i, t->count, t, NULL, NULL)) rc = -3;
     ctx_free(&c);
     return rc;
 }
@@ -765,7 +791,21 @@ int orc_trace(const orc_model *m, const orc_run *r, const uint64_t *ids, int64_t
     if (ctx_init(m, r, &c)) { ctx_free(&c); return -2; }
     int rc = 0;
     for (int64_t i = 0; i < n; ++i)
-        if (run_package(m, r, &c, ids[i], NULL, NULL, &out[i])) rc = -3;
+        if (run_package(m, r, &c, ids[i], NULL, NULL, &out[i], NULL)) rc = -3;
+    ctx_free(&c);
+    return rc;
+}
+
+int orc_trace_events(const orc_model *m, const orc_run *r, uint64_t id, int64_t max_out,
+                     orc_event *ev, int64_t *n_out)
+{
+    if (check_model(m)) return -1;
+    if (r->mode != ORC_MODE_FROZEN || !r->T_frozen || max_out < 0) return -1;
+    ctx_t c;
+    if (ctx_init(m, r, &c)) { ctx_free(&c); return -2; }
+    event_log lg = {ev, max_out, 0};
+    int rc = run_package(m, r, &c, id, NULL, NULL, NULL, &lg) ? -3 : 0;
+    *n_out = lg.n;
     ctx_free(&c);
     return rc;
 }

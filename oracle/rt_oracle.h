@@ -82,6 +82,15 @@ typedef struct {               /* one package's history (frozen mode replay) */
     double dir[3];
 } orc_trace_rec;
 
+typedef struct {               /* one event of a package's history (frozen mode replay) */
+    int32_t kind;              /* 1 scattering, 2 absorption, 3 escape, 4 capped */
+    int32_t species;           /* interacting species, -1 at the end */
+    int64_t leaf;              /* cell of the event (at the end: the last cell) */
+    int32_t bin;               /* frequency bin after the event */
+    int32_t pad;
+    double pos[3];             /* position, base-cube units */
+} orc_event;
+
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform(uint32_t x);
 double orc_planck_bin(double nu0, double nu1, double T);
@@ -99,6 +108,10 @@ double orc_optical_depth(const orc_model *m, const double p_cm[3], const double 
 int orc_transport(const orc_model *m, const orc_run *r, orc_tally *t);
 int orc_trace(const orc_model *m, const orc_run *r, const uint64_t *ids, int64_t n,
               orc_trace_rec *out);
+/* The events of package `id` in the frozen mode: at most max_out are written to
+ * ev, *n_out receives the number the history has (it may exceed max_out). */
+int orc_trace_events(const orc_model *m, const orc_run *r, uint64_t id, int64_t max_out,
+                     orc_event *ev, int64_t *n_out);
 int orc_temperatures(const orc_model *m, const uint64_t *count, double eps, double *T_out);
 int orc_reemit_bin(const orc_model *m, int species, int mode, uint64_t n, double eps_over_m,
                    double u_frozen, double t_min, double xi_u, double xi_bin);

@@ -65,6 +65,7 @@ struct rt_grid {
   float* d_pah_cdf = nullptr;
   float* d_pah_cell_cdf = nullptr;  // [n_pah][N][B] per-cell re-emission spectra
   unsigned* d_pahabs = nullptr;
+  unsigned* d_pah_flag = nullptr;  // [N] PAH-active bits per cell (bit p: PAH p)
   float* d_pathabs = nullptr;  // path-length tallies [S][N]
   // peel-off images
   int* d_plane_of_bin = nullptr;         // [B]
@@ -184,6 +185,7 @@ void free_all(rt_grid* g) {
   dfree(g->d_ufrozen);
   dfree(g->d_Tscratch);
   dfree(g->d_pahabs);
+  dfree(g->d_pah_flag);
   dfree(g->d_pathabs);
   dfree(g->d_plane_of_bin);
   dfree(g->d_image);
@@ -251,6 +253,8 @@ rt_status build_pah_tables(rt_grid* g, cudaStream_t s) {
   if (!g->d_pahabs) {
     if ((st = dalloc(&g->d_pahabs, (size_t)P * g->desc.n_leaves * K)) != RT_OK) return st;
     RT_CUDA(cudaMemsetAsync(g->d_pahabs, 0, sizeof(unsigned) * P * g->desc.n_leaves * K, s));
+    if ((st = dalloc(&g->d_pah_flag, (size_t)g->desc.n_leaves)) != RT_OK) return st;
+    RT_CUDA(cudaMemsetAsync(g->d_pah_flag, 0, sizeof(unsigned) * g->desc.n_leaves, s));
   }
   std::vector<double> sigma((size_t)P * B);
   PahBuild pb{};
@@ -671,9 +675,10 @@ rt_status rt_reset(rt_grid* g, void* stream) {
                           s));
   RT_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s));
   RT_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), s));
+  // only the rows of PAH-active cells hold counts: clear those and their flags
   if (g->d_pahabs)
-    RT_CUDA(cudaMemsetAsync(g->d_pahabs, 0,
-                            sizeof(unsigned) * g->n_pah * N * g->tab.n_coarse, s));
+    RT_CUDA(launch_pah_clear(g->d_pah_flag, (long long)N, g->tab.n_coarse, g->n_pah,
+                             g->d_pahabs, g->d_pah_flag, s));
   if (g->d_pathabs) RT_CUDA(cudaMemsetAsync(g->d_pathabs, 0, sizeof(float) * S * N, s));
   if (g->images) {
     const size_t n = (size_t)g->peel.n_planes * g->peel.ny * g->peel.nx;
@@ -711,6 +716,7 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
   r->counters = g->d_counters;
   r->status = g->d_status;
   r->pahabs = g->d_pahabs;
+  r->pah_flag = g->d_pah_flag;
   r->pathabs = (o && (o->estimators & RT_EST_PATHLENGTH)) ? g->d_pathabs : nullptr;
   for (int a = 0; a < 3; ++a) {
     double p = (g->pos[a] + g->desc.half_size_cm) / g->d0;
@@ -1066,6 +1072,48 @@ rt_status rt_trace(rt_grid* g, const uint64_t* ids, int64_t n, uint64_t seed,
   return sync_status(g, nullptr);
 }
 
+rt_status rt_trace_events(rt_grid* g, const uint64_t* ids, int64_t n, uint64_t seed,
+                          uint64_t max_events, int64_t max_out, rt_event* out,
+                          int64_t* n_out) {
+  static_assert(sizeof(rt_event) == sizeof(TraceEvent), "event record layouts differ");
+  if (!g || n < 0 || max_out < 0 || (n > 0 && (!ids || !n_out || (max_out > 0 && !out))))
+    return RT_ERR_ARG;
+  if (n == 0) return RT_OK;
+  RT_CUDA(cudaSetDevice(g->dev));
+  rt_status st = build_tables(g, nullptr);
+  if (st != RT_OK) return st;
+  if (!g->frozen_ready) return RT_ERR_STATE;
+  rt_run_opts o{};
+  o.mode = RT_REEMIT_FROZEN;
+  o.max_events = max_events;
+  DevRun r;
+  if ((st = fill_run(g, 0, seed, 0, &o, &r)) != RT_OK) return st;
+  DevTables t = g->tab;
+  t.u_frozen = g->d_ufrozen;
+  t.pah_cell_cdf = g->d_pah_cell_cdf;
+  unsigned long long* d_ids = nullptr;
+  long long *d_rec = nullptr, *d_n = nullptr;
+  TraceEvent* d_ev = nullptr;
+  const size_t n_ev = (size_t)n * (size_t)max_out;
+  if ((st = dalloc(&d_ids, (size_t)n)) == RT_OK && (st = dalloc(&d_rec, (size_t)n * 9)) == RT_OK &&
+      (st = dalloc(&d_n, (size_t)n)) == RT_OK && (n_ev == 0 || (st = dalloc(&d_ev, n_ev)) == RT_OK)) {
+    cudaError_t e = cudaMemcpy(d_ids, ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = launch_trace(g->g, t, r, d_ids, n, d_rec, nullptr, d_ev, max_out, d_n);
+    if (e == cudaSuccess && n_ev)
+      e = cudaMemcpy(out, d_ev, sizeof(TraceEvent) * n_ev, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(n_out, d_n, sizeof(int64_t) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = RT_ERR_CUDA;
+  }
+  dfree(d_ids);
+  dfree(d_rec);
+  dfree(d_n);
+  dfree(d_ev);
+  if (st != RT_OK) return st;
+  return sync_status(g, nullptr);
+}
+
 rt_status rt_set_pah(rt_grid* g, int species, int n_carbon, int n_hydrogen, double mol_mass_g,
                      const double* modes, int n_groups, int n_levels, double t_top) {
   if (!g || !modes) return RT_ERR_ARG;
@@ -1317,7 +1365,7 @@ static rt_status pah_emission_impl(rt_grid* g, int64_t first_cell, int64_t n_cel
   }
   // the cells where a PAH absorbed anything, in one list for the whole range
   RT_CUDA(cudaMemsetAsync(g->d_ucount, 0, 2 * sizeof(unsigned), s));
-  RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell, n_cells,
+  RT_CUDA(launch_compact(g->ptab, g->d_pah_flag, g->desc.n_leaves, pah, first_cell, n_cells,
                          nullptr, nullptr, g->d_list, g->d_ucount, s));
   unsigned na = 0;
   RT_CUDA(cudaMemcpyAsync(&na, g->d_ucount, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -1364,7 +1412,7 @@ static rt_status pah_emission_impl(rt_grid* g, int64_t first_cell, int64_t n_cel
                                      compact ? dst + (size_t)b0 * B : dst, s,
                                      compact ? nullptr : lst));
       }
-      RT_CUDA(launch_compact(g->ptab, g->d_pahabs, g->desc.n_leaves, pah, first_cell, nb,
+      RT_CUDA(launch_compact(g->ptab, g->d_pah_flag, g->desc.n_leaves, pah, first_cell, nb,
                              g->d_sflag, compact ? nullptr : lst, g->d_list2, g->d_ucount + 1,
                              s, (int)b0));
     }

@@ -81,6 +81,7 @@ struct DevRun {
   unsigned long long* counters;   // [kNumCounters]
   unsigned int* status;
   unsigned* pahabs;               // [n_pah][n_leaves][n_coarse] PAH absorptions
+  unsigned* pah_flag;             // [n_leaves] bit p set: PAH p absorbed in the cell
   float* pathabs;                 // [S][n_leaves] path-length tallies, or null
   float src[3];                   // source position, base-cube units
   float beam[3];
@@ -153,9 +154,17 @@ cudaError_t launch_image_profile(const double* image, int nx, int ny, int plane_
                                  cudaStream_t s);
 cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const DevRun& r,
                                    bool fp64, int threads, cudaStream_t s);
+// One event of a replayed history (rt_trace_events): kind 1 scattering, 2 absorption,
+// 3 escape, 4 capped; position in base-cube units.
+struct TraceEvent {
+  int kind, species, leaf, bin;
+  float pos[3];
+  int pad;
+};
 cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
                          const unsigned long long* ids, long long n, long long* out,
-                         cudaStream_t s);
+                         cudaStream_t s, TraceEvent* ev = nullptr, long long ev_cap = 0,
+                         long long* ev_n = nullptr);
 cudaError_t launch_build_links(const DevGrid& g, const int32_t* leaf_ijk, int32_t* links,
                                cudaStream_t s);
 
@@ -259,7 +268,9 @@ cudaError_t launch_surrogate_check(const float* Y, const float* X, const float* 
 cudaError_t launch_surrogate_add(const float* Y, const float* p_abs, long long n, int B,
                                  const unsigned char* flag, float* j_out, cudaStream_t s,
                                  const int* list = nullptr);
-cudaError_t launch_compact(const PahTables& t, const unsigned* pahabs, long long N, int pah,
+cudaError_t launch_pah_clear(const unsigned* pah_flag, long long N, int K, int n_pah,
+                             unsigned* pahabs, unsigned* pah_flag_out, cudaStream_t s);
+cudaError_t launch_compact(const PahTables& t, const unsigned* pah_flag, long long N, int pah,
                            long long first, long long n, const unsigned char* flag,
                            const int* list, int* out, unsigned* count, cudaStream_t s,
                            int off = 0);

@@ -478,25 +478,19 @@ __global__ void k_surrogate_add(const float* Y, const float* p_abs, long long n,
 }
 
 // Compaction: rows i < n with sel(i) true are appended to out (order not kept);
-// *count receives their number. sel = any PAH absorption in cell first + i (all PAH
-// or only `pah`), or flag[i] when flag is given (then out receives list[i], or
-// off + i without a list).
-__global__ void k_compact(const unsigned* pahabs, long long N, int K, int n_pah, int pah,
-                          long long first, long long n, const unsigned char* flag,
-                          const int* list, int off, int* out, unsigned* count) {
+// *count receives their number. sel = a PAH absorption in cell first + i (any PAH
+// or only `pah`: the cell's flag word), or flag[i] when flag is given (then out
+// receives list[i], or off + i without a list).
+__global__ void k_compact(const unsigned* pah_flag, int pah, long long first, long long n,
+                          const unsigned char* flag, const int* list, int off, int* out,
+                          unsigned* count) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   bool sel = false;
   if (i < n) {
-    if (flag) {
+    if (flag)
       sel = flag[i] != 0;
-    } else {
-      for (int p = 0; p < n_pah && !sel; ++p) {
-        if (pah >= 0 && p != pah) continue;
-        const unsigned* cnt = pahabs + ((size_t)p * N + first + i) * K;
-        for (int k = 0; k < K; ++k)
-          if (cnt[k]) { sel = true; break; }
-      }
-    }
+    else
+      sel = (pah_flag[first + i] & (pah >= 0 ? 1u << pah : ~0u)) != 0u;
   }
   const unsigned m = __ballot_sync(0xffffffffu, sel);
   if (!m) return;
@@ -508,6 +502,24 @@ __global__ void k_compact(const unsigned* pahabs, long long N, int K, int n_pah,
   if (sel)
     out[base + __popc(m & ((1u << lane) - 1u))] =
         flag ? (list ? list[i] : off + (int)i) : (int)i;
+}
+
+// Zero the absorbed spectra of the PAH-active cells and their flags (the other
+// rows are zero already). A warp per cell: one coalesced row of K words per PAH.
+__global__ void k_pah_clear(const unsigned* pah_flag, long long N, int K, int n_pah,
+                            unsigned* pahabs, unsigned* flag_out) {
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31;
+  for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < N;
+       c += warps) {
+    const unsigned f = pah_flag[c];
+    if (f == 0u) continue;
+    for (int p = 0; p < n_pah; ++p)
+      if (f & (1u << p))
+        for (int k = lane; k < K; k += 32) pahabs[((size_t)p * N + c) * K + k] = 0u;
+    __syncwarp();
+    if (lane == 0) flag_out[c] = 0u;
+  }
 }
 
 __global__ void k_count_flags(const unsigned char* flag, long long n, unsigned long long* out) {
@@ -751,13 +763,28 @@ cudaError_t launch_pah_cell_cdf(const float* J, long long n, int B, float* out, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const PahTables& t, const unsigned* pahabs, long long N, int pah,
+cudaError_t launch_compact(const PahTables& t, const unsigned* pah_flag, long long N, int pah,
                            long long first, long long n, const unsigned char* flag,
                            const int* list, int* out, unsigned* count, cudaStream_t s,
                            int off) {
+  (void)t;
+  (void)N;
   if (n <= 0) return cudaSuccess;
-  k_compact<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pahabs, N, t.K, t.n_pah, pah, first, n,
-                                                         flag, list, off, out, count);
+  k_compact<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pah_flag, pah, first, n, flag, list,
+                                                         off, out, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pah_clear(const unsigned* pah_flag, long long N, int K, int n_pah,
+                             unsigned* pahabs, unsigned* flag_out, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (N * 32 + 255) / 256;
+  const long long cap = (long long)(sms > 0 ? sms : 152) * 8;
+  if (blocks > cap) blocks = cap;
+  k_pah_clear<<<(unsigned)blocks, 256, 0, s>>>(pah_flag, N, K, n_pah, pahabs, flag_out);
   return cudaGetLastError();
 }
 

@@ -573,12 +573,13 @@ __device__ __forceinline__ void pah_bin(Pkg<R>& k, const DevGrid& g, const DevTa
 }
 
 // Absorption by a PAH species: tally the photon in the cell's coarse absorbed
-// spectrum, then draw the new bin.
+// spectrum and mark the cell as PAH-active for that PAH, then draw the new bin.
 template <typename R>
 __device__ __forceinline__ void pah_absorb(Pkg<R>& k, const DevGrid& g, const DevTables& t,
                                            const DevRun& r, int p, int leaf, const uint4& w1) {
   const int kc = (k.bin * t.n_coarse) / g.B;
   atomicAdd(&r.pahabs[((size_t)p * g.n_leaves + leaf) * t.n_coarse + kc], 1u);
+  atomicOr(&r.pah_flag[leaf], 1u << p);
   pah_bin(k, g, t, p, leaf, w1);
 }
 
@@ -1027,10 +1028,33 @@ __global__ void __launch_bounds__(256) k_transport_batch(const ModelDesc* models
 // ---------------------------------------------------------------- replay
 // Frozen mode only: counts do not steer the path, so each listed package is
 // followed alone and its history recorded.
+// ev (optional): the package's events, at most ev_cap of them at ev + i ev_cap;
+// ev_n[i] receives how many the history has.
+__device__ __forceinline__ void trace_event(TraceEvent* ev, long long cap, long long& n,
+                                            int kind, int species, int leaf, int bin,
+                                            const float p[3]) {
+  if (ev && n < cap) {
+    TraceEvent e;
+    e.kind = kind;
+    e.species = species;
+    e.leaf = leaf;
+    e.bin = bin;
+    e.pos[0] = p[0];
+    e.pos[1] = p[1];
+    e.pos[2] = p[2];
+    e.pad = 0;
+    ev[n] = e;
+  }
+  ++n;
+}
+
 __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long long* ids,
-                        long long n, long long* out) {
+                        long long n, long long* out, TraceEvent* ev, long long ev_cap,
+                        long long* ev_n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  TraceEvent* my_ev = ev ? ev + i * ev_cap : nullptr;
+  long long n_ev = 0;
   Tally tl = {};
   Pkg<float> k;
   emit<float>(k, ids[i], r, t.star_cdf, g.B);
@@ -1050,19 +1074,35 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
     const int a = advance_linked(k, c, g, t.kap, tl.levels, nullptr);
     rec[8] = lf;
     if (a == kCrossed) { ++rec[3]; continue; }
-    if (a == kEscaped) { ++rec[3]; rec[4] = 1; break; }
+    if (a == kEscaped) {
+      ++rec[3];
+      rec[4] = 1;
+      trace_event(my_ev, ev_cap, n_ev, 3, -1, lf, k.bin, k.p);
+      break;
+    }
     if (a == kError) { atomicOr(r.status, kStatusTree); break; }
-    if (++k.event > r.max_events) { rec[5] = 1; break; }
+    if (++k.event > r.max_events) {
+      rec[5] = 1;
+      trace_event(my_ev, ev_cap, n_ev, 4, -1, c.leaf, k.bin, k.p);
+      break;
+    }
     uint4 w1;
+    const float pi[3] = {k.p[0], k.p[1], k.p[2]};
     int s = interact<float>(k, g, t.kap, c.leaf, r, w1);
-    if (s < 0) { ++rec[2]; continue; }
+    if (s < 0) {
+      ++rec[2];
+      trace_event(my_ev, ev_cap, n_ev, 1, -1, c.leaf, k.bin, pi);
+      continue;
+    }
     if (t.pah_of[s] >= 0) {
       pah_bin(k, g, t, t.pah_of[s], c.leaf, w1);  // replay does not tally
     } else {
       reemit<float>(k, g, t, r, s, c.leaf, c.level(), 0ull, w1, tl);
     }
+    trace_event(my_ev, ev_cap, n_ev, 2, s, c.leaf, k.bin, pi);
     ++rec[1];
   }
+  if (ev_n) ev_n[i] = n_ev;
   rec[0] = k.event;
   rec[6] = k.bin;
   rec[7] = dir_bin(k.d[2], g.n_dir);
@@ -1254,9 +1294,10 @@ cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* ch
 
 cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
                          const unsigned long long* ids, long long n, long long* out,
-                         cudaStream_t s) {
+                         cudaStream_t s, TraceEvent* ev, long long ev_cap, long long* ev_n) {
   if (n <= 0) return cudaSuccess;
-  k_trace<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, t, r, ids, n, out);
+  k_trace<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, t, r, ids, n, out, ev, ev_cap,
+                                                      ev_n);
   return cudaGetLastError();
 }
 

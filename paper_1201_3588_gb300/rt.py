@@ -25,6 +25,10 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime e
           6: "package ids beyond the planned total", 7: "malformed grid met on the device",
           8: "request exceeds a fixed maximum"}
 
+EVENT_DTYPE = np.dtype([("kind", np.int32), ("species", np.int32), ("leaf", np.int32),
+                        ("bin", np.int32), ("pos", np.float32, (3,)), ("pad", np.int32)])
+EVENT_SCATTER, EVENT_ABSORB, EVENT_ESCAPE, EVENT_CAPPED = 1, 2, 3, 4
+
 TRACE_FIELDS = ("events", "absorptions", "scatters", "crossings", "escaped", "capped",
                 "final_bin", "dir_bin", "last_leaf")
 
@@ -96,6 +100,8 @@ SIGNATURES = {
     "rt_image_profile": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                          C.c_void_p],
     "rt_trace": [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_void_p],
+    "rt_trace_events": [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_uint64, C.c_int64,
+                        C.c_void_p, C.c_void_p],
     "rt_philox": [C.c_void_p, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p],
     "rt_status_string": [C.c_int],
     "rt_batch_create": [C.c_void_p, C.c_int, C.c_void_p, C.c_uint64, C.POINTER(_Opts),
@@ -424,6 +430,17 @@ class Grid:
         _check(load().rt_trace(self._h, idv.ctypes.data, idv.shape[0], int(seed),
                                int(max_events), out.ctypes.data), "rt_trace")
         return out
+
+    def trace_events(self, ids, seed: int = 0, max_events: int = 0, max_out: int = 4096):
+        """Event-level replay (frozen mode): for each id a structured array of its
+        events (kind, species, leaf, bin, pos), and the total number of events."""
+        idv = np.ascontiguousarray(ids, dtype=np.uint64)
+        out = np.zeros((idv.shape[0], max_out), dtype=EVENT_DTYPE)
+        n = np.zeros(idv.shape[0], dtype=np.int64)
+        _check(load().rt_trace_events(self._h, idv.ctypes.data, idv.shape[0], int(seed),
+                                      int(max_events), int(max_out), out.ctypes.data,
+                                      n.ctypes.data), "rt_trace_events")
+        return [out[i, :min(int(n[i]), max_out)].copy() for i in range(idv.shape[0])], n
 
 
 def pah_temperature_distribution(cases, nu_edges, sigma, n_levels: int = 400,

@@ -133,3 +133,29 @@ def test_active_cell_emission_equals_range_form(pah_model):
         with pytest.raises(rt.RTError) as e:
             g.pah_emission_active(cells=small_c, out=small_r)
         assert e.value.code == 6
+
+
+def test_reset_clears_pah_tallies(pah_model):
+    """rt_reset clears the absorbed spectra of exactly the cells that hold counts:
+    after a first run and a reset, a second run's tallies and active cells equal
+    those of the same run on a fresh grid (frozen mode: package histories are pure
+    functions of the seed, so the sums are identical)."""
+    N = 200_000
+    Tf = frozen_field(pah_model)
+    out = []
+    for first_seed in (1, None):
+        with rt.Grid(pah_model) as g:
+            g.emit_star(N)
+            g.set_frozen_temperatures(Tf)
+            if first_seed is not None:
+                g.transport(N, seed=first_seed, mode=rt.REEMIT_FROZEN)
+                assert g.pah_absorbed().sum() > 0
+                g.reset()
+                assert g.pah_absorbed().sum() == 0
+            g.transport(N, seed=2, mode=rt.REEMIT_FROZEN)
+            cells, _, _ = g.pah_emission_active()
+            out.append((g.pah_absorbed(), np.sort(cells)))
+    (a1, c1), (a2, c2) = out
+    assert np.array_equal(a1, a2)
+    assert np.array_equal(c1, c2)
+    assert np.array_equal(c2, np.nonzero(a2.sum(axis=(0, 2)) > 0)[0])
