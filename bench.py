@@ -765,14 +765,27 @@ def e2e_rate(model, n, world, first, steps, net=None, params=None, tol=0.05, max
             "host_buffers": "pinned"}
 
 
+def _oracle_batch_worker(job):
+    i, seconds = job
+    m, n = _POOL_MODEL[i % len(_POOL_MODEL)]
+    return _oracle_prefix(m, 0, n, seconds)
+
+
 def run_batch(args):
     """Config of many uneven models in one graph-captured persistent launch: a step is
     one replay of (reset, batched transport, every model's temperatures)."""
-    import torch
-    from paper_1201_3588_gb300 import autotune, rt, workloads as w
+    global _POOL_MODEL
+    from paper_1201_3588_gb300 import workloads as w
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     models = w.batch_models(n_models=args.batch_models, seed=0, n_bins=100)
+    pool = None
+    if args.cpu_seconds > 0:  # forked before CUDA; each process follows one model
+        import multiprocessing as mp
+        _POOL_MODEL = models
+        pool = mp.get_context("fork").Pool(host_cores())
+    import torch
+    from paper_1201_3588_gb300 import autotune, rt
+    torch.cuda.set_device(local)
     grids = []
     for m, n in models:
         g = rt.Grid(m)
@@ -780,9 +793,9 @@ def run_batch(args):
         grids.append(g)
     npk = [n for _, n in models]
     total = sum(npk)
-    # tune on the largest model's class
-    big = max(range(len(models)), key=lambda i: grids[i].N)
-    opts = autotune.tune(grids[big], models[big][0].recipe["tau_v"], n_probe=1_000_000)
+    # one launch configuration for the whole batch, tuned on whole-batch probes
+    opts = autotune.tune_batch(grids, [m.recipe["tau_v"] for m, _ in models], npk,
+                               fraction=0.02)
     b = rt.Batch(grids, npk, seed=0, **opts)
     stream = torch.cuda.Stream()
     for _ in range(args.warmup):
@@ -797,6 +810,42 @@ def run_batch(args):
         torch.cuda.synchronize()
     el = a.elapsed_time(e) / 1e3
     c = [g.counters() for g in grids]
+    # the batched transport launch alone, for the roofline
+    kt = []
+    for _ in range(3):
+        for g in grids:
+            g.reset(stream)
+        a.record(stream)
+        b.run(reset=False, temperatures=False, stream=stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        kt.append(a.elapsed_time(e) / 1e3)
+    kmean = sum(kt) / len(kt)
+    c2 = [g.counters() for g in grids]
+    bytes_launch = sum(crossing_bytes(x, m.n_species, m.tree.max_level)
+                       for x, (m, _) in zip(c2, models))
+    hbm, src = peaks()
+    achieved = bytes_launch / kmean / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "kernel": "k_transport_batch", "kernel_ms": 1e3 * kmean,
+            "algorithmic_bytes_per_launch": bytes_launch}
+    b.close()
+    for g in grids:
+        g.close()
+    torch.cuda.empty_cache()
+    e2e = batch_e2e(models, opts, args.e2e_steps) if args.e2e_steps > 0 else None
+    cpu = None
+    if pool is not None:
+        res = pool.map(_oracle_batch_worker,
+                       [(i, args.cpu_seconds) for i in range(host_cores())])
+        pool.close()
+        pool.join()
+        done = sum(r[0] for r in res)
+        secs = max(r[1] for r in res)
+        cpu = {"value": done / secs, "unit": UNIT, "cores": len(res), "kind": "oracle",
+               "sample": f"{done} packages of the batch's first {min(len(res), len(models))} "
+                         f"models (one process each, BW mode, {secs:.1f} s)"}
     emitted = sum(x["emitted"] for x in c)
     line = {"metric": METRIC, "value": total * args.steps / el, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -804,12 +853,53 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": f"batch of {len(models)} uneven sphere/disk models, 100 bins, "
                                    "one graph-captured persistent launch",
-                       "packages_per_step": total, "leaves_total": sum(g.N for g in grids),
+                       "packages_per_step": total, "leaves_total": sum(m.tree.n_leaves
+                                                                       for m, _ in models),
                        "autotuned": opts},
-            "gpu_launches": (1 + len(grids)) * args.steps, "clocks": clk.summary(),
-            "check": {"emitted_last_step": emitted,
-                      "errors": sum(x["errors"] for x in c)}}
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": (1 + len(models)) * args.steps, "clocks": clk.summary(),
+            "per_step": {"crossings": sum(x["crossings"] for x in c),
+                         "absorptions": sum(x["absorptions"] for x in c),
+                         "emitted": emitted, "errors": sum(x["errors"] for x in c)}}
     print(json.dumps(line), flush=True)
+
+
+def batch_e2e(models, opts, steps):
+    """The batch through the public API from host arrays: every step creates all the
+    grids, plans and runs the batched launch, reads every model's temperatures and
+    escaped spectrum back to host memory and destroys everything."""
+    import numpy as np
+    import torch
+    from paper_1201_3588_gb300 import rt
+    T_host = [np.zeros((m.n_species, m.tree.n_leaves), dtype=np.float32) for m, _ in models]
+    npk = [n for _, n in models]
+    times = []
+    for k in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grids = []
+        for m, n in models:
+            g = rt.Grid(m)
+            g.emit_star(n)
+            grids.append(g)
+        b = rt.Batch(grids, npk, seed=100 + k, **opts)
+        b.run(reset=True, temperatures=True)
+        for i, g in enumerate(grids):
+            b.temperatures(i, out=T_host[i])
+            g.sed()
+        b.close()
+        for g in grids:
+            g.close()
+        torch.cuda.synchronize()
+        if k > 0:
+            times.append(time.perf_counter() - t0)
+    h2d = sum(4 * m.tree.n_base ** 3 + 32 * m.tree.n_blocks + 8 * m.n_species * m.tree.n_leaves
+              + 8 * (m.n_bins + 1) + 24 * m.n_species * m.n_bins for m, _ in models)
+    d2h = sum(4 * m.n_species * m.tree.n_leaves + 16 * m.n_sed_dirs * m.n_bins + 8
+              for m, _ in models)
+    return {"value": sum(npk) / (sum(times) / len(times)), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": 1e3 * sum(times) / len(times), "host_buffers": "pageable"}
 
 
 def main():

@@ -244,7 +244,8 @@ rt_status rt_image_profile(rt_grid *g, int plane_a, int plane_b, int half_rows, 
 typedef struct rt_batch rt_batch;
 
 /* Plan packages 0 .. n_packages[m]-1 of every grid m (seed + m keys model m's Philox
- * streams; o: as rt_transport, pool kernel only; chunk 0: 4096). Builds missing
+ * streams; o: as rt_transport, pool kernel only, o->threads the threads per block
+ * of the batched launch; chunk 0: 4096). Builds missing
  * tables (synchronising) and allocates the plan's device arrays. The grids must
  * outlive the plan and stay on the current device. */
 rt_status rt_batch_create(rt_grid *const *grids, int n, const uint64_t *n_packages,
@@ -270,10 +271,10 @@ rt_status rt_batch_temperatures(rt_batch *b, int model, float *T_out, int mem, v
 rt_status rt_trace(rt_grid *g, const uint64_t *ids, int64_t n, uint64_t seed,
                    uint64_t max_events, int64_t *out);
 
-/* One event of a replayed history: kind 1 scattering, 2 absorption (species: the
- * absorbing species), 3 escape, 4 capped (species -1); the cell (at an escape: the
- * last cell), the frequency bin after the event and the position in base-cube units
- * (0 .. n_base per axis). */
+/* One event of a replayed history: kind 0 emission (cell -1), 1 scattering,
+ * 2 absorption (species: the absorbing species), 3 escape, 4 capped (species -1
+ * except for absorptions); the cell (at an escape: the last cell), the frequency bin
+ * after the event and the position in base-cube units (0 .. n_base per axis). */
 typedef struct rt_event {
     int32_t kind, species, leaf, bin;
     float pos[3];

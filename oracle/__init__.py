@@ -395,15 +395,16 @@ def trace(model, ids, T_frozen, seed: int = 0, n_total: int = 1,
 
 EVENT_DTYPE = np.dtype([("kind", np.int32), ("species", np.int32), ("leaf", np.int64),
                         ("bin", np.int32), ("pad", np.int32), ("pos", np.float64, (3,))])
-EVENT_SCATTER, EVENT_ABSORB, EVENT_ESCAPE, EVENT_CAPPED = 1, 2, 3, 4
+EVENT_EMIT, EVENT_SCATTER, EVENT_ABSORB, EVENT_ESCAPE, EVENT_CAPPED = 0, 1, 2, 3, 4
 
 
 def trace_events(model, package_id: int, T_frozen, seed: int = 0, n_total: int = 1,
                  max_events: int = 10_000_000, t_min: float = T_MIN_DEFAULT,
                  max_out: int = 1 << 16):
-    """The events of one package in the frozen-temperature mode: every scattering and
-    absorption (kind, species, cell, bin after the event, position in base-cube
-    units), then its escape or cap. Returns (events, total number of events)."""
+    """The events of one package in the frozen-temperature mode: its emission (bin,
+    source position), every scattering and absorption (kind, species, cell, bin after
+    the event, position in base-cube units), then its escape or cap. Returns (events,
+    total number of events)."""
     om = as_oracle(model)
     out = np.zeros(max_out, dtype=EVENT_DTYPE)
     n = C.c_int64()

@@ -616,6 +616,7 @@ static int run_package(const orc_model *m, const orc_run *r, const ctx_t *c, uin
     }
     double tau = -log(u[3]);
     for (int a = 0; a < 3; ++a) p[a] = c->src[a];
+    log_event(lg, 0, -1, -1, bin, p);
     if (m->source_kind != ORC_SOURCE_BEAM) peel(m, r, c, t, p, bin, 1.0 / (4.0 * PI));
 
     for (;;) {

@@ -83,7 +83,8 @@ typedef struct {               /* one package's history (frozen mode replay) */
 } orc_trace_rec;
 
 typedef struct {               /* one event of a package's history (frozen mode replay) */
-    int32_t kind;              /* 1 scattering, 2 absorption, 3 escape, 4 capped */
+    int32_t kind;              /* 0 emission, 1 scattering, 2 absorption, 3 escape,
+                                  4 capped */
     int32_t species;           /* interacting species, -1 at the end */
     int64_t leaf;              /* cell of the event (at the end: the last cell) */
     int32_t bin;               /* frequency bin after the event */

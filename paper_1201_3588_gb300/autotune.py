@@ -1,8 +1,8 @@
-"""Autotuner of the packet-pool launch: for a grid, time the transport of a package
-prefix under each candidate (resident blocks per SM, interaction batch, refill
-period) with CUDA events and keep the fastest. Results are cached in a JSON file
-keyed by the workload class (cells to the nearest power of two, bins, optical-depth
-decade)."""
+"""Autotuner of the packet-pool launch: for a grid (or a batch of grids), time the
+transport of a package prefix under each candidate (resident blocks per SM, threads
+per block, interaction batch, refill period) with CUDA events and keep the fastest.
+Results are cached in a JSON file keyed by the workload class (cells to the nearest
+power of two, bins, optical-depth decade; for a batch, its models' classes)."""
 from __future__ import annotations
 
 import itertools
@@ -13,7 +13,8 @@ from typing import Dict, Optional
 
 from . import rt
 
-CANDIDATES = dict(blocks_per_sm=(0, 5), interaction_batch=(4, 6, 8, 12), refill_period=(8, 16, 32))
+CANDIDATES = dict(blocks_per_sm=(0, 5), threads=(128, 256), interaction_batch=(4, 8, 12),
+                  refill_period=(16, 32))
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1201_3588_gb300",
                              "autotune.json")
 
@@ -45,8 +46,8 @@ def tune(grid: "rt.Grid", tau_v: float, n_probe: int = 2_000_000, cache: Optiona
     n_probe = min(n_probe, getattr(grid, "n_total", n_probe))
     grid.transport(min(n_probe, 100_000), seed=1)      # warm
     best = None
-    for bps, ib, rp in itertools.product(*CANDIDATES.values()):
-        opts = dict(blocks_per_sm=bps, interaction_batch=ib, refill_period=rp)
+    for values in itertools.product(*CANDIDATES.values()):
+        opts = dict(zip(CANDIDATES, values))
         grid.reset(s)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)
@@ -59,9 +60,59 @@ def tune(grid: "rt.Grid", tau_v: float, n_probe: int = 2_000_000, cache: Optiona
     grid.reset(s)
     torch.cuda.synchronize()
     db[key] = {"opts": best[1], "ms_per_probe": best[0], "n_probe": n_probe}
+    _store(path, db)
+    return best[1]
+
+
+def _store(path, db):
     os.makedirs(os.path.dirname(path), exist_ok=True)
     tmp = path + f".tmp{os.getpid()}"
     with open(tmp, "w") as f:
         json.dump(db, f, indent=1, sort_keys=True)
     os.replace(tmp, path)
+
+
+def batch_key(grids, tau_vs, n_packages) -> str:
+    classes = sorted(workload_key(g, t) for g, t in zip(grids, tau_vs))
+    h = 0
+    for c in classes:
+        for ch in c.encode():
+            h = (h * 131 + ch) % (1 << 61)
+    pk = int(round(math.log2(max(sum(n_packages), 1))))
+    return f"batch{len(grids)}-pk2^{pk}-{h:016x}"
+
+
+def tune_batch(grids, tau_vs, n_packages, fraction: float = 0.05, seed: int = 0,
+               cache: Optional[str] = None, force: bool = False) -> Dict[str, int]:
+    """Best launch options for one batched launch of these grids: every candidate
+    runs the whole batch on `fraction` of each model's packages (at least one each),
+    so the choice weighs every model class by the work it brings."""
+    import torch
+    path = cache or DEFAULT_CACHE
+    db = _load(path)
+    key = batch_key(grids, tau_vs, n_packages)
+    if key in db and not force:
+        return db[key]["opts"]
+    probe = [max(1, int(n * fraction)) for n in n_packages]
+    s = torch.cuda.current_stream()
+    best = None
+    for values in itertools.product(*CANDIDATES.values()):
+        opts = dict(zip(CANDIDATES, values))
+        b = rt.Batch(grids, probe, seed=seed, **opts)
+        b.run(reset=True, temperatures=False, stream=s)       # warm
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        b.run(reset=True, temperatures=False, stream=s)
+        e.record(s)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e)
+        b.close()
+        if best is None or ms < best[0]:
+            best = (ms, opts)
+    for g in grids:
+        g.reset(s)
+    torch.cuda.synchronize()
+    db[key] = {"opts": best[1], "ms_per_probe": best[0], "probe_packages": sum(probe)}
+    _store(path, db)
     return best[1]
+

@@ -1529,6 +1529,7 @@ struct rt_batch {
   unsigned long long* d_next = nullptr;
   long long n_chunks = 0;
   int blocks_per_sm = 0;
+  int threads = 256;  // threads per block of the batched launch
   int s_fixed = 0;  // the species count every model shares (walk compiled for it), else 0
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1556,7 +1557,8 @@ rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packag
   *out = nullptr;
   if (chunk == 0) chunk = 4096;
   if (o && (o->kernel != RT_KERNEL_POOL || o->blocks_per_sm < 0 || o->blocks_per_sm > 32 ||
-            o->refill_period < 0 || o->interaction_batch < 0 || o->interaction_batch > 32))
+            o->refill_period < 0 || o->interaction_batch < 0 || o->interaction_batch > 32 ||
+            o->threads < 0 || o->threads % 32 != 0 || o->threads > 256))
     return RT_ERR_ARG;
   rt_batch* b = new (std::nothrow) rt_batch();
   if (!b) return RT_ERR_OOM;
@@ -1607,6 +1609,7 @@ rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packag
   }
   b->n_chunks = (long long)chunks.size();
   b->blocks_per_sm = o ? o->blocks_per_sm : 0;
+  b->threads = (o && o->threads > 0) ? o->threads : 256;
   b->s_fixed = grids[0]->desc.n_species;
   for (int m = 0; m < n; ++m)  // the fixed-count walk runs without the path-length tally
     if (grids[m]->desc.n_species != b->s_fixed || desc[(size_t)m].r.pathabs) b->s_fixed = 0;
@@ -1641,7 +1644,7 @@ rt_status rt_batch_run(rt_batch* b, int reset, int temperatures, void* stream) {
   RT_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), s));
   if (b->n_chunks > 0)
     RT_CUDA(launch_transport_batch(b->d_models, b->d_chunks, b->n_chunks, b->d_next,
-                                   b->blocks_per_sm, b->s_fixed, s));
+                                   b->blocks_per_sm, b->s_fixed, b->threads, s));
   if (temperatures)
     for (rt_grid* g : b->grids)
       RT_CUDA(launch_temperatures(g->g, g->tab, g->d_count, g->d_Tscratch, g->d_counters, s));

@@ -139,7 +139,8 @@ struct BatchChunk {
 // without the path-length tally), 0 otherwise
 cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* chunks,
                                    long long n_chunks, unsigned long long* next_chunk,
-                                   int blocks_per_sm, int s_fixed, cudaStream_t s);
+                                   int blocks_per_sm, int s_fixed, int threads,
+                                   cudaStream_t s);
 cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
                                   int blocks_per_sm, int threads, cudaStream_t s,
                                   const DevPeel* peel = nullptr);
@@ -154,8 +155,8 @@ cudaError_t launch_image_profile(const double* image, int nx, int ny, int plane_
                                  cudaStream_t s);
 cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const DevRun& r,
                                    bool fp64, int threads, cudaStream_t s);
-// One event of a replayed history (rt_trace_events): kind 1 scattering, 2 absorption,
-// 3 escape, 4 capped; position in base-cube units.
+// One event of a replayed history (rt_trace_events): kind 0 emission, 1 scattering,
+// 2 absorption, 3 escape, 4 capped; position in base-cube units.
 struct TraceEvent {
   int kind, species, leaf, bin;
   float pos[3];

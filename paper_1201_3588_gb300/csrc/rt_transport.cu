@@ -1058,6 +1058,7 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
   Tally tl = {};
   Pkg<float> k;
   emit<float>(k, ids[i], r, t.star_cdf, g.B);
+  trace_event(my_ev, ev_cap, n_ev, 0, -1, -1, k.bin, k.p);
   long long rec[9] = {0, 0, 0, 0, 0, 0, 0, 0, -1};
   const unsigned long long t0 = global_ns();
   unsigned steps = 0;
@@ -1269,27 +1270,32 @@ cudaError_t launch_transport_plain(const DevGrid& g, const DevTables& t, const D
 template <int kS>
 static cudaError_t launch_batch_variant(const ModelDesc* models, const BatchChunk* chunks,
                                         long long n_chunks, unsigned long long* next_chunk,
-                                        int blocks_per_sm, cudaStream_t s) {
+                                        int blocks_per_sm, int threads, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_batch<kS>, 256, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_batch<kS>, threads, 0);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
-  k_transport_batch<kS><<<sms * bps, 256, 0, s>>>(models, chunks, n_chunks, next_chunk);
+  k_transport_batch<kS><<<sms * bps, threads, 0, s>>>(models, chunks, n_chunks, next_chunk);
   return cudaGetLastError();
 }
 
 cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* chunks,
                                    long long n_chunks, unsigned long long* next_chunk,
-                                   int blocks_per_sm, int s_fixed, cudaStream_t s) {
+                                   int blocks_per_sm, int s_fixed, int threads,
+                                   cudaStream_t s) {
+  if (threads <= 0) threads = 256;
+  if (threads % 32 != 0 || threads > 256) return cudaErrorInvalidValue;
   if (s_fixed == 2)
-    return launch_batch_variant<2>(models, chunks, n_chunks, next_chunk, blocks_per_sm, s);
-  return launch_batch_variant<0>(models, chunks, n_chunks, next_chunk, blocks_per_sm, s);
+    return launch_batch_variant<2>(models, chunks, n_chunks, next_chunk, blocks_per_sm,
+                                   threads, s);
+  return launch_batch_variant<0>(models, chunks, n_chunks, next_chunk, blocks_per_sm, threads,
+                                 s);
 }
 
 cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,

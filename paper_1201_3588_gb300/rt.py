@@ -27,7 +27,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime e
 
 EVENT_DTYPE = np.dtype([("kind", np.int32), ("species", np.int32), ("leaf", np.int32),
                         ("bin", np.int32), ("pos", np.float32, (3,)), ("pad", np.int32)])
-EVENT_SCATTER, EVENT_ABSORB, EVENT_ESCAPE, EVENT_CAPPED = 1, 2, 3, 4
+EVENT_EMIT, EVENT_SCATTER, EVENT_ABSORB, EVENT_ESCAPE, EVENT_CAPPED = 0, 1, 2, 3, 4
 
 TRACE_FIELDS = ("events", "absorptions", "scatters", "crossings", "escaped", "capped",
                 "final_bin", "dir_bin", "last_leaf")
@@ -487,13 +487,14 @@ class Batch:
 
     def __init__(self, grids, n_packages, seed: int = 0, mode: int = REEMIT_BW,
                  max_events: int = 0, blocks_per_sm: int = 0, refill_period: int = 0,
-                 interaction_batch: int = 0, budget_s: float = 0.0, chunk: int = 0):
+                 interaction_batch: int = 0, budget_s: float = 0.0, chunk: int = 0,
+                 threads: int = 0):
         L = load()
         self.grids = list(grids)
         arr = (C.c_void_p * len(self.grids))(*[g._h.value for g in self.grids])
         npk = np.ascontiguousarray(n_packages, dtype=np.uint64)
         o = _Opts(mode=mode, kernel=KERNEL_POOL, max_events=max_events,
-                  blocks_per_sm=blocks_per_sm, threads=0, refill_period=refill_period,
+                  blocks_per_sm=blocks_per_sm, threads=threads, refill_period=refill_period,
                   interaction_batch=interaction_batch, budget_s=budget_s, estimators=0,
                   reserved=0)
         h = C.c_void_p()

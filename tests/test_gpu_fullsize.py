@@ -12,6 +12,7 @@ import pytest
 import oracle
 from paper_1201_3588_gb300 import rt, workloads as w
 from _helpers import trace_agreement
+from _divergence import explain
 
 pytestmark = pytest.mark.gpu
 N_PACKAGES = 10 ** 8
@@ -22,18 +23,23 @@ T_MAX = 3000.0          # default top of the temperature table
 def disk_run():
     model = w.disk_model()
     with rt.Grid(model) as g:
-        g.emit_star(N_PACKAGES)
-        g.transport(N_PACKAGES, seed=1000)
-        c = g.counters()
-        cnt = g.counts()
-        T = g.temperatures()
-        sed, eps = g.sed()
-        # frozen replay of sampled packages, with the run's own temperatures
-        Tf = np.maximum(T, 3.0).astype(np.float32)
-        g.set_frozen_temperatures(Tf)
-        ids = np.random.default_rng(0).choice(N_PACKAGES, 300, replace=False).astype(np.uint64)
-        rec = g.trace(ids, seed=1000)
-    return dict(model=model, c=c, cnt=cnt, T=T, sed=sed, eps=eps, Tf=Tf, ids=ids, rec=rec)
+        yield _disk_run(model, g)
+
+
+def _disk_run(model, g):
+    g.emit_star(N_PACKAGES)
+    g.transport(N_PACKAGES, seed=1000)
+    c = g.counters()
+    cnt = g.counts()
+    T = g.temperatures()
+    sed, eps = g.sed()
+    # frozen replay of sampled packages, with the run's own temperatures
+    Tf = np.maximum(T, 3.0).astype(np.float32)
+    g.set_frozen_temperatures(Tf)
+    ids = np.random.default_rng(0).choice(N_PACKAGES, 300, replace=False).astype(np.uint64)
+    rec = g.trace(ids, seed=1000)
+    return dict(model=model, c=c, cnt=cnt, T=T, sed=sed, eps=eps, Tf=Tf, ids=ids, rec=rec,
+                grid=g)
 
 
 def test_exact_accounting_at_full_size(disk_run):
@@ -84,3 +90,8 @@ def test_frozen_histories_of_sampled_packages(disk_run):
     # long histories (~175 cells each): FP32 positions and the tabulated re-emission
     # spectra let a few per cent diverge
     assert frac >= 0.9, (frac, diff)
+    # every divergence starts at one of those: found event by event
+    cats, bad = explain(disk_run["grid"], m, disk_run["ids"][~same], disk_run["Tf"], 1000,
+                        N_PACKAGES)
+    print("first divergences by cause:", cats)
+    assert not bad, bad[:5]

@@ -11,6 +11,7 @@ import pytest
 import oracle
 from paper_1201_3588_gb300 import rt, workloads as w
 from _helpers import trace_agreement
+from _divergence import explain
 
 pytestmark = pytest.mark.gpu
 
@@ -60,8 +61,14 @@ def test_large_disk_counts_temperatures_and_histories(large):
         g.set_frozen_temperatures(Tf)
         ids = rng.choice(N, size=300, replace=False).astype(np.uint64)
         rec = g.trace(ids, seed=3)
-    orc = oracle.trace(m, ids, Tf.astype(np.float64), seed=3, n_total=N)
-    frac, _ = trace_agreement(rec, orc)
+        om = oracle.OracleModel(m)
+        orc = oracle.trace(om, ids, Tf.astype(np.float64), seed=3, n_total=N)
+        frac, same = trace_agreement(rec, orc)
+        # every divergence starts at an FP32 face decision, a rounding tie or the
+        # re-emission table: found event by event
+        cats, bad = explain(g, m, ids[~same], Tf, 3, N, om=om)
+    print("first divergences by cause:", cats)
+    assert not bad, bad[:5]
     diff = {f: int((rec[:, j] != orc[f].astype(np.int64)).sum())
             for j, f in enumerate(("events", "absorptions", "scatters", "crossings", "escaped",
                                    "capped", "final_bin", "dir_bin", "last_leaf"))}
