@@ -405,7 +405,7 @@ def surrogate_error(g, net, cells_dev, j_dev, tol, stream):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_1201_3588_gb300 import rt
+    from paper_1201_3588_gb300 import rt, shard
 
     rank, world, local = dist_env()
     model, desc = build_model(args.workload)
@@ -455,14 +455,12 @@ def run_ours(args):
         g.reset(stream)
         if ev:
             ev[0].record(stream)
-        g.transport(n, seed=1000 + k, first_id=first, stream=stream)
+        g.transport(n, seed=1000 + k, first_id=first, stream=stream,
+                    count_scale=shard.count_scale(world))
         if ev:
             ev[1].record(stream)
         if world > 1:  # sum the integer counts over ranks (package ranges are disjoint)
-            g.counts(out=cnt_dev, stream=stream)
-            with torch.cuda.stream(stream):
-                dist.all_reduce(cnt_dev)
-            g.set_counts(cnt_dev, stream=stream)
+            shard.reduce_counts(g, cnt_dev, stream=stream)
         g.temperatures(out=T_dev, stream=stream)
         g.sed(out=sed_dev, stream=stream)
         if pah:

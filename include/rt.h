@@ -96,7 +96,13 @@ typedef struct rt_run_opts {
                                point that start an interaction phase, 1..32; 0: 8 */
     double budget_s;        /* device time budget per launch in s; 0: 120 */
     int32_t estimators;     /* RT_EST_* bits: extra tallies kept during the launch */
-    int32_t reserved;
+    int32_t count_scale;    /* BW / no-correction: an absorption that finds n earlier
+                               ones in its cell indexes the temperature at
+                               count_scale * n (0 or 1: n). When W ranks share the
+                               packages and each keeps its own counts, W makes every
+                               rank's re-emission spectra telescope to the cell's
+                               total in expectation; 1 leaves them at the rank's own
+                               share, a W-fold underestimate of the cell's energy. */
 } rt_run_opts;
 
 /* Lucy (1999) path-length estimator: every cell segment a package crosses adds

@@ -485,7 +485,7 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   ALLOC(g->d_child, (size_t)d->n_blocks * 8);
   ALLOC(g->d_rho, (size_t)S * N);
   ALLOC(g->d_level, (size_t)N);
-  ALLOC(g->d_links, (size_t)N * 8);
+  ALLOC(g->d_links, (size_t)N * kRecFor(d->n_species));
   ALLOC(g->d_count, (size_t)S * N);
   ALLOC(g->d_sed, (size_t)2 * d->n_sed_dirs * B);
   ALLOC(g->d_counters, (size_t)kNumCounters);
@@ -560,6 +560,7 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   g->g.rho = g->d_rho;
   g->g.level = g->d_level;
   g->g.links = g->d_links;
+  g->g.rec = kRecFor(d->n_species);
   g->g.n_leaves = N;
   g->g.n_blocks = d->n_blocks;
   g->g.n_base = d->n_base;
@@ -703,6 +704,7 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
                           const rt_run_opts* o, DevRun* r) {
   int mode = o ? o->mode : RT_REEMIT_BW;
   if (mode < 0 || mode > 2) return RT_ERR_ARG;
+  if (o && o->count_scale < 0) return RT_ERR_ARG;
   if (mode == RT_REEMIT_FROZEN && !g->frozen_ready) return RT_ERR_STATE;
   *r = DevRun{};
   r->seed = seed;
@@ -729,6 +731,7 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
   r->mode = mode;
   r->refill_period = (o && o->refill_period > 0) ? o->refill_period : 32;
   r->interaction_batch = (o && o->interaction_batch > 0) ? o->interaction_batch : 8;
+  r->count_scale = (o && o->count_scale > 1) ? (float)o->count_scale : 1.0f;
   double budget = (o && o->budget_s > 0) ? o->budget_s : 120.0;
   r->budget_ns = (unsigned long long)(budget * 1e9);
   return RT_OK;

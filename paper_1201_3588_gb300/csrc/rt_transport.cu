@@ -350,13 +350,16 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
   const float tex = fmaxf(tmin, 0.f);
   const float dax = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
   const bool up = dax > 0.f;
-  const int* rec = g.links + (size_t)c.leaf * 8;
+  const int* rec = g.links + (size_t)c.leaf * (kS > 0 ? kRecFor(kS) : g.rec);
   const int link = __ldg(rec + 2 * ax + (up ? 1 : 0));
-  // kS: the species count when fixed at compile time (2: both densities in the
-  // record), 0 when read from the grid
+  // kS: the species count when fixed at compile time (2 or 4: the densities are in
+  // the record), 0 when read from the grid
   const Kappa* kb = kap + k.bin * (kS > 0 ? kS : g.S);
   float kx;
-  if (kS == 2 || (kS == 0 && g.S <= 2)) {
+  if (kS == 4) {
+    const float4 r4 = __ldg(reinterpret_cast<const float4*>(rec + 8));
+    kx = r4.x * kb[0].kext + r4.y * kb[1].kext + r4.z * kb[2].kext + r4.w * kb[3].kext;
+  } else if (kS == 2 || (kS == 0 && g.S <= 2)) {
     kx = __int_as_float(__ldg(rec + 6)) * kb[0].kext;
     if (kS == 2 || g.S == 2) kx += __int_as_float(__ldg(rec + 7)) * kb[1].kext;
   } else {
@@ -461,6 +464,7 @@ __device__ __forceinline__ float hg_per_sr(float g, float mu) {
 template <int kS>
 __device__ __forceinline__ float cell_rho(const DevGrid& g, int leaf, int s) {
   if (kS == 2) return __int_as_float(__ldg(g.links + (size_t)leaf * 8 + 6 + s));
+  if (kS == 4) return __int_as_float(__ldg(g.links + (size_t)leaf * 16 + 8 + s));
   return __ldg(&g.rho[(size_t)leaf * g.S + s]);
 }
 
@@ -522,10 +526,10 @@ __device__ __forceinline__ void reemit(Pkg<R>& k, const DevGrid& g, const DevTab
   float rho = cell_rho<kS>(g, leaf, s);
   float u;
   if (r.mode == 0) {
-    float e = t.eps_d0_over_V[level] / rho;
+    float e = r.count_scale * t.eps_d0_over_V[level] / rho;
     u = ((float)n + xu) * e;
   } else if (r.mode == 1) {
-    float e = t.eps_d0_over_V[level] / rho;
+    float e = r.count_scale * t.eps_d0_over_V[level] / rho;
     u = xu * fmaxf((float)n * e, t.u_tmin[s]);
   } else {
     u = xu * __ldg(&t.u_frozen[(size_t)s * g.n_leaves + leaf]);
@@ -864,9 +868,10 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
     for (int step = 0; step < K; ++step) {
       // walk phase: lanes not waiting for an interaction cross one cell
       if (alive && !pending) {
-        // the two-species form runs without the path-length tally (launched only then)
+        // the two- and four-species forms run without the path-length tally (launched
+        // only then)
         const int a = advance_linked<false, kS>(k, cell, g, kap, tl.levels,
-                                                kS == 2 ? nullptr : r.pathabs);
+                                                kS > 0 ? nullptr : r.pathabs);
         if (a == kCrossed) {
           ++tl.crossings;
         } else if (a == kEscaped) {
@@ -1137,10 +1142,17 @@ __global__ void k_build_links(DevGrid g, const int32_t* ijk, int32_t* links) {
     }
     link = node >= 0 ? (node | (l << 28)) : node;
   }
-  links[leaf * 8 + f] = link;
+  int32_t* rec = links + leaf * g.rec;
+  rec[f] = link;
   if (f == 0) {
-    links[leaf * 8 + 6] = g.S >= 1 ? __float_as_int(g.rho[leaf * g.S]) : 0;
-    links[leaf * 8 + 7] = g.S >= 2 ? __float_as_int(g.rho[leaf * g.S + 1]) : 0;
+    if (g.rec == 8) {
+      rec[6] = g.S >= 1 && g.S <= 2 ? __float_as_int(g.rho[leaf * g.S]) : 0;
+      rec[7] = g.S == 2 ? __float_as_int(g.rho[leaf * g.S + 1]) : 0;
+    } else {  // four species: words 8-11, the rest zero
+      rec[6] = rec[7] = 0;
+      for (int s = 0; s < 4; ++s) rec[8 + s] = __float_as_int(g.rho[leaf * 4 + s]);
+      for (int w = 12; w < 16; ++w) rec[w] = 0;
+    }
   }
 }
 
@@ -1218,6 +1230,9 @@ cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const De
   // variant for four species reading them as one 16-byte load measured 4 % slower)
   if (g.S == 2 && !r.pathabs)
     return launch_pool_variant<4, false, 2>(g, t, r, none, blocks_per_sm, threads, sms, s);
+  // four species: the densities come from the 64-byte face-link record
+  if (g.S == 4 && !r.pathabs)
+    return launch_pool_variant<4, false, 4>(g, t, r, none, blocks_per_sm, threads, sms, s);
   return launch_pool_variant<4, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
 }
 
@@ -1291,6 +1306,9 @@ cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* ch
                                    cudaStream_t s) {
   if (threads <= 0) threads = 256;
   if (threads % 32 != 0 || threads > 256) return cudaErrorInvalidValue;
+  if (s_fixed == 4)
+    return launch_batch_variant<4>(models, chunks, n_chunks, next_chunk, blocks_per_sm,
+                                   threads, s);
   if (s_fixed == 2)
     return launch_batch_variant<2>(models, chunks, n_chunks, next_chunk, blocks_per_sm,
                                    threads, s);

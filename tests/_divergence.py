@@ -9,7 +9,12 @@ divergence; it is explained when one of these holds there:
 * face: one side's event point lies within an optical depth TAU_TIE of a face of
   its cell (FP32 accumulates the optical depth with a relative error near 1e-7, so
   the interaction falls just before or just after the face), or the two points are
-  the same (POS_TOL) and each lies on the other's cell (a point on a shared face);
+  the same and each lies on the other's cell (a point on a shared face). Two points
+  are the same when they lie within POS_TOL, or within an optical depth TAU_POS of
+  each other (in a thin cell a tiny optical-depth difference moves the point far);
+* edge crossing: every event agrees and only the number of cells crossed differs
+  (a path through an edge or corner steps one axis at a time on the GPU and crosses
+  a cell over zero length; the oracle steps all axes at once);
 * decision tie: at the same point and cell, the uniform deviate that decides the
   event (albedo test, species, bin from a discrete spectrum) lies within REL_TIE of
   its threshold recomputed in FP64;
@@ -28,6 +33,7 @@ import oracle
 
 TAU_TIE = 1e-4
 POS_TOL = 2e-3      # base-cube units
+TAU_POS = 1e-4      # optical depth between two points taken as the same point
 REL_TIE = 1e-5
 KINDS = ("emission", "scatter", "absorption", "escape", "capped")
 
@@ -131,8 +137,10 @@ class Classifier:
             x = _deviates(self.seed, pid, 0, 0)[0]
             return ("decision tie", where) if _cum_tie(w, x) else ("unexplained", where)
         b_prev = int(oe["bin"][j - 1])
-        same_point = float(np.abs(gp - op).max()) <= POS_TOL
         leaf = int(o["leaf"])
+        kx = float(self.m.rho[:, leaf] @ self.kext[:, b_prev]) * self.d0
+        dist = float(np.abs(gp - op).max())
+        same_point = dist <= POS_TOL or dist * kx <= TAU_POS
         if same_point and int(g["leaf"]) == leaf and kg in (1, 2) and ko in (1, 2):
             w0 = _deviates(self.seed, pid, j, 0)
             w1 = _deviates(self.seed, pid, j, 1)
@@ -176,8 +184,11 @@ def explain(grid, model, ids, T_frozen, seed, n_total, om=None, max_out=1 << 16)
         oev, on = oracle.trace_events(cl.om, int(pid), cl.Tf, seed=seed, n_total=n_total,
                                       max_out=max_out)
         cat, detail = cl.classify(int(pid), gev[i], oev)
-        if cat == "same" and (gn[i] > max_out or on > max_out) and gn[i] != on:
-            cat, detail = "unexplained", f"diverges beyond the first {max_out} events"
+        if cat == "same":
+            if gn[i] > max_out or on > max_out:
+                cat, detail = "unexplained", f"diverges beyond the first {max_out} events"
+            else:  # the summaries differ in the cells crossed only
+                cat = "edge crossing"
         out[cat] = out.get(cat, 0) + 1
         if cat == "unexplained":
             bad.append((int(pid), detail))
