@@ -103,7 +103,18 @@ typedef struct rt_run_opts {
                                rank's re-emission spectra telescope to the cell's
                                total in expectation; 1 leaves them at the rank's own
                                share, a W-fold underestimate of the cell's energy. */
+    int32_t walk;           /* pool kernel: RT_WALK_* */
+    int32_t reserved;
 } rt_run_opts;
+
+/* How the pool kernel finds the next cell. LINKED reads the leaf's face-link record
+ * (one dependent read per crossing); PATH climbs the package's own stack of the
+ * blocks on its path to the common ancestor with the neighbour and descends from
+ * there (no link records; for grids of at most 4 levels). Both give the same
+ * histories. On large grids the path walk's smaller set of randomly read arrays
+ * (densities and child table) costs less address translation than the records; AUTO
+ * takes it when the records exceed 4 GB. */
+enum { RT_WALK_AUTO = 0, RT_WALK_LINKED = 1, RT_WALK_PATH = 2 };
 
 /* Lucy (1999) path-length estimator: every cell segment a package crosses adds
  * rho_s kappa_abs,s(bin) * length (an absorption optical depth) to its cell and

@@ -1,6 +1,7 @@
 """Autotuner of the packet-pool launch: for a grid (or a batch of grids), time the
 transport of a package prefix under each candidate (resident blocks per SM, threads
-per block, interaction batch, refill period) with CUDA events and keep the fastest.
+per block, interaction batch, refill period, and for a single grid the walk) with CUDA
+events and keep the fastest.
 Results are cached in a JSON file keyed by the workload class (cells to the nearest
 power of two, bins, optical-depth decade; for a batch, its models' classes)."""
 from __future__ import annotations
@@ -13,8 +14,10 @@ from typing import Dict, Optional
 
 from . import rt
 
-CANDIDATES = dict(blocks_per_sm=(0, 5), threads=(128, 256), interaction_batch=(4, 8, 12),
-                  refill_period=(16, 32))
+# the batched launch runs the linked walk; a single grid also tries the path walk
+BATCH_CANDIDATES = dict(blocks_per_sm=(0, 5), threads=(128, 256), interaction_batch=(4, 8, 12),
+                        refill_period=(16, 32))
+CANDIDATES = dict(BATCH_CANDIDATES, walk=(rt.WALK_LINKED, rt.WALK_PATH))
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1201_3588_gb300",
                              "autotune.json")
 
@@ -96,8 +99,8 @@ def tune_batch(grids, tau_vs, n_packages, fraction: float = 0.05, seed: int = 0,
     probe = [max(1, int(n * fraction)) for n in n_packages]
     s = torch.cuda.current_stream()
     best = None
-    for values in itertools.product(*CANDIDATES.values()):
-        opts = dict(zip(CANDIDATES, values))
+    for values in itertools.product(*BATCH_CANDIDATES.values()):
+        opts = dict(zip(BATCH_CANDIDATES, values))
         b = rt.Batch(grids, probe, seed=seed, **opts)
         b.run(reset=True, temperatures=False, stream=s)       # warm
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

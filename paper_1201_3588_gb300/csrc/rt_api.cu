@@ -737,12 +737,24 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
   return RT_OK;
 }
 
+// The pool walk for this grid: the path walk when asked for, or (automatic) when the
+// face-link records exceed 4 GB; grids deeper than the path walk serves keep the links.
+static bool use_path_walk(const rt_grid* g, const rt_run_opts* o) {
+  if (g->desc.max_level > 4) return false;
+  const int w = o ? o->walk : RT_WALK_AUTO;
+  if (w == RT_WALK_PATH) return true;
+  if (w == RT_WALK_LINKED) return false;
+  const double rec_bytes = 4.0 * kRecFor(g->desc.n_species) * (double)g->desc.n_leaves;
+  return rec_bytes > 4.0e9;
+}
+
 rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
                        uint64_t first_package_id, const rt_run_opts* o, void* stream) {
   if (!g) return RT_ERR_ARG;
   int kernel = o ? o->kernel : RT_KERNEL_POOL;
   int threads = (o && o->threads > 0) ? o->threads : 256;
   if (kernel < 0 || kernel > 2 || threads % 32 != 0 || threads > 256) return RT_ERR_ARG;
+  if (o && (o->walk < RT_WALK_AUTO || o->walk > RT_WALK_PATH)) return RT_ERR_ARG;
   if (o && (o->blocks_per_sm < 0 || o->blocks_per_sm > 32 || o->refill_period < 0 ||
             o->interaction_batch < 0 || o->interaction_batch > 32 ||
             (o->estimators & ~RT_EST_PATHLENGTH)))
@@ -764,7 +776,7 @@ rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
   if (kernel == RT_KERNEL_POOL) {
     RT_CUDA(cudaMemsetAsync(g->d_next, 0, sizeof(unsigned long long), s));
     RT_CUDA(launch_transport_pool(g->g, t, r, o ? o->blocks_per_sm : 0, threads, s,
-                                  g->images ? &g->peel : nullptr));
+                                  g->images ? &g->peel : nullptr, use_path_walk(g, o)));
     if (g->images) {
       RT_CUDA(launch_peel_source(g->g, t, r, g->peel, s));
       RT_CUDA(launch_peel_trace(g->g, t, r, g->peel, s));

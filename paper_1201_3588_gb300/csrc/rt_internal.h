@@ -152,7 +152,7 @@ cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* ch
                                    cudaStream_t s);
 cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
                                   int blocks_per_sm, int threads, cudaStream_t s,
-                                  const DevPeel* peel = nullptr);
+                                  const DevPeel* peel = nullptr, bool path = false);
 cudaError_t launch_peel_source(const DevGrid& g, const DevTables& t, const DevRun& r,
                                const DevPeel& peel, cudaStream_t s);
 cudaError_t launch_peel_trace(const DevGrid& g, const DevTables& t, const DevRun& r,

@@ -34,6 +34,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 namespace rt {
 namespace {
 
@@ -447,6 +449,173 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
   }
 }
 
+// ---------------------------------------------------------------- path walk
+// The walk without face links. A package keeps the ids of the child blocks on the
+// path from its base cube to its leaf (blk(l): the block holding the path's node at
+// level l). Crossing a face, it climbs to the deepest common ancestor of its leaf and
+// of the neighbouring position -- the highest bit in which their integer coordinates
+// differ gives the number of levels to climb -- and descends from there: a neighbour
+// in the same block costs one child read, in the sector the leaf's own read left in
+// L1. Its random reads go to the densities and the child table (3.5 GB for the large
+// disk's 1.7e8 cells) instead of the face-link records (5.5-11 GB), whose address
+// translation misses cost more than the extra reads on grids that large. The
+// geometry is the linked walk's, and so is every neighbour it finds: both walks give
+// the same histories.
+constexpr int kPathLevels = 4;  // the path walk serves grids of at most 4 levels
+
+struct PathCell {
+  int leaf;
+  float lo[3];
+  float sz;  // 2^-level
+  int b1, b2, b3, b4;
+  __device__ __forceinline__ int level() const { return 127 - (__float_as_int(sz) >> 23); }
+  __device__ __forceinline__ int blk(int l) const {
+    return l == 1 ? b1 : (l == 2 ? b2 : (l == 3 ? b3 : b4));
+  }
+  __device__ __forceinline__ void set_blk(int l, int b) {
+    if (l == 1) b1 = b;
+    else if (l == 2) b2 = b;
+    else if (l == 3) b3 = b;
+    else b4 = b;
+  }
+};
+
+// Enter the grid at the package's position: descent from the base cube, recording
+// the blocks on the path. 0 inside, 1 outside, -1 malformed (or deeper than the
+// walk serves).
+__device__ __forceinline__ int enter_path(const Pkg<float>& k, const DevGrid& g, PathCell& c,
+                                          unsigned& child_reads) {
+  const int n = g.n_base;
+  int I[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    I[a] = cell_index(k.p[a], k.d[a]);
+    if (I[a] < 0 || I[a] >= n) return 1;
+  }
+  int node = __ldg(&g.base[I[0] + n * (I[1] + n * I[2])]);
+  int lev = 0;
+  while (node < 0) {
+    const long long blk = -(long long)node - 1;
+    if (blk >= g.n_blocks || lev >= g.max_level || lev >= kPathLevels) return -1;
+    ++lev;
+    c.set_blk(lev, (int)blk);
+    const float sc = (float)(1 << lev);
+    int oct = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int j = cell_index(k.p[a] * sc, k.d[a]);
+      const int o = j - 2 * I[a];
+      if ((unsigned)o > 1u) return -1;
+      oct |= o << a;
+      I[a] = j;
+    }
+    node = __ldg(&g.child[blk * 8 + oct]);
+    ++child_reads;
+  }
+  if ((long long)node >= g.n_leaves) return -1;
+  c.leaf = node;
+  c.sz = __int_as_float((127 - lev) << 23);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) c.lo[a] = (float)I[a] * c.sz;
+  return 0;
+}
+
+// One cell of the path walk (kS: 2 or 4 species read as one vector from rho, 0 the
+// generic loop).
+template <int kS>
+__device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const DevGrid& g,
+                                            const Kappa* kap, unsigned& child_reads) {
+  const float sz = c.sz;
+  const float lo0 = c.lo[0], lo1 = c.lo[1], lo2 = c.lo[2];
+  const float hi0 = lo0 + sz, hi1 = lo1 + sz, hi2 = lo2 + sz;
+  const float d0 = k.d[0], d1 = k.d[1], d2 = k.d[2];
+  const float t0 = ((k.inv[0] > 0.f ? hi0 : lo0) - k.p[0]) * k.inv[0];
+  const float t1 = ((k.inv[1] > 0.f ? hi1 : lo1) - k.p[1]) * k.inv[1];
+  const float t2 = ((k.inv[2] > 0.f ? hi2 : lo2) - k.p[2]) * k.inv[2];
+  const float tmin = fminf(fminf(t0, t1), t2);
+  const int ax = t0 == tmin ? 0 : (t1 == tmin ? 1 : 2);
+  const float tex = fmaxf(tmin, 0.f);
+  const float dax = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
+  const bool up = dax > 0.f;
+  const Kappa* kb = kap + k.bin * (kS > 0 ? kS : g.S);
+  float kx;
+  if (kS == 4) {
+    const float4 r4 = __ldg(reinterpret_cast<const float4*>(g.rho) + c.leaf);
+    kx = r4.x * kb[0].kext + r4.y * kb[1].kext + r4.z * kb[2].kext + r4.w * kb[3].kext;
+  } else if (kS == 2) {
+    const float2 r2 = __ldg(reinterpret_cast<const float2*>(g.rho) + c.leaf);
+    kx = r2.x * kb[0].kext + r2.y * kb[1].kext;
+  } else {
+    const float* rho = g.rho + (size_t)c.leaf * g.S;
+    kx = 0.f;
+    for (int s = 0; s < g.S; ++s) kx += __ldg(&rho[s]) * kb[s].kext;
+  }
+  const float dtau = kx * tex;
+  if (kx > 0.f && dtau > k.tau) {
+    const float sd = k.tau / kx;
+    k.p[0] = fminf(hi0, fmaxf(lo0, k.p[0] + sd * d0));
+    k.p[1] = fminf(hi1, fmaxf(lo1, k.p[1] + sd * d1));
+    k.p[2] = fminf(hi2, fmaxf(lo2, k.p[2] + sd * d2));
+    return kInteract;
+  }
+  k.tau -= dtau;
+  const float f0 = d0 > 0.f ? hi0 : lo0, f1 = d1 > 0.f ? hi1 : lo1, f2 = d2 > 0.f ? hi2 : lo2;
+  k.p[0] = ax == 0 ? f0 : fminf(hi0, fmaxf(lo0, k.p[0] + tex * d0));
+  k.p[1] = ax == 1 ? f1 : fminf(hi1, fmaxf(lo1, k.p[1] + tex * d1));
+  k.p[2] = ax == 2 ? f2 : fminf(hi2, fmaxf(lo2, k.p[2] + tex * d2));
+  // integer coordinates of the leaf and of the same-size neighbour across face ax
+  const int L = c.level();
+  const float isz = __int_as_float((127 + L) << 23);  // 2^L
+  int J0 = (int)(lo0 * isz), J1 = (int)(lo1 * isz), J2 = (int)(lo2 * isz);
+  const int Iax = ax == 0 ? J0 : (ax == 1 ? J1 : J2);
+  const int Jax = up ? Iax + 1 : Iax - 1;
+  if (Jax < 0 || Jax >= (g.n_base << L)) return kEscaped;
+  if (ax == 0) J0 = Jax;
+  else if (ax == 1) J1 = Jax;
+  else J2 = Jax;
+  const int u = 32 - __clz(Iax ^ Jax);  // levels up to the common ancestor
+  int lev, node;
+  if (u > L) {  // another base cube
+    lev = 0;
+    const int n = g.n_base;
+    node = __ldg(&g.base[(J0 >> L) + n * ((J1 >> L) + n * (J2 >> L))]);
+  } else {      // the common ancestor's block holds the first node off the path
+    lev = L - u + 1;
+    const int sh = L - lev;
+    const int oct = ((J0 >> sh) & 1) | (((J1 >> sh) & 1) << 1) | (((J2 >> sh) & 1) << 2);
+    node = __ldg(&g.child[(long long)c.blk(lev) * 8 + oct]);
+    ++child_reads;
+  }
+  int K0 = J0 >> (L - lev), K1 = J1 >> (L - lev), K2 = J2 >> (L - lev);
+  while (node < 0) {
+    const long long blk = -(long long)node - 1;
+    if (blk >= g.n_blocks || lev >= g.max_level || lev >= kPathLevels) return kError;
+    ++lev;
+    c.set_blk(lev, (int)blk);
+    if (lev <= L) {
+      const int sh = L - lev;
+      K0 = J0 >> sh;
+      K1 = J1 >> sh;
+      K2 = J2 >> sh;
+    } else {  // a finer neighbour: the child holding the crossing point
+      const float sc = (float)(1 << lev);
+      K0 = min(max(cell_index(k.p[0] * sc, d0), 2 * K0), 2 * K0 + 1);
+      K1 = min(max(cell_index(k.p[1] * sc, d1), 2 * K1), 2 * K1 + 1);
+      K2 = min(max(cell_index(k.p[2] * sc, d2), 2 * K2), 2 * K2 + 1);
+    }
+    const int oct = (K0 & 1) | ((K1 & 1) << 1) | ((K2 & 1) << 2);
+    node = __ldg(&g.child[blk * 8 + oct]);
+    ++child_reads;
+  }
+  if ((long long)node >= g.n_leaves) return kError;
+  c.leaf = node;
+  c.sz = __int_as_float((127 - lev) << 23);
+  c.lo[0] = (float)K0 * c.sz;
+  c.lo[1] = (float)K1 * c.sz;
+  c.lo[2] = (float)K2 * c.sz;
+  return kCrossed;
+}
+
 constexpr float kInv4Pi = 0.0795774715459476679f;  // 1 / (4 pi)
 
 // Henyey-Greenstein phase function per steradian at cos(angle) = mu.
@@ -459,12 +628,14 @@ __device__ __forceinline__ float hg_per_sr(float g, float mu) {
 // absorbing species. Returns the species (>= 0) for an absorption, -1 for a scatter.
 // peel_o / peel_w (peel-off): for a scattering, *peel_w receives the phase function
 // per steradian toward the unit vector peel_o, at the direction before the turn.
-// kS: the species count when fixed at compile time (2: the densities come from the
-// cell's face-link record, which the walk has just read), 0 when read from the grid.
+// kS: the species count when fixed at compile time (2 or 4: the densities come from
+// the cell's face-link record, which the walk has just read; -2 or -4: from the
+// density array, which the path walk has just read), 0 when read from the grid.
 template <int kS>
 __device__ __forceinline__ float cell_rho(const DevGrid& g, int leaf, int s) {
   if (kS == 2) return __int_as_float(__ldg(g.links + (size_t)leaf * 8 + 6 + s));
   if (kS == 4) return __int_as_float(__ldg(g.links + (size_t)leaf * 16 + 8 + s));
+  if (kS < 0) return __ldg(&g.rho[(size_t)leaf * (-kS) + s]);
   return __ldg(&g.rho[(size_t)leaf * g.S + s]);
 }
 
@@ -475,7 +646,7 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
                                         float* peel_w = nullptr) {
   uint4 w0 = draw(r.seed, k.id, k.event, 0u);
   w1 = draw(r.seed, k.id, k.event, 1u);
-  const int S = kS > 0 ? kS : g.S;
+  const int S = kS > 0 ? kS : (kS < 0 ? -kS : g.S);
   const Kappa* kb = kap + k.bin * S;
   float ksca = 0.f, kext = 0.f, kabs = 0.f;
   for (int s = 0; s < S; ++s) {
@@ -809,7 +980,7 @@ struct RangeIds {
 // kPeel: scatterings and re-emissions at image bins are recorded (position, w,
 // bin) in the peel-off event buffer, one slot range per warp and phase; point-source
 // emissions are counted per bin in s_nemit.
-template <bool kPeel, class Ids, int kS = 0>
+template <bool kPeel, class Ids, int kS = 0, bool kPath = false>
 __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, const DevRun& r,
                                           const Kappa* kap, const float* star_cdf,
                                           unsigned long long* sed, unsigned long long n_end,
@@ -823,7 +994,12 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
   k.id = 0;
   bool alive = false;
   bool pending = false;  // reached an interaction point, waiting for the batch
-  Cell cell{0, {0.f, 0.f, 0.f}, 1.f};
+  // kPath: the path walk (densities from the density array, kI = -kS for the
+  // interaction); otherwise the linked walk
+  using CellT = typename std::conditional<kPath, PathCell, Cell>::type;
+  constexpr int kI = kPath ? -kS : kS;
+  CellT cell{};
+  cell.sz = 1.f;
   const int K = r.refill_period > 0 ? r.refill_period : 32;
   const int batch = r.interaction_batch > 0 ? r.interaction_batch : 8;
 
@@ -840,7 +1016,11 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
           if constexpr (kPeel) {
             if (r.source_kind != 1) atomicAdd(&s_nemit[k.bin], 1ull);
           }
-          const int rc = enter(k, g, cell, tl.levels);
+          int rc;
+          if constexpr (kPath)
+            rc = enter_path(k, g, cell, tl.levels);
+          else
+            rc = enter(k, g, cell, tl.levels);
           if (rc == 0) {
             alive = true;
           } else if (rc == 1) {  // source outside the grid, moving away
@@ -868,10 +1048,14 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
     for (int step = 0; step < K; ++step) {
       // walk phase: lanes not waiting for an interaction cross one cell
       if (alive && !pending) {
-        // the two- and four-species forms run without the path-length tally (launched
-        // only then)
-        const int a = advance_linked<false, kS>(k, cell, g, kap, tl.levels,
-                                                kS > 0 ? nullptr : r.pathabs);
+        // the two- and four-species forms and the path walk run without the
+        // path-length tally (launched only then)
+        int a;
+        if constexpr (kPath)
+          a = advance_path<kS>(k, cell, g, kap, tl.levels);
+        else
+          a = advance_linked<false, kS>(k, cell, g, kap, tl.levels,
+                                        kS > 0 ? nullptr : r.pathabs);
         if (a == kCrossed) {
           ++tl.crossings;
         } else if (a == kEscaped) {
@@ -905,7 +1089,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
           ++tl.capped;
           alive = false;
         } else {
-          sp = interact<float, kS>(k, g, kap, cell.leaf, r, w1, kPeel ? pe->o : nullptr,
+          sp = interact<float, kI>(k, g, kap, cell.leaf, r, w1, kPeel ? pe->o : nullptr,
                                    kPeel ? &wv : nullptr);
           if (sp < 0) {
             ++tl.scatters;
@@ -928,7 +1112,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
         if (t.pah_of[sp] >= 0)
           pah_absorb<float>(k, g, t, r, t.pah_of[sp], cell.leaf, w1);
         else
-          reemit<float, kS>(k, g, t, r, sp, cell.leaf, cell.level(), old + __popc(peers & lt_mask),
+          reemit<float, kI>(k, g, t, r, sp, cell.leaf, cell.level(), old + __popc(peers & lt_mask),
                         w1, tl);
         ++tl.absorptions;
       }
@@ -959,7 +1143,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
 // Persistent packet pool over one model: all warps draw package indices from one
 // global counter; the opacity table, the stellar CDF and (when it fits) the
 // escaped-spectrum histogram live in shared memory.
-template <int kMinBlocks, bool kPeel, int kS = 0>
+template <int kMinBlocks, bool kPeel, int kS = 0, bool kPath = false>
 __global__ void __launch_bounds__(256, kMinBlocks)
     k_transport_pool(DevGrid g, DevTables t, DevRun r, const __grid_constant__ DevPeel pe) {
   extern __shared__ unsigned long long smem_u64[];
@@ -983,7 +1167,8 @@ __global__ void __launch_bounds__(256, kMinBlocks)
   __syncthreads();
   Tally tl = {};
   GlobalIds ids{r.next};
-  pool_warp<kPeel, GlobalIds, kS>(g, t, r, s_kap, s_cdf, s_sed, r.n_packages, ids, tl, global_ns(), &pe,
+  pool_warp<kPeel, GlobalIds, kS, kPath>(g, t, r, s_kap, s_cdf, s_sed, r.n_packages, ids, tl,
+                                         global_ns(), &pe,
                    s_nemit);
   flush_tally(tl, r.counters);
   if (sed_local || kPeel) __syncthreads();
@@ -1181,7 +1366,7 @@ static size_t sed_smem(const DevGrid& g) {
 
 static size_t peel_smem(const DevGrid& g) { return 16 + sizeof(unsigned long long) * g.B; }
 
-template <int kMinBlocks, bool kPeel, int kS = 0>
+template <int kMinBlocks, bool kPeel, int kS = 0, bool kPath = false>
 static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, const DevRun& r,
                                        const DevPeel& pe, int blocks_per_sm, int threads,
                                        int sms, cudaStream_t s) {
@@ -1191,17 +1376,18 @@ static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, con
   size_t sm = table_smem(g) + extra + (rr.sed_in_smem ? sed_smem(g) : 0);
   cudaError_t e;
   if (sm > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_transport_pool<kMinBlocks, kPeel, kS>,
+    e = cudaFuncSetAttribute(k_transport_pool<kMinBlocks, kPeel, kS, kPath>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport_pool<kMinBlocks, kPeel, kS>,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ,
+                                                    k_transport_pool<kMinBlocks, kPeel, kS, kPath>,
                                                     threads, sm);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   int bps = blocks_per_sm > 0 ? (blocks_per_sm < occ ? blocks_per_sm : occ) : occ;
-  k_transport_pool<kMinBlocks, kPeel, kS><<<sms * bps, threads, sm, s>>>(g, t, rr, pe);
+  k_transport_pool<kMinBlocks, kPeel, kS, kPath><<<sms * bps, threads, sm, s>>>(g, t, rr, pe);
   return cudaGetLastError();
 }
 
@@ -1212,7 +1398,7 @@ static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, con
 // of spills). With peel-off images the 4-block variants are used.
 cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const DevRun& r,
                                   int blocks_per_sm, int threads, cudaStream_t s,
-                                  const DevPeel* peel) {
+                                  const DevPeel* peel, bool path) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -1222,6 +1408,14 @@ cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const De
     return launch_pool_variant<4, true, 2>(g, t, r, *peel, blocks_per_sm, threads, sms, s);
   if (peel) return launch_pool_variant<4, true>(g, t, r, *peel, blocks_per_sm, threads, sms, s);
   const DevPeel none{};
+  // the path walk (no face links; grids of at most kPathLevels levels)
+  if (path && !r.pathabs && g.max_level <= kPathLevels) {
+    if (g.S == 4)
+      return launch_pool_variant<4, false, 4, true>(g, t, r, none, blocks_per_sm, threads, sms, s);
+    if (g.S == 2)
+      return launch_pool_variant<4, false, 2, true>(g, t, r, none, blocks_per_sm, threads, sms, s);
+    return launch_pool_variant<4, false, 0, true>(g, t, r, none, blocks_per_sm, threads, sms, s);
+  }
   if (threads == 256 && blocks_per_sm == 6)
     return launch_pool_variant<6, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
   if (threads == 256 && blocks_per_sm == 5)

@@ -19,6 +19,7 @@ REEMIT_BW, REEMIT_NOCORR, REEMIT_FROZEN = 0, 1, 2
 EST_PATHLENGTH = 1
 PAH_EXACT, PAH_SURROGATE, PAH_AUTO = 0, 1, 2
 KERNEL_POOL, KERNEL_PLAIN_F32, KERNEL_PLAIN_F64 = 0, 1, 2
+WALK_AUTO, WALK_LINKED, WALK_PATH = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA runtime error",
           4: "kernel stopped at its time budget", 5: "call out of order",
@@ -52,7 +53,7 @@ class _Opts(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("threads", C.c_int32),
                 ("refill_period", C.c_int32), ("interaction_batch", C.c_int32),
                 ("budget_s", C.c_double), ("estimators", C.c_int32),
-                ("count_scale", C.c_int32)]
+                ("count_scale", C.c_int32), ("walk", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _Counters(C.Structure):
@@ -263,11 +264,11 @@ class Grid:
                   mode: int = REEMIT_BW, kernel: int = KERNEL_POOL, max_events: int = 0,
                   blocks_per_sm: int = 0, threads: int = 0, refill_period: int = 0,
                   interaction_batch: int = 0, budget_s: float = 0.0, estimators: int = 0,
-                  count_scale: int = 0, stream=None):
+                  count_scale: int = 0, walk: int = WALK_AUTO, stream=None):
         o = _Opts(mode=mode, kernel=kernel, max_events=max_events, blocks_per_sm=blocks_per_sm,
                   threads=threads, refill_period=refill_period,
                   interaction_batch=interaction_batch, budget_s=budget_s,
-                  estimators=estimators, count_scale=count_scale)
+                  estimators=estimators, count_scale=count_scale, walk=walk, reserved=0)
         _check(load().rt_transport(self._h, int(n_packages), int(seed), int(first_id),
                                    C.byref(o), _stream(stream)), "rt_transport")
 
@@ -496,7 +497,7 @@ class Batch:
         o = _Opts(mode=mode, kernel=KERNEL_POOL, max_events=max_events,
                   blocks_per_sm=blocks_per_sm, threads=threads, refill_period=refill_period,
                   interaction_batch=interaction_batch, budget_s=budget_s, estimators=0,
-                  count_scale=0)
+                  count_scale=0, walk=0, reserved=0)
         h = C.c_void_p()
         _check(L.rt_batch_create(C.cast(arr, C.c_void_p), len(self.grids), npk.ctypes.data,
                                  int(seed), C.byref(o), int(chunk), C.byref(h)),

@@ -548,6 +548,17 @@ def large_disk_model() -> Model:
     return m
 
 
+def disk4_model(n_base: int = 128, max_level: int = 2, n_bins: int = 400) -> Model:
+    """The PAH disk's geometry and four species' opacities, all four treated as
+    ordinary dust (no PAH tallies): the four-species walk with about 2.5 GB on the
+    device at 128^3 base cubes and two levels, for profiling the transport."""
+    m = disk_pah_model(n_base=n_base, max_level=max_level, n_bins=n_bins)
+    m.species = [dataclasses.replace(sp, is_pah=0, n_carbon=0, n_hydrogen=0, mol_mass=0.0,
+                                     modes=()) for sp in m.species]
+    m.name = "disk4"
+    return m
+
+
 def uniform_box_model(n_base: int, n_bins: int, tau_half: float, species: List[Species],
                       half_size_cm: float = AU, star: Optional[Star] = None,
                       max_level: int = 0, refine=None, n_sed_dirs: int = 1) -> Model:

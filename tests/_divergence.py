@@ -6,12 +6,18 @@ the oracle (FP64, exact re-emission spectra) agree event by event until a decisi
 falls the other way. The first event whose (kind, cell, bin) differ is the
 divergence; it is explained when one of these holds there:
 
-* face: one side's event point lies within an optical depth TAU_TIE of a face of
-  its cell (FP32 accumulates the optical depth with a relative error near 1e-7, so
-  the interaction falls just before or just after the face), or the two points are
+* face: one side's event point lies within an optical depth tau_tol of a face of
+  its cell (FP32 accumulates the optical depth and the position as the package
+  crosses cells, so the interaction falls just before or just after the face), or
+  the two points are
   the same and each lies on the other's cell (a point on a shared face). Two points
-  are the same when they lie within POS_TOL, or within an optical depth TAU_POS of
-  each other (in a thin cell a tiny optical-depth difference moves the point far);
+  are the same when they lie within POS_TOL, or within an optical depth tau_tol of
+  each other (in a thin cell a tiny optical-depth difference moves the point far).
+  tau_tol = TAU_TIE + n eps32 (TAU_MAX + kx |p|) bounds the FP32 error linearly over
+  the n cells crossed since the previous event (estimated as the distance flown over
+  the cell's edge, plus one): per cell one rounding of the remaining optical depth
+  (at most TAU_MAX) and of the position (|p| base-cube units, extinction kx per
+  unit);
 * edge crossing: every event agrees and only the number of cells crossed differs
   (a path through an edge or corner steps one axis at a time on the GPU and crosses
   a cell over zero length; the oracle steps all axes at once);
@@ -33,8 +39,9 @@ import oracle
 
 TAU_TIE = 1e-4
 POS_TOL = 2e-3      # base-cube units
-TAU_POS = 1e-4      # optical depth between two points taken as the same point
 REL_TIE = 1e-5
+EPS32 = 2.0 ** -24
+TAU_MAX = 16.7      # the largest optical depth a package draws (-ln of the smallest deviate)
 KINDS = ("emission", "scatter", "absorption", "escape", "capped")
 
 
@@ -94,11 +101,17 @@ class Classifier:
         self.pah_of = {s: p for p, s in enumerate(self.om.pah_species)}
 
     # -- geometry
+    def _kx(self, leaf, b):
+        return float(self.m.rho[:, leaf] @ self.kext[:, b]) * self.d0
+
     def _tau_to_face(self, leaf, p, b):
         lo, hi = self.lo[leaf], self.hi[leaf]
         d = max(0.0, float(np.min(np.minimum(p - lo, hi - p))))
-        kx = float(self.m.rho[:, leaf] @ self.kext[:, b]) * self.d0
-        return kx * d
+        return self._kx(leaf, b) * d
+
+    def _tau_tol(self, leaf, p, p_prev, b):
+        n = float(np.linalg.norm(p - p_prev)) / float(self.hi[leaf][0] - self.lo[leaf][0]) + 1.0
+        return TAU_TIE + n * EPS32 * (TAU_MAX + self._kx(leaf, b) * float(np.abs(p).max()))
 
     def _dist_to_box(self, leaf, p):
         q = np.clip(p, self.lo[leaf], self.hi[leaf])
@@ -138,9 +151,10 @@ class Classifier:
             return ("decision tie", where) if _cum_tie(w, x) else ("unexplained", where)
         b_prev = int(oe["bin"][j - 1])
         leaf = int(o["leaf"])
-        kx = float(self.m.rho[:, leaf] @ self.kext[:, b_prev]) * self.d0
+        prev = np.asarray(oe["pos"][j - 1], np.float64)
+        tol = self._tau_tol(leaf, op, prev, b_prev)
         dist = float(np.abs(gp - op).max())
-        same_point = dist <= POS_TOL or dist * kx <= TAU_POS
+        same_point = dist <= POS_TOL or dist * self._kx(leaf, b_prev) <= tol
         if same_point and int(g["leaf"]) == leaf and kg in (1, 2) and ko in (1, 2):
             w0 = _deviates(self.seed, pid, j, 0)
             w1 = _deviates(self.seed, pid, j, 1)
@@ -165,7 +179,8 @@ class Classifier:
                 return ("re-emission table", detail) if ok else ("unexplained", detail)
         # the walk: an interaction point at a face of its cell, or a point on a shared face
         for k, p, lf in ((kg, gp, int(g["leaf"])), (ko, op, int(o["leaf"]))):
-            if k in (1, 2) and self._tau_to_face(lf, p, b_prev) <= TAU_TIE:
+            if k in (1, 2) and self._tau_to_face(lf, p, b_prev) <= \
+                    self._tau_tol(lf, p, prev, b_prev):
                 return "face", where
         if same_point and self._dist_to_box(leaf, gp) <= POS_TOL and \
                 self._dist_to_box(int(g["leaf"]), op) <= POS_TOL:

@@ -78,7 +78,8 @@ def test_autotuner_picks_and_caches(tmp_path, models):
         g.emit_star(10 ** 6)
         path = str(tmp_path / "tune.json")
         opts = autotune.tune(g, m.recipe["tau_v"], n_probe=200_000, cache=path)
-        assert set(opts) == {"blocks_per_sm", "threads", "interaction_batch", "refill_period"}
+        assert set(opts) == {"blocks_per_sm", "threads", "interaction_batch", "refill_period",
+                             "walk"}
         db = json.load(open(path))
         assert len(db) == 1 and list(db.values())[0]["opts"] == opts
         assert autotune.tune(g, m.recipe["tau_v"], cache=path) == opts
@@ -196,7 +197,7 @@ def test_batch_autotuner_covers_the_batch(tmp_path, models):
     path = str(tmp_path / "tune.json")
     taus = [m.recipe["tau_v"] for m, _ in models]
     opts = autotune.tune_batch(grids, taus, npk, fraction=0.05, cache=path)
-    assert set(opts) == set(autotune.CANDIDATES) and opts["threads"] in (128, 256)
+    assert set(opts) == set(autotune.BATCH_CANDIDATES) and opts["threads"] in (128, 256)
     assert autotune.tune_batch(grids, taus, npk, cache=path) == opts
     b = rt.Batch(grids, npk, seed=1, **opts)
     b.run(reset=True, temperatures=False)
