@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--plain-packages", type=float, default=1e7)
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--walk", choices=["auto", "linked", "path"], default="auto",
+                   help="the pool kernel's walk (auto: the path walk when the face-link "
+                        "records exceed 4 GB)")
     p.add_argument("--no-pah", action="store_true",
                    help="leave the PAH emission out of the step (the transport still "
                         "tallies PAH absorptions); for profiling the transport alone")
@@ -74,6 +77,7 @@ def parse():
 # packages per step: config 5 is timed on a prefix of its 1e10 packages, sized so
 # that 20 timed steps take under a minute
 DEFAULT_PACKAGES = {"large_disk": 2.5e8}
+WALKS = {"auto": 0, "linked": 1, "path": 2}
 FULL_PACKAGES = {"large_disk": 1e10, "disk": 1e8, "disk_pah": 1e8, "disk_images": 1e8,
                  "sphere": 1e5}
 
@@ -333,6 +337,14 @@ def walk_bytes(c, S):
             + c.get("peel_crossings", 0) * (4 + 4 * S) + 16 * c.get("peel_events", 0))
 
 
+def walk_label(choice, N, S, L):
+    """The pool walk the library runs for this grid (the same rule as rt_transport)."""
+    if choice == "auto":
+        choice = "path" if L <= 4 and (S == 4 or 32 * N > 4e9) else "linked"
+        return f"{choice} (automatic)"
+    return choice
+
+
 def has_pah(model):
     return any(sp.is_pah for sp in model.species)
 
@@ -382,10 +394,12 @@ def surrogate_error(g, net, cells_dev, j_dev, tol, stream):
     j_ex = torch.empty_like(j_dev)
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("pah_exact_all")  # lets a profiler select this pass
     a.record(stream)
     c_ex, r_ex, _ = g.pah_emission_active(mode=rt.PAH_EXACT, cells=cells_ex, out=j_ex,
                                           stream=stream)
     e.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t_exact = a.elapsed_time(e)
     a.record(stream)
@@ -464,7 +478,7 @@ def run_ours(args):
         if ev:
             ev[0].record(stream)
         g.transport(n, seed=1000 + k, first_id=first, stream=stream,
-                    count_scale=shard.count_scale(world))
+                    count_scale=shard.count_scale(world), walk=WALKS[args.walk])
         if ev:
             ev[1].record(stream)
         if world > 1:  # sum the integer counts over ranks (package ranges are disjoint)
@@ -576,6 +590,7 @@ def run_ours(args):
                        "packages_full_workload": FULL_PACKAGES.get(args.workload),
                        "leaves": N, "bins": B, "species": S, "levels": L,
                        "reemission": "bjorkman-wood",
+                       "walk": walk_label(args.walk, N, S, L),
                        "form": "FP32 packet-pool transport" +
                                (" + BF16 tcgen05 PAH surrogate with exact fallback"
                                 if pah else ""),

@@ -108,12 +108,13 @@ typedef struct rt_run_opts {
 } rt_run_opts;
 
 /* How the pool kernel finds the next cell. LINKED reads the leaf's face-link record
- * (one dependent read per crossing); PATH climbs the package's own stack of the
- * blocks on its path to the common ancestor with the neighbour and descends from
- * there (no link records; for grids of at most 4 levels). Both give the same
- * histories. On large grids the path walk's smaller set of randomly read arrays
- * (densities and child table) costs less address translation than the records; AUTO
- * takes it when the records exceed 4 GB. */
+ * (one dependent read per crossing; the record also holds the densities of up to two
+ * species); PATH climbs the package's own stack of the blocks on its path to the
+ * common ancestor with the neighbour and descends from there (no link records; for
+ * grids of at most 4 levels). Both give the same histories. AUTO takes the path walk
+ * for four species, and for any species count when the records exceed 4 GB: its
+ * randomly read arrays (densities and child table) are smaller, which costs less
+ * address translation on large grids. */
 enum { RT_WALK_AUTO = 0, RT_WALK_LINKED = 1, RT_WALK_PATH = 2 };
 
 /* Lucy (1999) path-length estimator: every cell segment a package crosses adds

@@ -38,18 +38,14 @@ struct DevGrid {
   const int32_t* child;    // [n_blocks*8]
   const float* rho;        // [n_leaves][S]: density times the base-cube edge, g cm^-2
   const int8_t* level;     // [n_leaves] refinement level of every leaf
-  const int32_t* links;    // [n_leaves][rec] face links and densities (see kRecFor)
+  const int32_t* links;    // [n_leaves][8] face links (+ densities when S <= 2)
   long long n_leaves, n_blocks;
   int n_base, max_level, S, B, n_dir, n_T;
-  int rec;                 // int32 words per face-link record: 8, or 16 for four species
 };
 
-// Face-link record of a leaf. 8 words (32 bytes): links of faces -x,+x,-y,+y,-z,+z,
-// then the densities of species 0 and 1 (S <= 2; zero otherwise). With four species
-// 16 words (64 bytes, one aligned DRAM access): the six links, two zero words, the
-// four densities as one 16-byte vector at words 8-11, four zero words. The walk then
-// reads everything a crossing needs from one record.
-__host__ __device__ constexpr int kRecFor(int S) { return S == 4 ? 16 : 8; }
+// Face-link record of a leaf, 8 words (32 bytes): links of faces -x,+x,-y,+y,-z,+z,
+// then the densities of species 0 and 1 when S <= 2 (zero otherwise).
+constexpr int kRec = 8;
 
 // Per-bin opacity record for one species, kept in shared memory during transport.
 struct Kappa {
@@ -144,7 +140,7 @@ struct BatchChunk {
 };
 
 // Kernel launchers (rt_transport.cu, rt_tables.cu).
-// s_fixed: the species count all models share (2 and 4 have walks compiled for them,
+// s_fixed: the species count all models share (2 has a walk compiled for it,
 // without the path-length tally), 0 otherwise
 cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* chunks,
                                    long long n_chunks, unsigned long long* next_chunk,

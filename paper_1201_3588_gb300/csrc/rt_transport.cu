@@ -352,16 +352,13 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
   const float tex = fmaxf(tmin, 0.f);
   const float dax = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
   const bool up = dax > 0.f;
-  const int* rec = g.links + (size_t)c.leaf * (kS > 0 ? kRecFor(kS) : g.rec);
+  const int* rec = g.links + (size_t)c.leaf * kRec;
   const int link = __ldg(rec + 2 * ax + (up ? 1 : 0));
-  // kS: the species count when fixed at compile time (2 or 4: the densities are in
-  // the record), 0 when read from the grid
+  // kS: the species count when fixed at compile time (2: both densities in the
+  // record), 0 when read from the grid
   const Kappa* kb = kap + k.bin * (kS > 0 ? kS : g.S);
   float kx;
-  if (kS == 4) {
-    const float4 r4 = __ldg(reinterpret_cast<const float4*>(rec + 8));
-    kx = r4.x * kb[0].kext + r4.y * kb[1].kext + r4.z * kb[2].kext + r4.w * kb[3].kext;
-  } else if (kS == 2 || (kS == 0 && g.S <= 2)) {
+  if (kS == 2 || (kS == 0 && g.S <= 2)) {
     kx = __int_as_float(__ldg(rec + 6)) * kb[0].kext;
     if (kS == 2 || g.S == 2) kx += __int_as_float(__ldg(rec + 7)) * kb[1].kext;
   } else {
@@ -457,8 +454,8 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
 // differ gives the number of levels to climb -- and descends from there: a neighbour
 // in the same block costs one child read, in the sector the leaf's own read left in
 // L1. Its random reads go to the densities and the child table (3.5 GB for the large
-// disk's 1.7e8 cells) instead of the face-link records (5.5-11 GB), whose address
-// translation misses cost more than the extra reads on grids that large. The
+// disk's 1.7e8 cells) instead of the face-link records and densities (8.3 GB), whose
+// address translation misses cost more than the extra reads on grids that large. The
 // geometry is the linked walk's, and so is every neighbour it finds: both walks give
 // the same histories.
 constexpr int kPathLevels = 4;  // the path walk serves grids of at most 4 levels
@@ -628,13 +625,12 @@ __device__ __forceinline__ float hg_per_sr(float g, float mu) {
 // absorbing species. Returns the species (>= 0) for an absorption, -1 for a scatter.
 // peel_o / peel_w (peel-off): for a scattering, *peel_w receives the phase function
 // per steradian toward the unit vector peel_o, at the direction before the turn.
-// kS: the species count when fixed at compile time (2 or 4: the densities come from
-// the cell's face-link record, which the walk has just read; -2 or -4: from the
+// kS: the species count when fixed at compile time (2: the densities come from the
+// cell's face-link record, which the linked walk has just read; -2 or -4: from the
 // density array, which the path walk has just read), 0 when read from the grid.
 template <int kS>
 __device__ __forceinline__ float cell_rho(const DevGrid& g, int leaf, int s) {
-  if (kS == 2) return __int_as_float(__ldg(g.links + (size_t)leaf * 8 + 6 + s));
-  if (kS == 4) return __int_as_float(__ldg(g.links + (size_t)leaf * 16 + 8 + s));
+  if (kS == 2) return __int_as_float(__ldg(g.links + (size_t)leaf * kRec + 6 + s));
   if (kS < 0) return __ldg(&g.rho[(size_t)leaf * (-kS) + s]);
   return __ldg(&g.rho[(size_t)leaf * g.S + s]);
 }
@@ -1048,8 +1044,8 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
     for (int step = 0; step < K; ++step) {
       // walk phase: lanes not waiting for an interaction cross one cell
       if (alive && !pending) {
-        // the two- and four-species forms and the path walk run without the
-        // path-length tally (launched only then)
+        // the two-species form and the path walk run without the path-length tally
+        // (launched only then)
         int a;
         if constexpr (kPath)
           a = advance_path<kS>(k, cell, g, kap, tl.levels);
@@ -1327,17 +1323,11 @@ __global__ void k_build_links(DevGrid g, const int32_t* ijk, int32_t* links) {
     }
     link = node >= 0 ? (node | (l << 28)) : node;
   }
-  int32_t* rec = links + leaf * g.rec;
+  int32_t* rec = links + leaf * kRec;
   rec[f] = link;
   if (f == 0) {
-    if (g.rec == 8) {
-      rec[6] = g.S >= 1 && g.S <= 2 ? __float_as_int(g.rho[leaf * g.S]) : 0;
-      rec[7] = g.S == 2 ? __float_as_int(g.rho[leaf * g.S + 1]) : 0;
-    } else {  // four species: words 8-11, the rest zero
-      rec[6] = rec[7] = 0;
-      for (int s = 0; s < 4; ++s) rec[8 + s] = __float_as_int(g.rho[leaf * 4 + s]);
-      for (int w = 12; w < 16; ++w) rec[w] = 0;
-    }
+    rec[6] = g.S >= 1 && g.S <= 2 ? __float_as_int(g.rho[leaf * g.S]) : 0;
+    rec[7] = g.S == 2 ? __float_as_int(g.rho[leaf * g.S + 1]) : 0;
   }
 }
 
@@ -1424,9 +1414,6 @@ cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const De
   // variant for four species reading them as one 16-byte load measured 4 % slower)
   if (g.S == 2 && !r.pathabs)
     return launch_pool_variant<4, false, 2>(g, t, r, none, blocks_per_sm, threads, sms, s);
-  // four species: the densities come from the 64-byte face-link record
-  if (g.S == 4 && !r.pathabs)
-    return launch_pool_variant<4, false, 4>(g, t, r, none, blocks_per_sm, threads, sms, s);
   return launch_pool_variant<4, false>(g, t, r, none, blocks_per_sm, threads, sms, s);
 }
 
@@ -1500,9 +1487,6 @@ cudaError_t launch_transport_batch(const ModelDesc* models, const BatchChunk* ch
                                    cudaStream_t s) {
   if (threads <= 0) threads = 256;
   if (threads % 32 != 0 || threads > 256) return cudaErrorInvalidValue;
-  if (s_fixed == 4)
-    return launch_batch_variant<4>(models, chunks, n_chunks, next_chunk, blocks_per_sm,
-                                   threads, s);
   if (s_fixed == 2)
     return launch_batch_variant<2>(models, chunks, n_chunks, next_chunk, blocks_per_sm,
                                    threads, s);
