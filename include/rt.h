@@ -427,7 +427,8 @@ rt_status rt_pah_training_pairs(rt_grid *g, int pah, int64_t first_cell, int64_t
 
 /* ---------------------------------------------------------------------------
  * Multilayer perceptron of the PAH emission surrogate (the learned stand-in for the
- * transient-heating computation; BF16 tensor-core GEMMs with FP32 accumulation,
+ * transient-heating computation; BF16 GEMMs on the 5th-generation tensor cores
+ * (tcgen05) with FP32 accumulation in tensor memory,
  * FP32 master weights and Adam). Hidden layers use silu(z) = z / (1 + e^-z), the
  * output layer is linear, the loss is the mean squared error over rows and outputs.
  * Parameters are exchanged as FP32 host arrays in the layout: for each layer
@@ -455,7 +456,7 @@ rt_status rt_mlp_set_params(rt_mlp *m, const float *in);  /* host [n_params] */
  * the whole network runs per 128-row tile in one kernel on the 5th-generation tensor
  * cores (tcgen05.mma, FP32 accumulators in tensor memory, BF16 operands in shared
  * memory; an output layer wider than 256 in chunks of 256 columns); otherwise layer
- * by layer (WMMA). */
+ * by layer (one tcgen05 GEMM of 128 x 128 output tiles per layer, as in training). */
 rt_status rt_mlp_forward(rt_mlp *m, const float *x, float *y, int64_t M, void *stream);
 
 /* Loss and gradients of a batch (device x [M][n_in], targets t [M][n_out]) into the

@@ -1,8 +1,8 @@
 // rt_mlp.cu -- the multilayer perceptron of the PAH emission surrogate: forward
-// pass, mean-squared-error gradients and Adam, on tensor cores in BF16 with FP32
-// accumulation. Inference runs the whole network per 128-row tile in one kernel on
-// the 5th-generation tensor cores (tcgen05.mma into tensor memory); training runs
-// layer by layer on WMMA m16n16k16 tiles.
+// pass, mean-squared-error gradients and Adam, on the 5th-generation tensor cores
+// (tcgen05.mma, FP32 accumulators in tensor memory) in BF16 with FP32 accumulation.
+// Inference runs the whole network per 128-row tile in one kernel; training runs
+// layer by layer, each GEMM on 128 x 128 output tiles.
 //
 // Network: a_0 = x; z_l = a_{l-1} W_l^T + b_l; a_l = silu(z_l) for the hidden layers,
 // linear output. Loss = mean over rows and outputs of (y - t)^2. Master weights,
@@ -16,19 +16,17 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <mma.h>
 
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
 
-using namespace nvcuda;
 typedef __nv_bfloat16 bf16;
 
 namespace {
 
-constexpr int kTile = 64;     // block tile (M and N)
+constexpr int kTile = 64;     // rows are padded to a multiple of this
 constexpr int kMaxLayers = 8;
 
 inline int pad16(int x) { return (x + 15) / 16 * 16; }
@@ -71,76 +69,6 @@ struct rt_mlp {
 namespace {
 
 // ---------------------------------------------------------------- kernels
-// C[M][N] (=|+=) A[M][K] . B[K][N]; A row-major (lda) or column-major, B row-major
-// (ldb) or column-major; BF16 operands, FP32 accumulation. Block = 4 warps, tile
-// 64x64, each warp 32x32. gridDim.z splits K into chunks of k_chunk (atomics).
-template <bool kAcol, bool kBcol>
-__global__ void __launch_bounds__(128) k_gemm(const bf16* A, int lda, const bf16* B, int ldb,
-                                              float* C, int ldc, int M, int N, int K,
-                                              int k_chunk, int atomic_out) {
-  typedef typename std::conditional<kAcol, wmma::col_major, wmma::row_major>::type LA;
-  typedef typename std::conditional<kBcol, wmma::col_major, wmma::row_major>::type LB;
-  const int warp = threadIdx.x >> 5;
-  const int m0 = blockIdx.x * kTile + (warp >> 1) * 32;
-  const int n0 = blockIdx.y * kTile + (warp & 1) * 32;
-  const int k_begin = blockIdx.z * k_chunk;
-  const int k_end = min(K, k_begin + k_chunk);
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) wmma::fill_fragment(acc[i][j], 0.0f);
-  wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, LA> fa[2];
-  wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, LB> fb[2];
-  for (int k = k_begin; k < k_end; k += 16) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      int m = m0 + 16 * i;
-      if (m < M) {
-        const bf16* pa = kAcol ? A + (size_t)k * lda + m : A + (size_t)m * lda + k;
-        wmma::load_matrix_sync(fa[i], pa, lda);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      int n = n0 + 16 * j;
-      if (n < N) {
-        const bf16* pb = kBcol ? B + (size_t)n * ldb + k : B + (size_t)k * ldb + n;
-        wmma::load_matrix_sync(fb[j], pb, ldb);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-        if (m0 + 16 * i < M && n0 + 16 * j < N) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
-  }
-  if (!atomic_out) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-        if (m0 + 16 * i < M && n0 + 16 * j < N)
-          wmma::store_matrix_sync(C + (size_t)(m0 + 16 * i) * ldc + n0 + 16 * j, acc[i][j], ldc,
-                                  wmma::mem_row_major);
-    return;
-  }
-  // split-K: add through shared memory staging
-  __shared__ float stage[4][16 * 16];
-  const int lane = threadIdx.x & 31;
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 2; ++j) {
-      if (m0 + 16 * i >= M || n0 + 16 * j >= N) continue;
-      wmma::store_matrix_sync(stage[warp], acc[i][j], 16, wmma::mem_row_major);
-      __syncwarp();
-      for (int e = lane; e < 256; e += 32) {
-        int r = e >> 4, c = e & 15;
-        atomicAdd(&C[(size_t)(m0 + 16 * i + r) * ldc + n0 + 16 * j + c], stage[warp][e]);
-      }
-      __syncwarp();
-    }
-}
-
 // x [M][n_in] FP32 -> a0 [Mp][in_p] BF16, zero padding
 __global__ void k_pack_input(const float* x, long long M, int n_in, long long Mp, int in_p,
                              bf16* a0) {
@@ -361,6 +289,168 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// ---------------------------------------------------------------- training GEMM
+// C[M][N] (=|+=) A[M][K] . B[K][N] on the 5th-generation tensor cores, for the
+// layer-by-layer passes of training: A row-major (lda) or column-major, B row-major
+// (ldb) or column-major; BF16 operands, FP32 accumulation in tensor memory. A CTA of
+// 4 warps owns a 128 x 128 tile of C. The contraction runs in chunks of 64: all
+// threads pack the chunk's A and B tiles from global memory (any layout) into the
+// K-major core-matrix layout in one of two shared-memory buffers, one thread issues
+// the chunk's four MMAs (K = 16 each) and commits them to that buffer's mbarrier, and
+// the packing of the next chunk overlaps them. gridDim.z splits K into chunks of
+// k_chunk (atomic adds). Every wait is bounded: after 2 s the tile's outputs are left
+// untouched and *err is set.
+constexpr int kGemmRows = 128, kGemmCols = 128, kGemmK = 64, kGemmThreads = 128;
+
+template <bool kAcol, bool kBcol>
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const bf16* A, int lda, const bf16* B,
+                                                          int ldb, float* C, int ldc, int M, int N,
+                                                          int K, int k_chunk, int atomic_out,
+                                                          unsigned* err) {
+  extern __shared__ __align__(128) unsigned char gemm_smem[];
+  bf16* sA0 = reinterpret_cast<bf16*>(gemm_smem);          // [2][128 x 64]: 2 x 16 KB
+  bf16* sB0 = sA0 + 2 * kGemmRows * kGemmK;                 // [2][128 x 64]: 2 x 16 KB
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kGemmRows, n0 = blockIdx.y * kGemmCols;
+  const int k_begin = blockIdx.z * k_chunk;
+  const int k_end = min(K, k_begin + k_chunk);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kGemmCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = tc_idesc(kGemmRows, kGemmCols);
+  bool ok = true;
+  int n_chunks = 0;
+  for (int k0 = k_begin; k0 < k_end && ok; k0 += kGemmK, ++n_chunks) {
+    const int buf = n_chunks & 1;
+    // the buffer was last read by the MMAs of chunk n_chunks - 2
+    if (n_chunks >= 2) {
+      const bool got = mbar_wait(smem_addr(&bar[buf]), (uint32_t)(((n_chunks - 2) >> 1) & 1));
+      if (!__syncthreads_and(got)) {
+        if (tid == 0) atomicOr(err, 1u);
+        ok = false;
+        break;
+      }
+    }
+    const int kc = min(kGemmK, k_end - k0);  // a multiple of 16
+    // A tile: element (r, k) = A[m0 + r][k0 + k], zero outside; 8 k per item
+    bf16* a = sA0 + buf * kGemmRows * kGemmK;
+    for (int i = tid; i < kGemmRows * (kGemmK / 8); i += kGemmThreads) {
+      const int r = i / (kGemmK / 8), k8 = (i % (kGemmK / 8)) * 8;
+      const int m = m0 + r;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (m < M && k8 < kc) {
+        if (!kAcol) {
+          v = *reinterpret_cast<const uint4*>(A + (size_t)m * lda + k0 + k8);
+        } else {
+          uint32_t w[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            w[j] = (uint32_t)__bfloat16_as_ushort(A[(size_t)(k0 + k8 + 2 * j) * lda + m]) |
+                   ((uint32_t)__bfloat16_as_ushort(A[(size_t)(k0 + k8 + 2 * j + 1) * lda + m])
+                    << 16);
+          v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      *reinterpret_cast<uint4*>(&a[core_off(r, k8, kGemmK)]) = v;
+    }
+    // B tile as the MMA's [N][K] operand: element (n, k) = B[k0 + k][n0 + n]
+    bf16* b = sB0 + buf * kGemmCols * kGemmK;
+    for (int i = tid; i < kGemmCols * (kGemmK / 8); i += kGemmThreads) {
+      const int c = i / (kGemmK / 8), k8 = (i % (kGemmK / 8)) * 8;
+      const int n = n0 + c;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (n < N && k8 < kc) {
+        if (kBcol) {
+          v = *reinterpret_cast<const uint4*>(B + (size_t)n * ldb + k0 + k8);
+        } else {
+          uint32_t w[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            w[j] = (uint32_t)__bfloat16_as_ushort(B[(size_t)(k0 + k8 + 2 * j) * ldb + n]) |
+                   ((uint32_t)__bfloat16_as_ushort(B[(size_t)(k0 + k8 + 2 * j + 1) * ldb + n])
+                    << 16);
+          v = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      *reinterpret_cast<uint4*>(&b[core_off(c, k8, kGemmK)]) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t a0 = smem_addr(a), b0 = smem_addr(b);
+      const uint32_t sbo = (uint32_t)kGemmK * 16u;
+      for (int kk = 0; kk < kc / 16; ++kk)
+        tc_mma(tmem, tc_desc(a0 + kk * 256u, 128u, sbo), tc_desc(b0 + kk * 256u, 128u, sbo), idesc,
+               (n_chunks > 0 || kk > 0) ? 1u : 0u);
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              smem_addr(&bar[buf]))
+          : "memory");
+    }
+  }
+  // the last chunk's MMAs (and with them all earlier ones) done
+  if (ok && n_chunks > 0) {
+    const int last = n_chunks - 1;
+    const bool got = mbar_wait(smem_addr(&bar[last & 1]), (uint32_t)((last >> 1) & 1));
+    if (!__syncthreads_and(got)) {
+      if (tid == 0) atomicOr(err, 1u);
+      ok = false;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok && n_chunks > 0) {
+    // warp w holds rows 32 w .. 32 w + 31 of the tile (tensor-memory lanes)
+    const int m = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < kGemmCols; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (m >= M || n0 + c0 >= N) continue;
+      float* cr = C + (size_t)m * ldc + n0 + c0;
+      const int nv = min(16, N - n0 - c0);
+      if (atomic_out) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j < nv) atomicAdd(&cr[j], v[j]);
+      } else if (nv == 16 && ((reinterpret_cast<uintptr_t>(cr) & 15) == 0)) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(&cr[j]) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j < nv) cr[j] = v[j];
+      }
+    }
+  } else if (!ok && n_chunks > 0 && warp == 0) {
+    // a wait ran out: let the MMAs still in flight land before releasing tensor memory
+    const int last = n_chunks - 1;
+    mbar_wait(smem_addr(&bar[last & 1]), (uint32_t)((last >> 1) & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kGemmCols));
+  }
 }
 
 struct TcNet {
@@ -612,21 +702,25 @@ inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 // ---------------------------------------------------------------- host helpers
 template <bool Acol, bool Bcol>
 cudaError_t gemm(const bf16* A, int lda, const bf16* B, int ldb, float* C, int ldc, long long M,
-                 int N, int K, bool split, cudaStream_t s) {
-  dim3 grid(nb(M, kTile), nb(N, kTile), 1);
+                 int N, int K, bool split, unsigned* err, cudaStream_t s) {
+  dim3 grid(nb(M, kGemmRows), nb(N, kGemmCols), 1);
   int chunk = K;
   if (split) {
     // split the contraction so that the grid fills the GPU
     long long tiles = (long long)grid.x * grid.y;
-    long long want = (152 * 8 + tiles - 1) / tiles;
-    long long ksteps = K / 16;
+    long long want = (152 * 2 + tiles - 1) / tiles;
+    long long ksteps = (K + kGemmK - 1) / kGemmK;
     if (want > ksteps) want = ksteps;
     if (want < 1) want = 1;
-    chunk = (int)(((ksteps + want - 1) / want) * 16);
+    chunk = (int)(((ksteps + want - 1) / want) * kGemmK);
     grid.z = (unsigned)((K + chunk - 1) / chunk);
   }
-  k_gemm<Acol, Bcol><<<grid, 128, 0, s>>>(A, lda, B, ldb, C, ldc, (int)M, N, K, chunk,
-                                          split ? 1 : 0);
+  const size_t smem = sizeof(bf16) * 2 * (kGemmRows + kGemmCols) * kGemmK;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<Acol, Bcol>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gemm_tc<Acol, Bcol><<<grid, kGemmThreads, smem, s>>>(A, lda, B, ldb, C, ldc, (int)M, N, K,
+                                                         chunk, split ? 1 : 0, err);
   return cudaGetLastError();
 }
 
@@ -737,7 +831,7 @@ rt_status forward_rows(rt_mlp* m, long long Mp, cudaStream_t s) {
   for (int l = 0; l < L; ++l) {
     const Layer& ly = m->layer[l];
     if (gemm<false, true>(m->d_a[l], ly.in_p, m->d_wbf + ly.w_off, ly.in_p, m->d_z[l], ly.out_p,
-                          Mp, ly.out_p, ly.in_p, false, s) != cudaSuccess)
+                          Mp, ly.out_p, ly.in_p, false, m->d_err, s) != cudaSuccess)
       return RT_ERR_CUDA;
     k_bias_act<<<nb(Mp * ly.out_p, 256), 256, 0, s>>>(m->d_z[l], m->d_param + ly.b_off, Mp,
                                                       ly.out_p, ly.n_out, l < L - 1,
@@ -951,14 +1045,14 @@ rt_status rt_mlp_loss_grad(rt_mlp* m, const float* x, const float* t, int64_t M,
     const Layer& ly = m->layer[l];
     // dW_l = dz^T a_{l-1}: [out_p][in_p], contraction over rows (split)
     if (gemm<true, false>(m->d_dzb, ly.out_p, m->d_a[l], ly.in_p, m->d_grad + ly.w_off, ly.in_p,
-                          ly.out_p, ly.in_p, (int)Mp, true, s) != cudaSuccess)
+                          ly.out_p, ly.in_p, (int)Mp, true, m->d_err, s) != cudaSuccess)
       return RT_ERR_CUDA;
     dim3 g2(nb(ly.out_p, 32), 64);
     k_col_sums<<<g2, 256, 0, s>>>(m->d_dz, Mp, ly.out_p, m->d_grad + ly.b_off);
     if (l > 0) {
       // da_{l-1} = dz W_l: [Mp][in_p]; then through silu'
       if (gemm<false, false>(m->d_dzb, ly.out_p, m->d_wbf + ly.w_off, ly.in_p, m->d_dz, ly.in_p,
-                             Mp, ly.in_p, ly.out_p, false, s) != cudaSuccess)
+                             Mp, ly.in_p, ly.out_p, false, m->d_err, s) != cudaSuccess)
         return RT_ERR_CUDA;
       const Layer& lp = m->layer[l - 1];
       k_act_back<<<nb(Mp * ly.in_p, 256), 256, 0, s>>>(m->d_dz, m->d_z[l - 1], Mp, ly.in_p,

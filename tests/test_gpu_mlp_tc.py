@@ -1,7 +1,7 @@
 """The fused tensor-core forward pass (tcgen05.mma into tensor memory) of the
 surrogate network: against the FP64 oracle within BF16 error, against the
-layer-by-layer WMMA forward of the training path (the same BF16 weights, so nearly
-identical), for ragged row counts, after the weights change, with an output layer
+layer-by-layer forward of the training path (tcgen05 GEMMs per layer on the same BF16
+weights, so nearly identical), for ragged row counts, after the weights change, with an output layer
 wider than one MMA (run in chunks of 256 columns), and with a hidden layer too wide
 for it (the layer-by-layer path takes over)."""
 import numpy as np
@@ -30,7 +30,7 @@ def _check_against_oracle(net, shapes, x, y):
 
 
 @pytest.mark.parametrize("M", [1, 127, 128, 1000, 70_001])
-def test_fused_forward_matches_oracle_and_wmma(M):
+def test_fused_forward_matches_oracle_and_layer_path(M):
     net = rt.MLP(66, 256, 3, 200, seed=7)
     shapes = omlp.layer_shapes(66, 256, 3, 200)
     rng = np.random.default_rng(M)
