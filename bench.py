@@ -49,8 +49,10 @@ def parse():
                    help="packages per GPU per step (default: 2.5e8 for the large disk, "
                         "1e8 otherwise)")
     p.add_argument("--workload", choices=["disk", "sphere", "batch", "disk_pah", "disk_images",
-                                          "large_disk", "disk4", "disk_pah_small"],
+                                          "large_disk", "disk4", "disk_pah_small", "surrogate"],
                    default="large_disk")
+    p.add_argument("--rows", type=float, default=5e5,
+                   help="surrogate workload: feature rows per forward pass")
     p.add_argument("--full-run", action="store_true",
                    help="after the timed steps, one untimed-by-the-line run of the "
                         "workload's full package count (1e10 for the large disk), reported "
@@ -291,7 +293,15 @@ def run_reference(args):
 # per executed warp instruction (warp execution efficiency x 32).
 PROFILE_SOURCES = ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                    "paper_1201_3588_gb300/csrc/rt_internal.h")
-PROFILE = {}
+PROFILE = {
+    # 1-pass counters of one 2e7-package launch on the full large disk (path walk):
+    # dram 292.27 GB read + 0.12 GB written; 6.889e10 warp and 1.111e12 thread
+    # instructions over 5.24e9 crossings
+    "large_disk": {"sha256": "0bb87f54571fab1d8125cf1b2ad3721fa80032214808ec8e6740f9edef8e0f89",
+                   "dram_bytes_per_package": 14619.7, "warp_lanes_active": 16.13,
+                   "warp_instr_per_crossing": 13.14,
+                   "file": "profiles/k_transport_pool_large_disk.md"},
+}
 
 
 def source_code_hash(paths):
@@ -511,9 +521,11 @@ def run_ours(args):
         t_start.record(stream)
         for k in range(args.steps):
             step(args.warmup + k, kev[k])
-            # transport, temperatures; the PAH pass (counted from its own sizes)
-            launches += 2 + (pah_step_launches(pah_state["active"], pah_state["fallback"],
-                                               g.n_pah) if pah else 0) + (4 if images else 0)
+            # transport, temperatures, the reset's clearing of PAH rows; the PAH pass
+            # (counted from its own sizes)
+            launches += 2 + (1 if g.n_pah else 0) + (
+                pah_step_launches(pah_state["active"], pah_state["fallback"], g.n_pah)
+                if pah else 0) + (4 if images else 0)
         t_end.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -925,10 +937,83 @@ def batch_e2e(models, opts, steps):
             "ms_per_step": 1e3 * sum(times) / len(times), "host_buffers": "pageable"}
 
 
+def peaks_tensor():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_surrogate(args):
+    """The PAH emission network alone (the large disk's shape: 64 coarse bins + 2
+    features -> 3 x 256 SiLU -> 400 bins): a step is one fused tensor-core forward
+    pass over `--rows` synthetic feature rows; the line reports its tensor roofline
+    (2 sum(in x out) FLOP per row against the bf16 peak) and the time of one training
+    step (loss, gradients and Adam on 1024 rows, layer-by-layer tcgen05 GEMMs)."""
+    import torch
+    from paper_1201_3588_gb300 import rt
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n_in, n_h, n_l, n_out = 66, 256, 3, 400
+    M = int(args.rows)
+    net = rt.MLP(n_in, n_h, n_l, n_out, seed=0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    x = torch.rand((M, n_in), device=dev, generator=gen) * 2.0 - 1.0
+    y = torch.empty((M, n_out), device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    for _ in range(args.warmup):
+        net.forward(x, y, stream=stream)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
+        a.record(stream)
+        for _ in range(args.steps):
+            net.forward(x, y, stream=stream)
+        e.record(stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+    el = a.elapsed_time(e) / 1e3 / args.steps
+    flops = 2.0 * (n_in * n_h + (n_l - 1) * n_h * n_h + n_h * n_out) * M
+    peak, src = peaks_tensor()
+    achieved = flops / el / 1e12
+    xb = x[:1024].contiguous()
+    tb = torch.rand((1024, n_out), device=dev, generator=gen)
+    for _ in range(3):
+        net.loss_grad(xb, tb, want_loss=False, stream=stream)
+        net.adam_step(1e-4, stream=stream)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(50):
+        net.loss_grad(xb, tb, want_loss=False, stream=stream)
+        net.adam_step(1e-4, stream=stream)
+    e.record(stream)
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(e) / 50
+    line = {"metric": "surrogate forward rows/s (PAH emission network, fused tcgen05)",
+            "value": M / el, "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"{M} feature rows, network {n_in} -> {n_l} x {n_h} SiLU "
+                                   f"-> {n_out}", "rows": M},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": src, "kernel": "k_mlp_forward_tc",
+                         "flop_per_row": flops / M},
+            "training_step_ms_1024_rows": train_ms,
+            "gpu_launches": args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
     elif args.workload == "batch":
         run_batch(args)
     else:
