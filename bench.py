@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--walk", choices=["auto", "linked", "path"], default="auto",
                    help="the pool kernel's walk (auto: the path walk when the face-link "
                         "records exceed 4 GB)")
+    p.add_argument("--no-tune", action="store_true",
+                   help="skip the autotuning of the pool launch before the timed steps")
     p.add_argument("--no-pah", action="store_true",
                    help="leave the PAH emission out of the step (the transport still "
                         "tallies PAH absorptions); for profiling the transport alone")
@@ -472,6 +474,15 @@ def run_ours(args):
         g.set_images((0.0, math.sin(inc), math.cos(inc)), pob, 256, 256, model.half_size)
         img_dev = torch.empty((2, 256, 256), dtype=torch.float64, device=dev)
         prof_dev = torch.empty(256, dtype=torch.float64, device=dev)
+    # the pool launch (blocks per SM, threads, interaction batch, refill period, walk)
+    # tuned on prefixes of this grid, before anything is timed
+    opts = {}
+    if not args.no_tune and not images:
+        from paper_1201_3588_gb300 import autotune
+        tau = model.recipe.get("tau_v_mid", model.recipe.get("tau_v", 1.0))
+        opts = autotune.tune(g, tau, n_probe=min(n, 20_000_000))
+    if args.walk != "auto":
+        opts["walk"] = WALKS[args.walk]
     net, pah_info = None, {}
     tol = 0.05
     cells_dev = j_dev = None
@@ -488,7 +499,7 @@ def run_ours(args):
         if ev:
             ev[0].record(stream)
         g.transport(n, seed=1000 + k, first_id=first, stream=stream,
-                    count_scale=shard.count_scale(world), walk=WALKS[args.walk])
+                    count_scale=shard.count_scale(world), **opts)
         if ev:
             ev[1].record(stream)
         if world > 1:  # sum the integer counts over ranks (package ranges are disjoint)
@@ -577,16 +588,16 @@ def run_ours(args):
                            "profile_peak": float(prof_dev.max())}
     if rank == 0 and not args.no_plain and not images:
         extra["plain"] = plain_rates(g, model, int(args.plain_packages), stream,
-                                     net if pah else None, cells_dev, j_dev, tol)
+                                     net if pah else None, cells_dev, j_dev, tol, opts)
     if args.full_run and rank == 0:
-        extra["full_run"] = full_run(g, args.workload, stream, net, cells_dev, j_dev, tol)
+        extra["full_run"] = full_run(g, args.workload, stream, net, cells_dev, j_dev, tol, opts)
     params = net.get_params() if pah else None
     n_active = pah_state["active"]
     del T_dev, cells_dev, j_dev
     g.close()
     torch.cuda.empty_cache()
     e2e = e2e_rate(model, n, world, first, args.e2e_steps, net, params, tol,
-                   max(1, 2 * n_active)) if args.e2e_steps > 0 and not images else None
+                   max(1, 2 * n_active), opts) if args.e2e_steps > 0 and not images else None
     if rank == 0:
         cpu_rate, cpu_n, cpu_s, cpu_cores = cpu_oracle_rate(model, n * world, args.cpu_seconds,
                                                             pool=pool)
@@ -602,7 +613,9 @@ def run_ours(args):
                        "packages_full_workload": FULL_PACKAGES.get(args.workload),
                        "leaves": N, "bins": B, "species": S, "levels": L,
                        "reemission": "bjorkman-wood",
-                       "walk": walk_label(args.walk, N, S, L),
+                       "walk": walk_label(args.walk, N, S, L) if "walk" not in opts else
+                       {1: "linked", 2: "path"}[opts["walk"]] + " (autotuned)",
+                       "launch": opts or "defaults",
                        "form": "FP32 packet-pool transport" +
                                (" + BF16 tcgen05 PAH surrogate with exact fallback"
                                 if pah else ""),
@@ -649,7 +662,8 @@ ORACLE_ERROR = {
 }
 
 
-def plain_rates(g, model, n_prefix, stream, net=None, cells_dev=None, j_dev=None, tol=0.05):
+def plain_rates(g, model, n_prefix, stream, net=None, cells_dev=None, j_dev=None, tol=0.05,
+                opts=None):
     """The plain form (one thread per package, global tables, per-lane atomics; FP64
     and FP32) against the pool on a package prefix of the same workload; with PAHs,
     also the plain form's exact PAH emission of every active cell against the
@@ -663,7 +677,8 @@ def plain_rates(g, model, n_prefix, stream, net=None, cells_dev=None, j_dev=None
         a, b = ev()
         g.reset(stream)
         a.record(stream)
-        g.transport(n_prefix, seed=77, kernel=kern, stream=stream)
+        g.transport(n_prefix, seed=77, kernel=kern, stream=stream,
+                    **(opts if kern == rt.KERNEL_POOL and opts else {}))
         b.record(stream)
         torch.cuda.synchronize()
         out[name] = n_prefix / (a.elapsed_time(b) / 1e3)
@@ -671,7 +686,7 @@ def plain_rates(g, model, n_prefix, stream, net=None, cells_dev=None, j_dev=None
     out["pool_over_plain_f64"] = out["pool_f32"] / out["plain_f64"]
     if net is not None:
         g.reset(stream)
-        g.transport(n_prefix, seed=77, stream=stream)
+        g.transport(n_prefix, seed=77, stream=stream, **(opts or {}))
         times = {}
         for name, mode in (("exact", rt.PAH_EXACT), ("auto", rt.PAH_AUTO)):
             a, b = ev()
@@ -694,7 +709,7 @@ def plain_rates(g, model, n_prefix, stream, net=None, cells_dev=None, j_dev=None
     return out
 
 
-def full_run(g, workload, stream, net, cells_dev, j_dev, tol):
+def full_run(g, workload, stream, net, cells_dev, j_dev, tol, opts=None):
     """One pass of the workload's full package count in launches of 1e9 packages
     (consecutive id ranges), then temperatures, spectrum and PAH emission."""
     import torch
@@ -708,7 +723,8 @@ def full_run(g, workload, stream, net, cells_dev, j_dev, tol):
     torch.cuda.synchronize()
     a.record(stream)
     for f0 in range(0, n_full, chunk):
-        g.transport(min(chunk, n_full - f0), seed=4242, first_id=f0, stream=stream)
+        g.transport(min(chunk, n_full - f0), seed=4242, first_id=f0, stream=stream,
+                    **(opts or {}))
     g.temperatures(out=T, stream=stream)
     g.sed(stream=stream)
     nf = na = 0
@@ -752,7 +768,8 @@ def pinned_model(model):
     return m, keep
 
 
-def e2e_rate(model, n, world, first, steps, net=None, params=None, tol=0.05, max_cells=1):
+def e2e_rate(model, n, world, first, steps, net=None, params=None, tol=0.05, max_cells=1,
+             opts=None):
     """Same metric through the public API with host buffers: every step creates the
     grid from pinned host arrays (tree, densities, opacities, PAH data), loads the
     surrogate's weights from the host, transports, and reads the temperatures, the
@@ -779,7 +796,7 @@ def e2e_rate(model, n, world, first, steps, net=None, params=None, tol=0.05, max
             if pah:
                 net.set_params(params)
             g.emit_star(n * world)
-            g.transport(n, seed=5000 + k, first_id=first)
+            g.transport(n, seed=5000 + k, first_id=first, **(opts or {}))
             g.temperatures(out=T_host)
             g.sed(out=sed_host)
             if pah:

@@ -1400,8 +1400,6 @@ cudaError_t launch_transport_pool(const DevGrid& g, const DevTables& t, const De
   const DevPeel none{};
   // the path walk (no face links; grids of at most kPathLevels levels)
   if (path && !r.pathabs && g.max_level <= kPathLevels) {
-    if (g.S == 4 && threads == 256 && blocks_per_sm == 5)
-      return launch_pool_variant<5, false, 4, true>(g, t, r, none, blocks_per_sm, threads, sms, s);
     if (g.S == 4)
       return launch_pool_variant<4, false, 4, true>(g, t, r, none, blocks_per_sm, threads, sms, s);
     if (g.S == 2)
