@@ -3,7 +3,8 @@ transport of a package prefix under each candidate (resident blocks per SM, thre
 per block, interaction batch, refill period, and for a single grid the walk) with CUDA
 events and keep the fastest.
 Results are cached in a JSON file keyed by the workload class (cells to the nearest
-power of two, bins, optical-depth decade; for a batch, its models' classes)."""
+power of two, species, levels, bins, optical-depth decade; for a batch, its models'
+classes)."""
 from __future__ import annotations
 
 import itertools
@@ -23,7 +24,8 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1201_3588
 
 
 def workload_key(grid: "rt.Grid", tau_v: float) -> str:
-    return (f"cells2^{int(round(math.log2(max(grid.N, 1))))}-bins{grid.B}-"
+    return (f"cells2^{int(round(math.log2(max(grid.N, 1))))}-S{grid.S}-"
+            f"L{grid.model.tree.max_level}-bins{grid.B}-"
             f"tau1e{int(math.floor(math.log10(max(tau_v, 1e-30))))}")
 
 

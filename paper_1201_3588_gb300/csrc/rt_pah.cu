@@ -505,20 +505,28 @@ __global__ void k_compact(const unsigned* pah_flag, int pah, long long first, lo
 }
 
 // Zero the absorbed spectra of the PAH-active cells and their flags (the other
-// rows are zero already). A warp per cell: one coalesced row of K words per PAH.
+// rows are zero already). Each lane reads one cell's flag word (coalesced); the warp
+// then clears the rows of its flagged cells one after another, a coalesced row of K
+// words per PAH.
 __global__ void k_pah_clear(const unsigned* pah_flag, long long N, int K, int n_pah,
                             unsigned* pahabs, unsigned* flag_out) {
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   const int lane = threadIdx.x & 31;
-  for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; c < N;
-       c += warps) {
-    const unsigned f = pah_flag[c];
-    if (f == 0u) continue;
-    for (int p = 0; p < n_pah; ++p)
-      if (f & (1u << p))
-        for (int k = lane; k < K; k += 32) pahabs[((size_t)p * N + c) * K + k] = 0u;
-    __syncwarp();
-    if (lane == 0) flag_out[c] = 0u;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  for (long long base = w0 * 32; base < N; base += warps * 32) {
+    const long long c = base + lane;
+    const unsigned f = c < N ? pah_flag[c] : 0u;
+    unsigned m = __ballot_sync(0xffffffffu, f != 0u);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const unsigned fc = __shfl_sync(0xffffffffu, f, src);
+      const long long cc = base + src;
+      for (int p = 0; p < n_pah; ++p)
+        if (fc & (1u << p))
+          for (int k = lane; k < K; k += 32) pahabs[((size_t)p * N + cc) * K + k] = 0u;
+    }
+    if (f) flag_out[c] = 0u;
   }
 }
 
@@ -781,7 +789,7 @@ cudaError_t launch_pah_clear(const unsigned* pah_flag, long long N, int K, int n
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  long long blocks = (N * 32 + 255) / 256;
+  long long blocks = (N + 255) / 256;  // a lane per cell
   const long long cap = (long long)(sms > 0 ? sms : 152) * 8;
   if (blocks > cap) blocks = cap;
   k_pah_clear<<<(unsigned)blocks, 256, 0, s>>>(pah_flag, N, K, n_pah, pahabs, flag_out);
