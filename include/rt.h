@@ -135,7 +135,8 @@ typedef struct rt_counters {
 
 /* Create a grid handle: copies the tree and densities to the device and walks the
  * tree there, level by level, to find every leaf's level and corner and build its
- * face links. RT_ERR_ARG when a leaf or block is reached twice or never, an id is
+ * face links (deferred to the first call that reads them -- a linked-walk transport,
+ * peel-off images, a replay, a batch -- when the automatic walk is the path walk). RT_ERR_ARG when a leaf or block is reached twice or never, an id is
  * out of range, a block lies at max_level or deeper, or a density is negative or
  * not finite. Synchronises. */
 rt_status rt_grid_create(const rt_grid_desc *d, rt_grid **out);

@@ -485,7 +485,11 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   ALLOC(g->d_child, (size_t)d->n_blocks * 8);
   ALLOC(g->d_rho, (size_t)S * N);
   ALLOC(g->d_level, (size_t)N);
-  ALLOC(g->d_links, (size_t)N * kRec);
+  // face links only where the automatic walk reads them (built below); otherwise on
+  // the first call that needs them (ensure_links)
+  const bool links_now = !(d->max_level <= 4 &&
+                           (S == 4 || 4.0 * kRec * (double)N > 4.0e9));
+  if (links_now) ALLOC(g->d_links, (size_t)N * kRec);
   ALLOC(g->d_count, (size_t)S * N);
   ALLOC(g->d_sed, (size_t)2 * d->n_sed_dirs * B);
   ALLOC(g->d_counters, (size_t)kNumCounters);
@@ -569,7 +573,7 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   g->g.n_dir = d->n_sed_dirs;
   g->g.n_T = g->desc.n_temp;
   // face links of every leaf, built on the device from the leaf corners
-  e = launch_build_links(g->g, d_ijk, g->d_links, nullptr);
+  if (links_now) e = launch_build_links(g->g, d_ijk, g->d_links, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   free_work();
   if (e != cudaSuccess) {
@@ -578,6 +582,61 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
     return RT_ERR_CUDA;
   }
   *out = g;
+  return RT_OK;
+}
+
+// The face links, built when a call first needs them (a linked-walk transport,
+// peel-off sight lines, a replay, a batch): the tree is walked again for the leaf
+// corners, then the links are built from them. Synchronises.
+static rt_status ensure_links(rt_grid* g) {
+  if (g->d_links) return RT_OK;
+  const long long N = g->desc.n_leaves;
+  const long long nbk = g->desc.n_blocks > 0 ? g->desc.n_blocks : 1;
+  int32_t *d_ijk = nullptr, *d_blk_ijk = nullptr;
+  int8_t* d_blk_level = nullptr;
+  unsigned *d_leaf_seen = nullptr, *d_blk_seen = nullptr, *d_err = nullptr;
+  rt_status st = dalloc(&g->d_links, (size_t)N * kRec);
+  if (st == RT_OK) st = dalloc(&d_ijk, (size_t)N * 3);
+  if (st == RT_OK) st = dalloc(&d_blk_ijk, (size_t)nbk * 3);
+  if (st == RT_OK) st = dalloc(&d_blk_level, (size_t)nbk);
+  if (st == RT_OK) st = dalloc(&d_leaf_seen, (size_t)((N + 31) >> 5));
+  if (st == RT_OK) st = dalloc(&d_blk_seen, (size_t)((nbk + 31) >> 5));
+  if (st == RT_OK) st = dalloc(&d_err, 2);
+  cudaError_t e = cudaSuccess;
+  if (st == RT_OK) {
+    TreeBuild tb{};
+    tb.base = g->d_base;
+    tb.child = g->d_child;
+    tb.n_leaves = N;
+    tb.n_blocks = g->desc.n_blocks;
+    tb.n_base = g->desc.n_base;
+    tb.max_level = g->desc.max_level;
+    tb.level = g->d_level;
+    tb.ijk = d_ijk;
+    tb.blk_level = d_blk_level;
+    tb.blk_ijk = d_blk_ijk;
+    tb.leaf_seen = d_leaf_seen;
+    tb.blk_seen = d_blk_seen;
+    tb.err = d_err;
+    tb.max_seen = reinterpret_cast<int*>(d_err + 1);
+    e = cudaMemset(d_err, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = launch_tree_walk(tb, nullptr);
+    if (e == cudaSuccess) e = launch_build_links(g->g, d_ijk, g->d_links, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = RT_ERR_CUDA;
+  }
+  dfree(d_ijk);
+  dfree(d_blk_ijk);
+  dfree(d_blk_level);
+  dfree(d_leaf_seen);
+  dfree(d_blk_seen);
+  dfree(d_err);
+  if (st != RT_OK) {
+    dfree(g->d_links);
+    g->d_links = nullptr;
+    return st;
+  }
+  g->g.links = g->d_links;
   return RT_OK;
 }
 
@@ -775,6 +834,9 @@ rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
   t.pah_cell_cdf = g->d_pah_cell_cdf;
   if (g->images && kernel != RT_KERNEL_POOL) return RT_ERR_STATE;
   if (kernel == RT_KERNEL_POOL) {
+    // the path walk runs without images and without the path-length tally
+    if ((g->images || r.pathabs || !use_path_walk(g, o)) && (st = ensure_links(g)) != RT_OK)
+      return st;
     RT_CUDA(cudaMemsetAsync(g->d_next, 0, sizeof(unsigned long long), s));
     RT_CUDA(launch_transport_pool(g->g, t, r, o ? o->blocks_per_sm : 0, threads, s,
                                   g->images ? &g->peel : nullptr, use_path_walk(g, o)));
@@ -1063,6 +1125,7 @@ rt_status rt_trace(rt_grid* g, const uint64_t* ids, int64_t n, uint64_t seed,
   RT_CUDA(cudaSetDevice(g->dev));
   rt_status st = build_tables(g, nullptr);
   if (st != RT_OK) return st;
+  if ((st = ensure_links(g)) != RT_OK) return st;
   if (!g->frozen_ready) return RT_ERR_STATE;
   rt_run_opts o{};
   o.mode = RT_REEMIT_FROZEN;
@@ -1098,6 +1161,7 @@ rt_status rt_trace_events(rt_grid* g, const uint64_t* ids, int64_t n, uint64_t s
   RT_CUDA(cudaSetDevice(g->dev));
   rt_status st = build_tables(g, nullptr);
   if (st != RT_OK) return st;
+  if ((st = ensure_links(g)) != RT_OK) return st;
   if (!g->frozen_ready) return RT_ERR_STATE;
   rt_run_opts o{};
   o.mode = RT_REEMIT_FROZEN;
@@ -1590,6 +1654,7 @@ rt_status rt_batch_create(rt_grid* const* grids, int n, const uint64_t* n_packag
     if (!g || g->dev != b->dev) { st = RT_ERR_ARG; break; }
     if (g->images) { st = RT_ERR_STATE; break; }  // images need the single-model pool
     if ((st = build_tables(g, nullptr)) != RT_OK) break;
+    if ((st = ensure_links(g)) != RT_OK) break;  // the batched launch walks the links
     if ((st = ensure_pathabs(g, o, nullptr)) != RT_OK) break;
     if (n_packages[m] > g->n_total) { st = RT_ERR_RANGE; break; }
     DevRun r;
