@@ -726,6 +726,8 @@ def full_run(g, workload, stream, net, cells_dev, j_dev, tol, opts=None):
     n_full = int(FULL_PACKAGES.get(workload, 1e8))
     T = torch.empty((g.S, g.N), dtype=torch.float32, device=j_dev.device if j_dev is not None
                     else torch.device("cuda"))
+    torch.cuda.synchronize()
+    g.emit_star(n_full)  # the source's package energy for the full count
     g.reset(stream)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     chunk = 10 ** 9

@@ -50,8 +50,8 @@ def runs_z(o_runs, g_runs):
     count. Returns (z, compared) with compared = cells where either mean is > 0."""
     mo, mg = o_runs.mean(axis=0), g_runs.mean(axis=0)
     ko, kg = o_runs.shape[0], g_runs.shape[0]
-    pooled = ((ko - 1) * o_runs.var(axis=0, ddof=1) + (kg - 1) * g_runs.var(axis=0, ddof=1)) \
-        / (ko + kg - 2)
+    ov = o_runs.var(axis=0, ddof=1) if ko > 1 else 0.0   # one oracle run: GPU spread only
+    pooled = ((ko - 1) * ov + (kg - 1) * g_runs.var(axis=0, ddof=1)) / (ko + kg - 2)
     var = np.maximum(np.maximum(pooled, 0.5 * (mo + mg)), 1.0)
     return (mo - mg) / np.sqrt(var * (1.0 / ko + 1.0 / kg)), mo + mg > 0
 

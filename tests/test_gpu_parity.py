@@ -6,7 +6,7 @@
   re-emission spectra) lets a small fraction diverge.
 * BW mode: counts depend on the arrival order, so GPU and oracle agree in
   distribution: per-cell counts within 4 sigma (sigma from GPU batch means,
-  floored at Poisson).
+  floored at Poisson; no more cells beyond than chance allows).
 * Temperatures: the GPU kernel and the oracle invert the same counts.
 * Closed forms on the GPU at large N: Beer-Lambert slab, 2x2x2 first interactions,
   the optically thin r^-1/2 law (0.5% where counts > 1e4).
@@ -19,8 +19,8 @@ import pytest
 
 import oracle
 from paper_1201_3588_gb300 import rt, workloads as w
-from _helpers import (binom_ok, escape_fraction_cube, frozen_field, grey_box,
-                      trace_agreement)
+from _helpers import (assert_runs_agree, binom_ok, escape_fraction_cube, frozen_field,
+                      grey_box, trace_agreement)
 
 pytestmark = pytest.mark.gpu
 SIGMA = 5.670374419e-5
@@ -121,16 +121,11 @@ def test_counts_statistics_match_oracle(sphere, mode):
     N = 20000
     runs, seds = _gpu_batches(sphere, N, 32, mode)
     o = oracle.transport(sphere, N, seed=77, mode=mode, n_total=N)
-    for gpu, orc in ((runs, o.count.astype(np.float64)), (seds, o.sed[0, 0].astype(np.float64))):
-        mean = gpu.mean(axis=0)
-        # batch-means variance, floored at Poisson and at one count (cells that see
-        # a count every few dozen runs would otherwise give spurious z-scores)
-        var = np.maximum(np.maximum(gpu.var(axis=0, ddof=1), mean), 1.0)
-        z = (orc - mean) / np.sqrt(var * (1 + 1 / gpu.shape[0]) + 1e-12)
-        ok = mean + orc > 0
-        assert np.abs(z[ok]).max() < 5.0, np.abs(z[ok]).max()
-        # aggregate: the mean square z stays near 1
-        assert (z[ok] ** 2).mean() < 1.3
+    # one oracle run against 32 GPU runs, per cell within 4 sigma (the variance from
+    # the GPU runs, floored at Poisson and at one count; beyond 4 sigma no more cells
+    # than chance allows over the 8192 compared)
+    assert_runs_agree(o.count.astype(np.float64)[None], runs, f"mode {mode} counts")
+    assert_runs_agree(o.sed[0, 0].astype(np.float64)[None], seds, f"mode {mode} spectrum")
 
 
 def test_temperature_kernel_inverts_like_oracle(sphere):
