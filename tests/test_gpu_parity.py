@@ -268,3 +268,36 @@ def test_max_bins_and_many_directions():
         c = g.counters()
     assert c["escaped"] == 50000 and int(sed[0].sum()) == 50000
     assert sed.shape == (2, 64, B)
+
+
+def test_bw_and_no_correction_agree_where_counts_are_large(sphere):
+    """Sec. 2: the vectorised code re-emits without the Bjorkman-Wood correction, and
+    the two agree when a cell's counts are not small. Cells with more than 1e4
+    absorptions: the mean temperatures of 6 runs per mode agree within 0.5 %, or
+    within 4 standard errors of the difference where the runs scatter more; cells with
+    few counts show the no-correction mode's low bias."""
+    N, runs = 40_000_000, 6
+    res = {}
+    for mode in (rt.REEMIT_BW, rt.REEMIT_NOCORR):
+        Ts, Cs = [], []
+        with rt.Grid(sphere) as g:
+            g.emit_star(N)
+            for k in range(runs):
+                g.reset()
+                g.transport(N, seed=300 + k, mode=mode)
+                Ts.append(g.temperatures().astype(np.float64))
+                Cs.append(g.counts().astype(np.float64))
+        res[mode] = (np.array(Ts), np.array(Cs))
+    (Tb, Cb), (Tn, Cn) = res[rt.REEMIT_BW], res[rt.REEMIT_NOCORR]
+    mb, mn = Tb.mean(axis=0), Tn.mean(axis=0)
+    se = np.sqrt(Tb.var(axis=0, ddof=1) / runs + Tn.var(axis=0, ddof=1) / runs)
+    big = (Cb.mean(axis=0) > 1e4) & (Cn.mean(axis=0) > 1e4)
+    d = np.abs(mb - mn)[big]
+    rel = d / mb[big]
+    print(f"{int(big.sum())} cells above 1e4 counts: max relative difference {rel.max():.4f}, "
+          f"max |d|/se {float((d / se[big]).max()):.2f}")
+    assert big.sum() > 50
+    assert np.all((rel <= 5e-3) | (d <= 4 * se[big]))
+    small = (Cb.mean(axis=0) > 0) & (Cb.mean(axis=0) < 30)
+    print(f"cells below 30 counts: mean T ratio no-correction / BW "
+          f"{float((mn[small] / mb[small]).mean()):.4f}")
