@@ -297,11 +297,11 @@ PROFILE_SOURCES = ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                    "paper_1201_3588_gb300/csrc/rt_internal.h")
 PROFILE = {
     # 1-pass counters of one 2e7-package launch on the full large disk (path walk):
-    # dram 292.27 GB read + 0.12 GB written; 6.889e10 warp and 1.111e12 thread
+    # dram 174.65 GB read + 0.11 GB written; 6.964e10 warp and 1.057e12 thread
     # instructions over 5.24e9 crossings
-    "large_disk": {"sha256": "0bb87f54571fab1d8125cf1b2ad3721fa80032214808ec8e6740f9edef8e0f89",
-                   "dram_bytes_per_package": 14619.7, "warp_lanes_active": 16.13,
-                   "warp_instr_per_crossing": 13.14,
+    "large_disk": {"sha256": "f477e8395bd46d988f5a9c909d748e50ae09aa1f09ec1844afdec6c3eabbce9e",
+                   "dram_bytes_per_package": 8738.0, "warp_lanes_active": 15.17,
+                   "warp_instr_per_crossing": 13.28,
                    "file": "profiles/k_transport_pool_large_disk.md"},
     # the same counters of one 1e8-package launch on the flared disk (linked walk):
     # dram 103.91 GB read + 0.24 GB written; 1.493e11 warp and 2.539e12 thread
@@ -344,15 +344,44 @@ def crossing_bytes(c, S, L):
     return c["crossings"] * (4 + 4 * L + 4 * S) + 16 * c["absorptions"]
 
 
-def walk_bytes(c, S):
-    """Bytes the linked walk itself reads per launch: every cell entered reads its
-    face link (4 B) and S densities (4 B each), every descent into a finer neighbour
-    one child id (4 B); every absorption is one 8-byte read-modify-write of a count
-    (16 B). Peel-off: every cell a sight line crosses reads the same link and
-    densities, every peeled event adds into an FP64 pixel (16 B)."""
-    entered = c["crossings"] + c["absorptions"] + c["scatters"] + c["capped"]
-    return (entered * (4 + 4 * S) + 4 * c["levels"] + 16 * c["absorptions"]
+def walk_bytes(c, S, path=False):
+    """Bytes the walk that ran reads per launch. Linked walk: every cell entered reads
+    its face link (4 B) and S densities (4 B each), every descent into a finer
+    neighbour one child id (4 B). Path walk: every crossing reads one slot row (S
+    densities or a block code, 4 B each), every level descended one more row (the
+    `levels` counter), every interaction the leaf id (4 B) and its densities. Both:
+    every absorption is one 8-byte read-modify-write of a count (16 B). Peel-off:
+    every cell a sight line crosses reads a link and densities, every peeled event
+    adds into an FP64 pixel (16 B)."""
+    events = c["absorptions"] + c["scatters"] + c["capped"]
+    if path:
+        walk = 4 * S * (c["crossings"] + c["levels"]) + (4 + 4 * S) * events
+    else:
+        walk = (c["crossings"] + events) * (4 + 4 * S) + 4 * c["levels"]
+    return (walk + 16 * c["absorptions"]
             + c.get("peel_crossings", 0) * (4 + 4 * S) + 16 * c.get("peel_events", 0))
+
+
+def grid_bytes(model, path):
+    """Device bytes of the grid arrays the transport reads and of the counts:
+    densities, levels, the walk's own array (slot rows for the path walk, face-link
+    records for the linked walk), tree, counts."""
+    t = model.tree
+    N, S = t.n_leaves, model.n_species
+    slots = t.n_base ** 3 + 8 * t.n_blocks
+    walk = 4 * S * slots if path else 32 * N
+    return 4 * N * S + N + walk + 4 * slots + 8 * N * S
+
+
+def path_walk_runs(walk, N, S, L, n_slots, images=False):
+    """Whether the pool kernel runs the path walk (the same rule as rt_transport):
+    walk is rt.WALK_* (0 automatic), n_slots the tree's base cells plus 8 per block."""
+    fits = L <= 4 and n_slots < 2 ** 31 - 1
+    if images or not fits:
+        return False
+    if walk == 0:
+        return S == 4 or 32 * N > 4e9
+    return walk == 2
 
 
 def walk_label(choice, N, S, L):
@@ -564,6 +593,8 @@ def run_ours(args):
     kmean = sum(kern_s) / len(kern_s)
     bytes_launch = crossing_bytes(c, S, L)
     achieved = bytes_launch / kmean / 1e9
+    path = path_walk_runs(opts.get("walk", WALKS[args.walk]), N, S, L,
+                          model.tree.n_base ** 3 + 8 * model.tree.n_blocks, images)
     prof = profile_figures(args.workload)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm,
@@ -573,8 +604,9 @@ def run_ours(args):
             "kernel_ms": 1e3 * kmean,
             "bytes_per_crossing": 4 + 4 * L + 4 * S,
             "algorithmic_bytes_per_launch": bytes_launch,
-            "linked_walk_bytes_per_launch": walk_bytes(c, S),
-            "linked_walk_frac": walk_bytes(c, S) / kmean / 1e9 / hbm}
+            "walk": "path" if path else "linked",
+            "walk_bytes_per_launch": walk_bytes(c, S, path),
+            "walk_frac": walk_bytes(c, S, path) / kmean / 1e9 / hbm}
     if prof:
         roof["warp_lanes_active_per_instruction"] = prof["warp_lanes_active"]
         roof["warp_execution_efficiency"] = prof["warp_lanes_active"] / 32.0
@@ -626,7 +658,7 @@ def run_ours(args):
                                (" + BF16 tcgen05 PAH surrogate with exact fallback"
                                 if pah else ""),
                        "l2": f"inputs larger than L2: grid + counts "
-                             f"{(4 * N * S + N + 32 * N + 8 * N * S) / 2**20:.0f} MiB > 129 MiB"},
+                             f"{grid_bytes(model, path) / 2**20:.0f} MiB > 129 MiB"},
             "roofline": roof,
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_cores,
                              "kind": "oracle",

@@ -110,11 +110,14 @@ typedef struct rt_run_opts {
 /* How the pool kernel finds the next cell. LINKED reads the leaf's face-link record
  * (one dependent read per crossing; the record also holds the densities of up to two
  * species); PATH climbs the package's own stack of the blocks on its path to the
- * common ancestor with the neighbour and descends from there (no link records; for
- * grids of at most 4 levels). Both give the same histories. AUTO takes the path walk
- * for four species, and for any species count when the records exceed 4 GB: its
- * randomly read arrays (densities and child table) are smaller, which costs less
- * address translation on large grids. */
+ * common ancestor with the neighbour and descends from there, reading one row per
+ * slot of the tree (every base cell and block child: a leaf's densities, or the code
+ * of the block below it) -- one read per crossing, one more per level descended (no
+ * link records; grids of at most 4 levels whose base cells plus 8 x blocks fit an
+ * int32). Both give the same histories. AUTO takes the path walk for four species,
+ * and for any species count when the link records exceed 4 GB: its randomly read
+ * array, (n^3 + 8 n_blocks) x S floats, is smaller, which costs less address
+ * translation on large grids. */
 enum { RT_WALK_AUTO = 0, RT_WALK_LINKED = 1, RT_WALK_PATH = 2 };
 
 /* Lucy (1999) path-length estimator: every cell segment a package crosses adds
@@ -126,8 +129,9 @@ enum { RT_EST_PATHLENGTH = 1 };
 typedef struct rt_counters {
     uint64_t emitted, escaped, capped, absorptions, scatters, crossings, errors;
     uint64_t clamped;       /* absorptions whose energy lay beyond the table's t_max */
-    uint64_t levels;        /* sum over cells entered (crossed or interacted in) of the
-                               cell's refinement level: child-table reads of the walk */
+    uint64_t levels;        /* tree reads below the base cubes: for the linked and plain
+                               walks the sum of the refinement levels of the cells
+                               entered; for the path walk the block-slot rows read */
     uint64_t peel_events;   /* scatterings and re-emissions sent toward the observer */
     uint64_t peel_crossings;/* cells crossed by their sight lines (and the source's) */
     uint64_t peel_dropped;  /* events beyond the event buffer's capacity (not imaged) */
@@ -136,9 +140,11 @@ typedef struct rt_counters {
 /* Create a grid handle: copies the tree and densities to the device and walks the
  * tree there, level by level, to find every leaf's level and corner and build its
  * face links (deferred to the first call that reads them -- a linked-walk transport,
- * peel-off images, a replay, a batch -- when the automatic walk is the path walk). RT_ERR_ARG when a leaf or block is reached twice or never, an id is
- * out of range, a block lies at max_level or deeper, or a density is negative or
- * not finite. Synchronises. */
+ * peel-off images, a replay, a batch -- when the automatic walk is the path walk).
+ * The path walk's slot rows are built here when it is the automatic walk, else by
+ * the first transport that takes it (which then synchronises). RT_ERR_ARG when a
+ * leaf or block is reached twice or never, an id is out of range, a block lies at
+ * max_level or deeper, or a density is negative or not finite. Synchronises. */
 rt_status rt_grid_create(const rt_grid_desc *d, rt_grid **out);
 
 /* Release every resource of the handle. NULL is accepted. */

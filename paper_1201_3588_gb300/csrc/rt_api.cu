@@ -30,6 +30,7 @@ struct rt_grid {
   float* d_rho = nullptr;
   int8_t* d_level = nullptr;
   int32_t* d_links = nullptr;
+  float* d_rho_slot = nullptr;  // densities by tree slot (path walk)
   unsigned long long* d_count = nullptr;
   unsigned long long* d_sed = nullptr;
   unsigned long long* d_counters = nullptr;
@@ -169,6 +170,13 @@ void free_tables(rt_grid* g) {
   g->tables_ready = false;
 }
 
+// The path walk serves grids of at most four levels whose tree slots (base cells and
+// block children) an int indexes.
+static bool path_walk_fits(const rt_grid_desc* d) {
+  const double nb = (double)d->n_base * d->n_base * d->n_base;
+  return d->max_level <= 4 && nb + 8.0 * (double)d->n_blocks < 2147483647.0;
+}
+
 void free_all(rt_grid* g) {
   free_tables(g);
   dfree(g->d_base);
@@ -176,6 +184,7 @@ void free_all(rt_grid* g) {
   dfree(g->d_rho);
   dfree(g->d_level);
   dfree(g->d_links);
+  dfree(g->d_rho_slot);
   dfree(g->d_count);
   dfree(g->d_sed);
   dfree(g->d_counters);
@@ -486,10 +495,12 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   ALLOC(g->d_rho, (size_t)S * N);
   ALLOC(g->d_level, (size_t)N);
   // face links only where the automatic walk reads them (built below); otherwise on
-  // the first call that needs them (ensure_links)
-  const bool links_now = !(d->max_level <= 4 &&
-                           (S == 4 || 4.0 * kRec * (double)N > 4.0e9));
+  // the first call that needs them (ensure_links). The path walk's densities by tree
+  // slot likewise: now where it is the automatic walk, else on first use.
+  const bool path_auto = path_walk_fits(d) && (S == 4 || 4.0 * kRec * (double)N > 4.0e9);
+  const bool links_now = !path_auto;
   if (links_now) ALLOC(g->d_links, (size_t)N * kRec);
+  if (path_auto) ALLOC(g->d_rho_slot, (size_t)S * (nb + 8 * d->n_blocks));
   ALLOC(g->d_count, (size_t)S * N);
   ALLOC(g->d_sed, (size_t)2 * d->n_sed_dirs * B);
   ALLOC(g->d_counters, (size_t)kNumCounters);
@@ -564,6 +575,8 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   g->g.rho = g->d_rho;
   g->g.level = g->d_level;
   g->g.links = g->d_links;
+  g->g.rho_slot = g->d_rho_slot;
+  g->g.n_base3 = (int)nb;
   g->g.n_leaves = N;
   g->g.n_blocks = d->n_blocks;
   g->g.n_base = d->n_base;
@@ -574,6 +587,7 @@ rt_status rt_grid_create(const rt_grid_desc* d, rt_grid** out) {
   g->g.n_T = g->desc.n_temp;
   // face links of every leaf, built on the device from the leaf corners
   if (links_now) e = launch_build_links(g->g, d_ijk, g->d_links, nullptr);
+  if (path_auto && e == cudaSuccess) e = launch_build_rho_slot(g->g, g->d_rho_slot, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   free_work();
   if (e != cudaSuccess) {
@@ -637,6 +651,25 @@ static rt_status ensure_links(rt_grid* g) {
     return st;
   }
   g->g.links = g->d_links;
+  return RT_OK;
+}
+
+// The path walk's densities by tree slot, built when a path-walk transport first
+// needs them. Synchronises.
+static rt_status ensure_rho_slot(rt_grid* g) {
+  if (g->d_rho_slot) return RT_OK;
+  const long long n_slots = (long long)g->g.n_base3 + 8 * g->desc.n_blocks;
+  rt_status st = dalloc(&g->d_rho_slot, (size_t)g->desc.n_species * n_slots);
+  if (st != RT_OK) return st;
+  g->g.rho_slot = g->d_rho_slot;
+  cudaError_t e = launch_build_rho_slot(g->g, g->d_rho_slot, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    dfree(g->d_rho_slot);
+    g->d_rho_slot = nullptr;
+    g->g.rho_slot = nullptr;
+    return RT_ERR_CUDA;
+  }
   return RT_OK;
 }
 
@@ -800,7 +833,7 @@ static rt_status fill_run(rt_grid* g, uint64_t n_packages, uint64_t seed, uint64
 // from 1.9e7 to 1.7e8 cells) and whenever the face-link records exceed 4 GB; grids
 // deeper than the path walk serves keep the links.
 static bool use_path_walk(const rt_grid* g, const rt_run_opts* o) {
-  if (g->desc.max_level > 4) return false;
+  if (!path_walk_fits(&g->desc)) return false;
   const int w = o ? o->walk : RT_WALK_AUTO;
   if (w == RT_WALK_PATH) return true;
   if (w == RT_WALK_LINKED) return false;
@@ -835,11 +868,12 @@ rt_status rt_transport(rt_grid* g, uint64_t n_packages, uint64_t seed,
   if (g->images && kernel != RT_KERNEL_POOL) return RT_ERR_STATE;
   if (kernel == RT_KERNEL_POOL) {
     // the path walk runs without images and without the path-length tally
-    if ((g->images || r.pathabs || !use_path_walk(g, o)) && (st = ensure_links(g)) != RT_OK)
-      return st;
+    const bool path = !g->images && !r.pathabs && use_path_walk(g, o);
+    if (!path && (st = ensure_links(g)) != RT_OK) return st;
+    if (path && (st = ensure_rho_slot(g)) != RT_OK) return st;
     RT_CUDA(cudaMemsetAsync(g->d_next, 0, sizeof(unsigned long long), s));
     RT_CUDA(launch_transport_pool(g->g, t, r, o ? o->blocks_per_sm : 0, threads, s,
-                                  g->images ? &g->peel : nullptr, use_path_walk(g, o)));
+                                  g->images ? &g->peel : nullptr, path));
     if (g->images) {
       RT_CUDA(launch_peel_source(g->g, t, r, g->peel, s));
       RT_CUDA(launch_peel_trace(g->g, t, r, g->peel, s));

@@ -39,8 +39,12 @@ struct DevGrid {
   const float* rho;        // [n_leaves][S]: density times the base-cube edge, g cm^-2
   const int8_t* level;     // [n_leaves] refinement level of every leaf
   const int32_t* links;    // [n_leaves][8] face links (+ densities when S <= 2)
+  // densities by tree slot for the path walk: [n_base^3 + 8 n_blocks][S], slot i < n^3
+  // the base cell i, slot n^3 + 8 b + o the child o of block b; zeros where refined
+  const float* rho_slot;
   long long n_leaves, n_blocks;
   int n_base, max_level, S, B, n_dir, n_T;
+  int n_base3;             // n_base^3, the first block slot
 };
 
 // Face-link record of a leaf, 8 words (32 bytes): links of faces -x,+x,-y,+y,-z,+z,
@@ -173,6 +177,7 @@ cudaError_t launch_trace(const DevGrid& g, const DevTables& t, const DevRun& r,
                          long long* ev_n = nullptr);
 cudaError_t launch_build_links(const DevGrid& g, const int32_t* leaf_ijk, int32_t* links,
                                cudaStream_t s);
+cudaError_t launch_build_rho_slot(const DevGrid& g, float* rho_slot, cudaStream_t s);
 
 // Device walk of the tree (rt_grid.cu): inputs, outputs and work arrays.
 struct TreeBuild {

@@ -461,7 +461,8 @@ __device__ __forceinline__ int advance_linked(Pkg<float>& k, Cell& c, const DevG
 constexpr int kPathLevels = 4;  // the path walk serves grids of at most 4 levels
 
 struct PathCell {
-  int leaf;
+  int slot;  // tree slot of the leaf: its row in rho_slot
+  float kx;  // the leaf's extinction at the package's bin, or -1 when not yet read
   float lo[3];
   float sz;  // 2^-level
   int b1, b2, b3, b4;
@@ -489,7 +490,8 @@ __device__ __forceinline__ int enter_path(const Pkg<float>& k, const DevGrid& g,
     I[a] = cell_index(k.p[a], k.d[a]);
     if (I[a] < 0 || I[a] >= n) return 1;
   }
-  int node = __ldg(&g.base[I[0] + n * (I[1] + n * I[2])]);
+  int slot = I[0] + n * (I[1] + n * I[2]);
+  int node = __ldg(&g.base[slot]);
   int lev = 0;
   while (node < 0) {
     const long long blk = -(long long)node - 1;
@@ -506,19 +508,63 @@ __device__ __forceinline__ int enter_path(const Pkg<float>& k, const DevGrid& g,
       oct |= o << a;
       I[a] = j;
     }
+    slot = g.n_base3 + (int)blk * 8 + oct;
     node = __ldg(&g.child[blk * 8 + oct]);
     ++child_reads;
   }
   if ((long long)node >= g.n_leaves) return -1;
-  c.leaf = node;
+  c.slot = slot;
+  c.kx = -1.f;
   c.sz = __int_as_float((127 - lev) << 23);
 #pragma unroll
   for (int a = 0; a < 3; ++a) c.lo[a] = (float)I[a] * c.sz;
   return 0;
 }
 
-// One cell of the path walk (kS: 2 or 4 species read as one vector from rho, 0 the
-// generic loop).
+// The row of a tree slot as one vector (kS = 4 or 2 species; the generic form reads
+// the first word here and the rest in slot_ext): a leaf's densities, or for a refined
+// slot the child block's code -(block + 1) in the first word (densities are >= +0, so
+// the sign bit tells them apart); and the extinction sum over species at the bin's
+// opacities kb.
+template <int kS>
+__device__ __forceinline__ float4 slot_row(const DevGrid& g, int slot) {
+  if constexpr (kS == 4) {
+    return __ldg(reinterpret_cast<const float4*>(g.rho_slot) + slot);
+  } else if constexpr (kS == 2) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(g.rho_slot) + slot);
+    return make_float4(v.x, v.y, 0.f, 0.f);
+  } else {
+    return make_float4(__ldg(&g.rho_slot[(size_t)slot * g.S]), 0.f, 0.f, 0.f);
+  }
+}
+
+// The leaf id of a leaf's tree slot (from the tree arrays; the walk itself reads only
+// the rows), or -1 if the slot holds no leaf.
+__device__ __forceinline__ int path_leaf(const DevGrid& g, int slot) {
+  const int node = slot < g.n_base3 ? __ldg(&g.base[slot]) : __ldg(&g.child[slot - g.n_base3]);
+  return node >= 0 && (long long)node < g.n_leaves ? node : -1;
+}
+
+template <int kS>
+__device__ __forceinline__ float slot_ext(const DevGrid& g, float4 v, int slot, const Kappa* kb) {
+  if constexpr (kS == 4) {
+    return v.x * kb[0].kext + v.y * kb[1].kext + v.z * kb[2].kext + v.w * kb[3].kext;
+  } else if constexpr (kS == 2) {
+    return v.x * kb[0].kext + v.y * kb[1].kext;
+  } else {
+    const float* rho = g.rho_slot + (size_t)slot * g.S;
+    float kx = 0.f;
+    for (int s = 0; s < g.S; ++s) kx += __ldg(&rho[s]) * kb[s].kext;
+    return kx;
+  }
+}
+
+// One cell of the path walk (kS: 2 or 4 species read as one vector, 0 the generic
+// loop). The next cell is found from the rows alone: the slot of the first node off
+// the package's path is known from the block ids it carries, and that slot's row is
+// either the leaf's densities or the code of the block to descend into -- one read
+// per crossing (one more per level descended). The extinction at the package's bin
+// is kept in the cell for the next step.
 template <int kS>
 __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const DevGrid& g,
                                             const Kappa* kap, unsigned& child_reads) {
@@ -535,18 +581,8 @@ __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const De
   const float dax = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
   const bool up = dax > 0.f;
   const Kappa* kb = kap + k.bin * (kS > 0 ? kS : g.S);
-  float kx;
-  if (kS == 4) {
-    const float4 r4 = __ldg(reinterpret_cast<const float4*>(g.rho) + c.leaf);
-    kx = r4.x * kb[0].kext + r4.y * kb[1].kext + r4.z * kb[2].kext + r4.w * kb[3].kext;
-  } else if (kS == 2) {
-    const float2 r2 = __ldg(reinterpret_cast<const float2*>(g.rho) + c.leaf);
-    kx = r2.x * kb[0].kext + r2.y * kb[1].kext;
-  } else {
-    const float* rho = g.rho + (size_t)c.leaf * g.S;
-    kx = 0.f;
-    for (int s = 0; s < g.S; ++s) kx += __ldg(&rho[s]) * kb[s].kext;
-  }
+  float kx = c.kx;
+  if (kx < 0.f) kx = slot_ext<kS>(g, slot_row<kS>(g, c.slot), c.slot, kb);
   const float dtau = kx * tex;
   if (kx > 0.f && dtau > k.tau) {
     const float sd = k.tau / kx;
@@ -571,21 +607,23 @@ __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const De
   else if (ax == 1) J1 = Jax;
   else J2 = Jax;
   const int u = 32 - __clz(Iax ^ Jax);  // levels up to the common ancestor
-  int lev, node;
+  int lev, slot;
   if (u > L) {  // another base cube
     lev = 0;
     const int n = g.n_base;
-    node = __ldg(&g.base[(J0 >> L) + n * ((J1 >> L) + n * (J2 >> L))]);
+    slot = (J0 >> L) + n * ((J1 >> L) + n * (J2 >> L));
   } else {      // the common ancestor's block holds the first node off the path
     lev = L - u + 1;
     const int sh = L - lev;
     const int oct = ((J0 >> sh) & 1) | (((J1 >> sh) & 1) << 1) | (((J2 >> sh) & 1) << 2);
-    node = __ldg(&g.child[(long long)c.blk(lev) * 8 + oct]);
+    slot = g.n_base3 + c.blk(lev) * 8 + oct;
     ++child_reads;
   }
+  float4 row = slot_row<kS>(g, slot);
+  int code = __float_as_int(row.x);
   int K0 = J0 >> (L - lev), K1 = J1 >> (L - lev), K2 = J2 >> (L - lev);
-  while (node < 0) {
-    const long long blk = -(long long)node - 1;
+  while (code < 0) {
+    const long long blk = -(long long)code - 1;
     if (blk >= g.n_blocks || lev >= g.max_level || lev >= kPathLevels) return kError;
     ++lev;
     c.set_blk(lev, (int)blk);
@@ -601,11 +639,13 @@ __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const De
       K2 = min(max(cell_index(k.p[2] * sc, d2), 2 * K2), 2 * K2 + 1);
     }
     const int oct = (K0 & 1) | ((K1 & 1) << 1) | ((K2 & 1) << 2);
-    node = __ldg(&g.child[blk * 8 + oct]);
+    slot = g.n_base3 + (int)blk * 8 + oct;
+    row = slot_row<kS>(g, slot);
+    code = __float_as_int(row.x);
     ++child_reads;
   }
-  if ((long long)node >= g.n_leaves) return kError;
-  c.leaf = node;
+  c.slot = slot;
+  c.kx = slot_ext<kS>(g, row, slot, kb);
   c.sz = __int_as_float((127 - lev) << 23);
   c.lo[0] = (float)K0 * c.sz;
   c.lo[1] = (float)K1 * c.sz;
@@ -631,7 +671,7 @@ __device__ __forceinline__ float hg_per_sr(float g, float mu) {
 template <int kS>
 __device__ __forceinline__ float cell_rho(const DevGrid& g, int leaf, int s) {
   if (kS == 2) return __int_as_float(__ldg(g.links + (size_t)leaf * kRec + 6 + s));
-  if (kS < 0) return __ldg(&g.rho[(size_t)leaf * (-kS) + s]);
+  if (kS < 0) return __ldg(&g.rho[(size_t)leaf * (size_t)(kS < 0 ? -kS : 1) + s]);
   return __ldg(&g.rho[(size_t)leaf * g.S + s]);
 }
 
@@ -1066,7 +1106,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
           atomicOr(r.status, kStatusTree);
           alive = false;
         } else {
-          pending = true;  // at the interaction point inside cell.leaf
+          pending = true;  // at the interaction point inside the cell
         }
       }
       // interaction phase, warp-uniform: once `batch` lanes wait, or nobody walks
@@ -1079,13 +1119,24 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
       bool absorbing = false;
       bool scattered = false;
       float wv = kInv4Pi;  // peel-off weight per steradian of this lane's event
+      int leaf = 0;
       if (pending) {
         pending = false;
+        if constexpr (kPath) {
+          cell.kx = -1.f;  // the bin may change: read the row again
+          leaf = path_leaf(g, cell.slot);
+        } else {
+          leaf = cell.leaf;
+        }
         if (++k.event > r.max_events) {
           ++tl.capped;
           alive = false;
+        } else if (leaf < 0) {
+          ++tl.errors;
+          atomicOr(r.status, kStatusTree);
+          alive = false;
         } else {
-          sp = interact<float, kI>(k, g, kap, cell.leaf, r, w1, kPeel ? pe->o : nullptr,
+          sp = interact<float, kI>(k, g, kap, leaf, r, w1, kPeel ? pe->o : nullptr,
                                    kPeel ? &wv : nullptr);
           if (sp < 0) {
             ++tl.scatters;
@@ -1097,19 +1148,19 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
       }
       const unsigned am = __ballot_sync(kFull, absorbing);
       if (absorbing) {
-        unsigned long long key = ((unsigned long long)sp << 48) | (unsigned long long)cell.leaf;
+        unsigned long long key = ((unsigned long long)sp << 48) | (unsigned long long)leaf;
         unsigned peers = __match_any_sync(am, key);
         int leader = __ffs(peers) - 1;
         unsigned long long old = 0;
         if (lane == leader)
-          old = atomicAdd(&r.count[(size_t)sp * g.n_leaves + cell.leaf],
+          old = atomicAdd(&r.count[(size_t)sp * g.n_leaves + leaf],
                           (unsigned long long)__popc(peers));
         old = __shfl_sync(peers, old, leader);
         if (t.pah_of[sp] >= 0)
-          pah_absorb<float>(k, g, t, r, t.pah_of[sp], cell.leaf, w1);
+          pah_absorb<float>(k, g, t, r, t.pah_of[sp], leaf, w1);
         else
-          reemit<float, kI>(k, g, t, r, sp, cell.leaf, cell.level(), old + __popc(peers & lt_mask),
-                        w1, tl);
+          reemit<float, kI>(k, g, t, r, sp, leaf, cell.level(), old + __popc(peers & lt_mask),
+                            w1, tl);
         ++tl.absorptions;
       }
       if constexpr (kPeel) {
@@ -1294,6 +1345,21 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
   rec[6] = k.bin;
   rec[7] = dir_bin(k.d[2], g.n_dir);
   for (int j = 0; j < 9; ++j) out[i * 9 + j] = rec[j];
+}
+
+// Rows by tree slot (the path walk's grid): slot i < n^3 is base cell i, slot
+// n^3 + 8 b + o the child o of block b. A leaf's row holds its densities (a -0 made
+// +0: the densities are non-negative); a refined slot's row holds the code -(block +
+// 1) of its block in the first word, zeros after it.
+__global__ void k_build_rho_slot(DevGrid g, long long n_slots, float* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n_slots) return;
+  const long long nb = g.n_base3;
+  const int node = i < nb ? g.base[i] : g.child[i - nb];
+  const bool leaf = node >= 0 && node < g.n_leaves;
+  for (int s = 0; s < g.S; ++s)
+    out[i * g.S + s] = leaf ? fabsf(g.rho[(long long)node * g.S + s])
+                            : (s == 0 && node < 0 ? __int_as_float(node) : 0.f);
 }
 
 // Face links: for each leaf and face, the neighbour across it at the leaf's level
@@ -1507,6 +1573,12 @@ cudaError_t launch_build_links(const DevGrid& g, const int32_t* leaf_ijk, int32_
                                cudaStream_t s) {
   long long n = g.n_leaves * 6;
   k_build_links<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, leaf_ijk, links);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_rho_slot(const DevGrid& g, float* rho_slot, cudaStream_t s) {
+  const long long n = (long long)g.n_base3 + 8 * g.n_blocks;
+  k_build_rho_slot<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, n, rho_slot);
   return cudaGetLastError();
 }
 
