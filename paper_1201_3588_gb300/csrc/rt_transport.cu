@@ -463,7 +463,7 @@ constexpr int kPathLevels = 4;  // the path walk serves grids of at most 4 level
 struct PathCell {
   int slot;  // tree slot of the leaf: its row in rho_slot
   float kx;  // the leaf's extinction at the package's bin, or -1 when not yet read
-  float lo[3];
+  int J[3];  // integer coordinates of the leaf's lower corner at its level
   float sz;  // 2^-level
   int b1, b2, b3, b4;
   __device__ __forceinline__ int level() const { return 127 - (__float_as_int(sz) >> 23); }
@@ -517,7 +517,7 @@ __device__ __forceinline__ int enter_path(const Pkg<float>& k, const DevGrid& g,
   c.kx = -1.f;
   c.sz = __int_as_float((127 - lev) << 23);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) c.lo[a] = (float)I[a] * c.sz;
+  for (int a = 0; a < 3; ++a) c.J[a] = I[a];
   return 0;
 }
 
@@ -545,12 +545,28 @@ __device__ __forceinline__ int path_leaf(const DevGrid& g, int slot) {
   return node >= 0 && (long long)node < g.n_leaves ? node : -1;
 }
 
+// The extinction opacities of a bin as one vector (kS = 4 or 2: from the block's
+// shared-memory copy, one 16- or 8-byte read; zeros for the generic form, which reads
+// them from the opacity records kb in slot_ext).
 template <int kS>
-__device__ __forceinline__ float slot_ext(const DevGrid& g, float4 v, int slot, const Kappa* kb) {
+__device__ __forceinline__ float4 bin_ext(const float* kext, int bin) {
   if constexpr (kS == 4) {
-    return v.x * kb[0].kext + v.y * kb[1].kext + v.z * kb[2].kext + v.w * kb[3].kext;
+    return reinterpret_cast<const float4*>(kext)[bin];
   } else if constexpr (kS == 2) {
-    return v.x * kb[0].kext + v.y * kb[1].kext;
+    const float2 e = reinterpret_cast<const float2*>(kext)[bin];
+    return make_float4(e.x, e.y, 0.f, 0.f);
+  } else {
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+template <int kS>
+__device__ __forceinline__ float slot_ext(const DevGrid& g, float4 v, int slot, float4 e,
+                                          const Kappa* kb) {
+  if constexpr (kS == 4) {
+    return v.x * e.x + v.y * e.y + v.z * e.z + v.w * e.w;
+  } else if constexpr (kS == 2) {
+    return v.x * e.x + v.y * e.y;
   } else {
     const float* rho = g.rho_slot + (size_t)slot * g.S;
     float kx = 0.f;
@@ -567,9 +583,11 @@ __device__ __forceinline__ float slot_ext(const DevGrid& g, float4 v, int slot, 
 // is kept in the cell for the next step.
 template <int kS>
 __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const DevGrid& g,
-                                            const Kappa* kap, unsigned& child_reads) {
+                                            const Kappa* kap, const float* kext,
+                                            unsigned& child_reads) {
   const float sz = c.sz;
-  const float lo0 = c.lo[0], lo1 = c.lo[1], lo2 = c.lo[2];
+  int J0 = c.J[0], J1 = c.J[1], J2 = c.J[2];
+  const float lo0 = (float)J0 * sz, lo1 = (float)J1 * sz, lo2 = (float)J2 * sz;
   const float hi0 = lo0 + sz, hi1 = lo1 + sz, hi2 = lo2 + sz;
   const float d0 = k.d[0], d1 = k.d[1], d2 = k.d[2];
   const float t0 = ((k.inv[0] > 0.f ? hi0 : lo0) - k.p[0]) * k.inv[0];
@@ -582,7 +600,7 @@ __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const De
   const bool up = dax > 0.f;
   const Kappa* kb = kap + k.bin * (kS > 0 ? kS : g.S);
   float kx = c.kx;
-  if (kx < 0.f) kx = slot_ext<kS>(g, slot_row<kS>(g, c.slot), c.slot, kb);
+  if (kx < 0.f) kx = slot_ext<kS>(g, slot_row<kS>(g, c.slot), c.slot, bin_ext<kS>(kext, k.bin), kb);
   const float dtau = kx * tex;
   if (kx > 0.f && dtau > k.tau) {
     const float sd = k.tau / kx;
@@ -596,10 +614,8 @@ __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const De
   k.p[0] = ax == 0 ? f0 : fminf(hi0, fmaxf(lo0, k.p[0] + tex * d0));
   k.p[1] = ax == 1 ? f1 : fminf(hi1, fmaxf(lo1, k.p[1] + tex * d1));
   k.p[2] = ax == 2 ? f2 : fminf(hi2, fmaxf(lo2, k.p[2] + tex * d2));
-  // integer coordinates of the leaf and of the same-size neighbour across face ax
+  // integer coordinates of the same-size neighbour across face ax
   const int L = c.level();
-  const float isz = __int_as_float((127 + L) << 23);  // 2^L
-  int J0 = (int)(lo0 * isz), J1 = (int)(lo1 * isz), J2 = (int)(lo2 * isz);
   const int Iax = ax == 0 ? J0 : (ax == 1 ? J1 : J2);
   const int Jax = up ? Iax + 1 : Iax - 1;
   if (Jax < 0 || Jax >= (g.n_base << L)) return kEscaped;
@@ -617,7 +633,6 @@ __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const De
     const int sh = L - lev;
     const int oct = ((J0 >> sh) & 1) | (((J1 >> sh) & 1) << 1) | (((J2 >> sh) & 1) << 2);
     slot = g.n_base3 + c.blk(lev) * 8 + oct;
-    ++child_reads;
   }
   float4 row = slot_row<kS>(g, slot);
   int code = __float_as_int(row.x);
@@ -645,11 +660,11 @@ __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const De
     ++child_reads;
   }
   c.slot = slot;
-  c.kx = slot_ext<kS>(g, row, slot, kb);
+  c.kx = slot_ext<kS>(g, row, slot, bin_ext<kS>(kext, k.bin), kb);
   c.sz = __int_as_float((127 - lev) << 23);
-  c.lo[0] = (float)K0 * c.sz;
-  c.lo[1] = (float)K1 * c.sz;
-  c.lo[2] = (float)K2 * c.sz;
+  c.J[0] = K0;
+  c.J[1] = K1;
+  c.J[2] = K2;
   return kCrossed;
 }
 
@@ -1022,7 +1037,8 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
                                           unsigned long long* sed, unsigned long long n_end,
                                           Ids& ids, Tally& tl, unsigned long long t0,
                                           const DevPeel* pe = nullptr,
-                                          unsigned long long* s_nemit = nullptr) {
+                                          unsigned long long* s_nemit = nullptr,
+                                          const float* kext = nullptr) {
   const int B = g.B;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -1088,7 +1104,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
         // (launched only then)
         int a;
         if constexpr (kPath)
-          a = advance_path<kS>(k, cell, g, kap, tl.levels);
+          a = advance_path<kS>(k, cell, g, kap, kext, tl.levels);
         else
           a = advance_linked<false, kS>(k, cell, g, kap, tl.levels,
                                         kS > 0 ? nullptr : r.pathabs);
@@ -1186,6 +1202,13 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
   }
 }
 
+// Shared-memory words (floats) of the path walk's per-bin extinction vectors: B x kS
+// for 2 or 4 species, rounded up to 16 bytes; none otherwise.
+template <int kS, bool kPath>
+__host__ __device__ constexpr int kext_words(int B) {
+  return (kPath && (kS == 2 || kS == 4)) ? (B * kS + 3) / 4 * 4 : 0;
+}
+
 // ---------------------------------------------------------------- pool kernel
 // Persistent packet pool over one model: all warps draw package indices from one
 // global counter; the opacity table, the stellar CDF and (when it fits) the
@@ -1197,12 +1220,19 @@ __global__ void __launch_bounds__(256, kMinBlocks)
   const int S = g.S, B = g.B;
   const int n_sed = 2 * g.n_dir * B;
   const bool sed_local = r.sed_in_smem != 0;
-  unsigned long long* s_sed = sed_local ? smem_u64 : r.sed;   // [2][n_dir][B]
-  Kappa* s_kap = reinterpret_cast<Kappa*>(smem_u64 + (sed_local ? n_sed : 0));  // [B][S]
+  // the path walk with 2 or 4 species: the extinction opacities [B][S] first, one
+  // vector per bin (a multiple of 16 bytes)
+  float* s_kext = reinterpret_cast<float*>(smem_u64);
+  const int n_kext = kext_words<kS, kPath>(B);
+  unsigned long long* s_u64 = smem_u64 + n_kext / 2;
+  unsigned long long* s_sed = sed_local ? s_u64 : r.sed;   // [2][n_dir][B]
+  Kappa* s_kap = reinterpret_cast<Kappa*>(s_u64 + (sed_local ? n_sed : 0));  // [B][S]
   float* s_cdf = reinterpret_cast<float*>(s_kap + B * S);     // [B]
   if (sed_local)
     for (int i = threadIdx.x; i < n_sed; i += blockDim.x) s_sed[i] = 0ull;
   for (int i = threadIdx.x; i < B * S; i += blockDim.x) s_kap[i] = t.kap[i];
+  if (n_kext)
+    for (int i = threadIdx.x; i < B * S; i += blockDim.x) s_kext[i] = t.kap[i].kext;
   for (int i = threadIdx.x; i < B; i += blockDim.x) s_cdf[i] = t.star_cdf[i];
   // peel-off: the block's point-source emission counts per bin
   unsigned long long* s_nemit = nullptr;
@@ -1215,8 +1245,7 @@ __global__ void __launch_bounds__(256, kMinBlocks)
   Tally tl = {};
   GlobalIds ids{r.next};
   pool_warp<kPeel, GlobalIds, kS, kPath>(g, t, r, s_kap, s_cdf, s_sed, r.n_packages, ids, tl,
-                                         global_ns(), &pe,
-                   s_nemit);
+                                         global_ns(), &pe, s_nemit, s_kext);
   flush_tally(tl, r.counters);
   if (sed_local || kPeel) __syncthreads();
   if (sed_local) {
@@ -1427,7 +1456,7 @@ static cudaError_t launch_pool_variant(const DevGrid& g, const DevTables& t, con
                                        const DevPeel& pe, int blocks_per_sm, int threads,
                                        int sms, cudaStream_t s) {
   DevRun rr = r;
-  const size_t extra = kPeel ? peel_smem(g) : 0;
+  const size_t extra = (kPeel ? peel_smem(g) : 0) + sizeof(float) * kext_words<kS, kPath>(g.B);
   rr.sed_in_smem = table_smem(g) + extra + sed_smem(g) <= kSmemBudget ? 1 : 0;
   size_t sm = table_smem(g) + extra + (rr.sed_in_smem ? sed_smem(g) : 0);
   cudaError_t e;
