@@ -831,24 +831,35 @@ def e2e_rate(model, n, world, first, steps, net=None, params=None, tol=0.05, max
         cells_t = torch.empty(max_cells, dtype=torch.int32, pin_memory=True)
         rows_t = torch.empty((max_cells, B), dtype=torch.float32, pin_memory=True)
         cells_host, rows_host = cells_t.numpy(), rows_t.numpy()
-    times, na = [], 0
+    times, parts, na = [], [], 0
     for k in range(steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with rt.Grid(pm) as g:
+        g = rt.Grid(pm)
+        try:
             if pah:
                 net.set_params(params)
             g.emit_star(n * world)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
             g.transport(n, seed=5000 + k, first_id=first, **(opts or {}))
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
             g.temperatures(out=T_host)
             g.sed(out=sed_host)
             if pah:
                 c, _, _ = g.pah_emission_active(mode=rt.PAH_AUTO, surrogate=net, tol=tol,
                                                 cells=cells_host, out=rows_host)
                 na = int(c.shape[0])
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+        finally:
+            g.close()
         torch.cuda.synchronize()
+        t4 = time.perf_counter()
         if k > 0:  # the first pass warms the process
-            times.append(time.perf_counter() - t0)
+            times.append(t4 - t0)
+            parts.append((t1 - t0, t2 - t1, t3 - t2, t4 - t3))
     t = model.tree
     h2d = (4 * t.n_base ** 3 + 32 * t.n_blocks + 8 * S * N + 8 * (B + 1) + 24 * S * B
            + (4 * params.size if pah else 0))
@@ -857,6 +868,8 @@ def e2e_rate(model, n, world, first, steps, net=None, params=None, tol=0.05, max
     return {"value": n * world / (sum(times) / len(times)), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": 1e3 * sum(times) / len(times),
+            "ms_by_part": {name: 1e3 * sum(p[i] for p in parts) / len(parts) for i, name in
+                           enumerate(("create_and_load", "transport", "outputs", "destroy"))},
             "host_buffers": "pinned"}
 
 

@@ -635,8 +635,8 @@ __device__ __forceinline__ int advance_path(Pkg<float>& k, PathCell& c, const De
     slot = g.n_base3 + c.blk(lev) * 8 + oct;
   }
   float4 row = slot_row<kS>(g, slot);
-  int code = __float_as_int(row.x);
   int K0 = J0 >> (L - lev), K1 = J1 >> (L - lev), K2 = J2 >> (L - lev);
+  int code = __float_as_int(row.x);
   while (code < 0) {
     const long long blk = -(long long)code - 1;
     if (blk >= g.n_blocks || lev >= g.max_level || lev >= kPathLevels) return kError;
@@ -682,17 +682,18 @@ __device__ __forceinline__ float hg_per_sr(float g, float mu) {
 // per steradian toward the unit vector peel_o, at the direction before the turn.
 // kS: the species count when fixed at compile time (2: the densities come from the
 // cell's face-link record, which the linked walk has just read; -2 or -4: from the
-// density array, which the path walk has just read), 0 when read from the grid.
+// slot row, which the path walk has just read), 0 when read from the grid. `row` is
+// the leaf id, or for the path walk (kS < 0) the leaf's tree slot.
 template <int kS>
-__device__ __forceinline__ float cell_rho(const DevGrid& g, int leaf, int s) {
-  if (kS == 2) return __int_as_float(__ldg(g.links + (size_t)leaf * kRec + 6 + s));
-  if (kS < 0) return __ldg(&g.rho[(size_t)leaf * (size_t)(kS < 0 ? -kS : 1) + s]);
-  return __ldg(&g.rho[(size_t)leaf * g.S + s]);
+__device__ __forceinline__ float cell_rho(const DevGrid& g, int row, int s) {
+  if (kS == 2) return __int_as_float(__ldg(g.links + (size_t)row * kRec + 6 + s));
+  if (kS < 0) return __ldg(&g.rho_slot[(size_t)row * (size_t)(kS < 0 ? -kS : 1) + s]);
+  return __ldg(&g.rho[(size_t)row * g.S + s]);
 }
 
 template <typename R, int kS = 0>
 __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa* kap,
-                                        int leaf, const DevRun& r, uint4& w1,
+                                        int row, const DevRun& r, uint4& w1,
                                         const float* peel_o = nullptr,
                                         float* peel_w = nullptr) {
   uint4 w0 = draw(r.seed, k.id, k.event, 0u);
@@ -701,7 +702,7 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
   const Kappa* kb = kap + k.bin * S;
   float ksca = 0.f, kext = 0.f, kabs = 0.f;
   for (int s = 0; s < S; ++s) {
-    const float rs = cell_rho<kS>(g, leaf, s);
+    const float rs = cell_rho<kS>(g, row, s);
     ksca += rs * kb[s].ksca;
     kext += rs * kb[s].kext;
     kabs += rs * kb[s].kabs;
@@ -713,7 +714,7 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
     const float target = xs * ksca;
     float cum = 0.f;
     for (int s = 0; s < S; ++s) {
-      cum += cell_rho<kS>(g, leaf, s) * kb[s].ksca;
+      cum += cell_rho<kS>(g, row, s) * kb[s].ksca;
       if (cum > target) { sp = s; break; }
     }
     if (peel_w)
@@ -728,7 +729,7 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
   const float target = xs * kabs;
   float cum = 0.f;
   for (int s = 0; s < S; ++s) {
-    cum += cell_rho<kS>(g, leaf, s) * kb[s].kabs;
+    cum += cell_rho<kS>(g, row, s) * kb[s].kabs;
     if (cum > target) { sp = s; break; }
   }
   isotropic<R>(unit<R>(w0.z), unit<R>(w0.w), k.d);
@@ -741,11 +742,11 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
 // absorption count (the count before it); draw the new bin.
 template <typename R, int kS = 0>
 __device__ __forceinline__ void reemit(Pkg<R>& k, const DevGrid& g, const DevTables& t,
-                                       const DevRun& r, int s, int leaf, int level,
+                                       const DevRun& r, int s, int leaf, int row, int level,
                                        unsigned long long n, const uint4& w1,
                                        Tally& tl) {
   float xu = unit<float>(w1.y), xb = unit<float>(w1.z);
-  float rho = cell_rho<kS>(g, leaf, s);
+  float rho = cell_rho<kS>(g, row, s);
   float u;
   if (r.mode == 0) {
     float e = r.count_scale * t.eps_d0_over_V[level] / rho;
@@ -771,9 +772,9 @@ __device__ __forceinline__ void reemit(Pkg<R>& k, const DevGrid& g, const DevTab
     while (i + 1 < nI && __ldg(&S[i + 1]) <= u) ++i;
   }
   // first bin whose cumulative value exceeds xb: guide start, then scan
-  const size_t row = ((size_t)s * nI + i) * g.B;
-  const float* cdf = t.dcdf + row;
-  int b = __ldg(&t.cdf_guide[row + min((int)(xb * (float)g.B), g.B - 1)]);
+  const size_t cdf_row = ((size_t)s * nI + i) * g.B;
+  const float* cdf = t.dcdf + cdf_row;
+  int b = __ldg(&t.cdf_guide[cdf_row + min((int)(xb * (float)g.B), g.B - 1)]);
   while (b > 0 && __ldg(&cdf[b - 1]) > xb) --b;
   while (__ldg(&cdf[b]) <= xb) ++b;
   k.bin = b;
@@ -992,7 +993,7 @@ __global__ void __launch_bounds__(256) k_transport_plain(DevGrid g, DevTables t,
       if (t.pah_of[s] >= 0)
         pah_absorb<R>(k, g, t, r, t.pah_of[s], leaf, w1);
       else
-        reemit<R>(k, g, t, r, s, leaf, level, n, w1, tl);
+        reemit<R>(k, g, t, r, s, leaf, leaf, level, n, w1, tl);
       ++tl.absorptions;
     }
   }
@@ -1135,14 +1136,16 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
       bool absorbing = false;
       bool scattered = false;
       float wv = kInv4Pi;  // peel-off weight per steradian of this lane's event
-      int leaf = 0;
+      int leaf = 0, row = 0;  // the cell's leaf id; its density row (leaf or slot)
       if (pending) {
         pending = false;
         if constexpr (kPath) {
           cell.kx = -1.f;  // the bin may change: read the row again
           leaf = path_leaf(g, cell.slot);
+          row = kI < 0 ? cell.slot : leaf;  // slot rows for 2 or 4 species
         } else {
           leaf = cell.leaf;
+          row = leaf;
         }
         if (++k.event > r.max_events) {
           ++tl.capped;
@@ -1152,7 +1155,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
           atomicOr(r.status, kStatusTree);
           alive = false;
         } else {
-          sp = interact<float, kI>(k, g, kap, leaf, r, w1, kPeel ? pe->o : nullptr,
+          sp = interact<float, kI>(k, g, kap, row, r, w1, kPeel ? pe->o : nullptr,
                                    kPeel ? &wv : nullptr);
           if (sp < 0) {
             ++tl.scatters;
@@ -1175,7 +1178,7 @@ __device__ __forceinline__ void pool_warp(const DevGrid& g, const DevTables& t, 
         if (t.pah_of[sp] >= 0)
           pah_absorb<float>(k, g, t, r, t.pah_of[sp], leaf, w1);
         else
-          reemit<float, kI>(k, g, t, r, sp, leaf, cell.level(), old + __popc(peers & lt_mask),
+          reemit<float, kI>(k, g, t, r, sp, leaf, row, cell.level(), old + __popc(peers & lt_mask),
                             w1, tl);
         ++tl.absorptions;
       }
@@ -1364,7 +1367,7 @@ __global__ void k_trace(DevGrid g, DevTables t, DevRun r, const unsigned long lo
     if (t.pah_of[s] >= 0) {
       pah_bin(k, g, t, t.pah_of[s], c.leaf, w1);  // replay does not tally
     } else {
-      reemit<float>(k, g, t, r, s, c.leaf, c.level(), 0ull, w1, tl);
+      reemit<float>(k, g, t, r, s, c.leaf, c.leaf, c.level(), 0ull, w1, tl);
     }
     trace_event(my_ev, ev_cap, n_ev, 2, s, c.leaf, k.bin, pi);
     ++rec[1];
