@@ -297,18 +297,18 @@ PROFILE_SOURCES = ("paper_1201_3588_gb300/csrc/rt_transport.cu",
                    "paper_1201_3588_gb300/csrc/rt_internal.h")
 PROFILE = {
     # 1-pass counters of one 2e7-package launch on the full large disk (path walk):
-    # dram 174.65 GB read + 0.11 GB written; 6.964e10 warp and 1.057e12 thread
+    # dram 174.27 GB read + 0.11 GB written; 6.759e10 warp and 1.053e12 thread
     # instructions over 5.24e9 crossings
-    "large_disk": {"sha256": "f477e8395bd46d988f5a9c909d748e50ae09aa1f09ec1844afdec6c3eabbce9e",
-                   "dram_bytes_per_package": 8738.0, "warp_lanes_active": 15.17,
-                   "warp_instr_per_crossing": 13.28,
+    "large_disk": {"sha256": "37df585bc0db86db4b62d16c47608a40489a74d084f398b36c592e962be6373b",
+                   "dram_bytes_per_package": 8718.9, "warp_lanes_active": 15.58,
+                   "warp_instr_per_crossing": 12.89,
                    "file": "profiles/k_transport_pool_large_disk.md"},
     # the same counters of one 1e8-package launch on the flared disk (linked walk):
-    # dram 103.91 GB read + 0.24 GB written; 1.493e11 warp and 2.539e12 thread
+    # dram 103.92 GB read + 0.24 GB written; 1.496e11 warp and 2.543e12 thread
     # instructions over 1.41e10 crossings
-    "disk": {"sha256": "0bb87f54571fab1d8125cf1b2ad3721fa80032214808ec8e6740f9edef8e0f89",
-             "dram_bytes_per_package": 1041.5, "warp_lanes_active": 17.0,
-             "warp_instr_per_crossing": 10.6, "file": "profiles/k_transport_pool_disk.md"},
+    "disk": {"sha256": "37df585bc0db86db4b62d16c47608a40489a74d084f398b36c592e962be6373b",
+             "dram_bytes_per_package": 1041.6, "warp_lanes_active": 17.0,
+             "warp_instr_per_crossing": 10.62, "file": "profiles/k_transport_pool_disk.md"},
 }
 
 
