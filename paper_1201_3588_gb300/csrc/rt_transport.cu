@@ -112,11 +112,13 @@ __device__ __forceinline__ R hg_mu(R g, R xi) {
   return fmin((R)1, fmax((R)-1, mu));
 }
 
-// turn d by polar cosine mu (s = sin of the polar angle) and azimuth phi (sp, cp =
-// sin, cos phi), azimuth counted from (dx dz, dy dz, -(1-dz^2))/sqrt(1-dz^2) towards
-// (-dy, dx, 0)/sqrt(1-dz^2)
+// turn d by polar cosine mu and azimuth 2 pi xphi, azimuth counted from
+// (dx dz, dy dz, -(1-dz^2))/sqrt(1-dz^2) towards (-dy, dx, 0)/sqrt(1-dz^2)
 template <typename R>
-__device__ __forceinline__ void turn(R d[3], R mu, R s, R sp, R cp) {
+__device__ __forceinline__ void turn(R d[3], R mu, R xphi) {
+  R s = sqrt(fmax((R)0, (R)1 - mu * mu));
+  R sp, cp;
+  sincos2pi(xphi, &sp, &cp);
   R ux = d[0], uy = d[1], uz = d[2], nx, ny, nz;
   if (fabs(uz) > (R)0.99999) {
     nx = s * cp;
@@ -697,54 +699,43 @@ __device__ __forceinline__ int interact(Pkg<R>& k, const DevGrid& g, const Kappa
   uint4 w0 = draw(r.seed, k.id, k.event, 0u);
   w1 = draw(r.seed, k.id, k.event, 1u);
   const int S = kS > 0 ? kS : (kS < 0 ? -kS : g.S);
-  constexpr int kSc = kS > 0 ? kS : -kS;  // species count when fixed at compile time
   const Kappa* kb = kap + k.bin * S;
-  float rs[kSc > 0 ? kSc : 1];
   float ksca = 0.f, kext = 0.f, kabs = 0.f;
   for (int s = 0; s < S; ++s) {
-    const float rho = cell_rho<kS>(g, row, s);
-    if constexpr (kSc > 0) rs[s] = rho;
-    ksca += rho * kb[s].ksca;
-    kext += rho * kb[s].kext;
-    kabs += rho * kb[s].kabs;
+    const float rs = cell_rho<kS>(g, row, s);
+    ksca += rs * kb[s].ksca;
+    kext += rs * kb[s].kext;
+    kabs += rs * kb[s].kabs;
   }
   k.touched = true;
-  // scattering (albedo test), then the species by its share of that process; the
-  // scattering and the absorption paths share all but the turn of the direction, so
-  // lanes taking different ones diverge only there
-  const bool scat = unit<float>(w0.x) * kext < ksca;
-  const float target = unit<float>(w0.y) * (scat ? ksca : kabs);
-  static_assert(sizeof(Kappa) == 4 * sizeof(float), "Kappa is four floats");
-  const float* kproc = scat ? &kb[0].ksca : &kb[0].kabs;  // stride 4 floats per species
+  const float xs = unit<float>(w0.y);
   int sp = S - 1;
+  if (unit<float>(w0.x) * kext < ksca) {
+    const float target = xs * ksca;
+    float cum = 0.f;
+    for (int s = 0; s < S; ++s) {
+      cum += cell_rho<kS>(g, row, s) * kb[s].ksca;
+      if (cum > target) { sp = s; break; }
+    }
+    if (peel_w)
+      *peel_w = hg_per_sr(kb[sp].g, (float)k.d[0] * peel_o[0] + (float)k.d[1] * peel_o[1] +
+                                        (float)k.d[2] * peel_o[2]);
+    R mu = hg_mu<R>((R)kb[sp].g, unit<R>(w0.z));
+    turn<R>(k.d, mu, unit<R>(w0.w));
+    set_inverse(k);
+    k.tau = -log_(unit<R>(w1.x));
+    return -1;
+  }
+  const float target = xs * kabs;
   float cum = 0.f;
   for (int s = 0; s < S; ++s) {
-    float rho;
-    if constexpr (kSc > 0) rho = rs[s];
-    else rho = cell_rho<kS>(g, row, s);
-    cum += rho * kproc[4 * s];
+    cum += cell_rho<kS>(g, row, s) * kb[s].kabs;
     if (cum > target) { sp = s; break; }
   }
-  if (scat && peel_w)
-    *peel_w = hg_per_sr(kb[sp].g, (float)k.d[0] * peel_o[0] + (float)k.d[1] * peel_o[1] +
-                                      (float)k.d[2] * peel_o[2]);
-  // polar cosine: Henyey-Greenstein about the old direction after a scattering,
-  // isotropic after an absorption (re-emission); azimuth uniform
-  const R xmu = unit<R>(w0.z);
-  const R mu = scat ? hg_mu<R>((R)kb[sp].g, xmu) : (R)2 * xmu - (R)1;
-  const R sn = sqrt(fmax((R)0, (R)1 - mu * mu));
-  R sphi, cphi;
-  sincos2pi(unit<R>(w0.w), &sphi, &cphi);
-  if (scat) {
-    turn<R>(k.d, mu, sn, sphi, cphi);
-  } else {
-    k.d[0] = sn * cphi;
-    k.d[1] = sn * sphi;
-    k.d[2] = mu;
-  }
+  isotropic<R>(unit<R>(w0.z), unit<R>(w0.w), k.d);
   set_inverse(k);
   k.tau = -log_(unit<R>(w1.x));
-  return scat ? -1 : sp;
+  return sp;
 }
 
 // Interaction part 2 (absorption): n is this package's place in the cell's
