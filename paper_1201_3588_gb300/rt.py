@@ -181,11 +181,46 @@ def _stream(stream) -> Optional[int]:
     return int(stream)
 
 
-def _ptr_mem(x):
-    """(pointer, mem kind) of a numpy array or a torch tensor."""
-    if hasattr(x, "data_ptr"):
-        return x.data_ptr(), (MEM_DEVICE if x.is_cuda else MEM_HOST)
-    return x.ctypes.data, MEM_HOST
+# element types a buffer may have for each kind of array the library reads or writes
+# (torch has no unsigned 64- or 32-bit type in every version: the signed one of the
+# same width stands in)
+_KINDS = {"f32": ("float32",), "f64": ("float64",), "u64": ("uint64", "int64"),
+          "u32": ("uint32", "int32"), "i32": ("int32",)}
+
+
+def _torch_device():
+    """The current CUDA device as torch sees it, or None when torch is not in use."""
+    import sys
+    torch = sys.modules.get("torch")
+    if torch is None or not torch.cuda.is_available():
+        return None
+    return torch.cuda.current_device()
+
+
+def _buf(x, kind: str, n: int, what: str, exact: bool = False, device=None):
+    """(pointer, mem kind) of a numpy array or a torch tensor that the library will read
+    or write as n elements of `kind`: checked to be contiguous, of that element type,
+    at least (exact: exactly) n elements long and, for a CUDA tensor, on `device` when
+    that is known. ValueError before anything is handed to the library otherwise."""
+    if hasattr(x, "data_ptr"):  # torch tensor
+        dtype = str(x.dtype).replace("torch.", "")
+        numel, contiguous = int(x.numel()), bool(x.is_contiguous())
+        if x.is_cuda and device is not None and x.device.index != device:
+            raise ValueError(f"{what} is on cuda:{x.device.index}, the grid on cuda:{device}")
+        ptr, mem = x.data_ptr(), (MEM_DEVICE if x.is_cuda else MEM_HOST)
+    elif isinstance(x, np.ndarray):
+        dtype, numel, contiguous = x.dtype.name, int(x.size), bool(x.flags.c_contiguous)
+        ptr, mem = x.ctypes.data, MEM_HOST
+    else:
+        raise TypeError(f"{what} must be a numpy array or a torch tensor")
+    if dtype not in _KINDS[kind]:
+        raise ValueError(f"{what} has dtype {dtype}, not {' or '.join(_KINDS[kind])}")
+    if not contiguous:
+        raise ValueError(f"{what} must be contiguous")
+    if numel < n or (exact and numel != n):
+        raise ValueError(f"{what} holds {numel} elements, {'exactly ' if exact else ''}"
+                         f"{n} needed")
+    return ptr, mem
 
 
 class Grid:
@@ -224,6 +259,7 @@ class Grid:
                                     pah_levels, float(pah_t_top)), "rt_set_pah")
         self.n_pah = sum(1 for sp in model.species if sp.is_pah)
         self.n_coarse = min(64, self.B)
+        self.device = _torch_device()  # the device the grid lives on, when torch knows it
 
     # -- lifecycle
     def close(self):
@@ -255,7 +291,7 @@ class Grid:
     def set_frozen_temperatures(self, T, stream=None):
         if not hasattr(T, "data_ptr"):
             T = np.ascontiguousarray(T, dtype=np.float32).reshape(self.S, self.N)
-        p, mem = _ptr_mem(T)
+        p, mem = _buf(T, "f32", self.S * self.N, "T", exact=True, device=self.device)
         _check(load().rt_set_frozen_temperatures(self._h, p, mem, _stream(stream)),
                "rt_set_frozen_temperatures")
 
@@ -278,7 +314,7 @@ class Grid:
     def temperatures(self, out=None, stream=None) -> np.ndarray:
         if out is None:
             out = np.zeros((self.S, self.N), dtype=np.float32)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "f32", self.S * self.N, "out", device=self.device)
         _check(load().rt_cell_temperatures(self._h, p, mem, _stream(stream)),
                "rt_cell_temperatures")
         return out
@@ -286,7 +322,7 @@ class Grid:
     def temperatures_pathlength(self, out=None, stream=None) -> np.ndarray:
         if out is None:
             out = np.zeros((self.S, self.N), dtype=np.float32)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "f32", self.S * self.N, "out", device=self.device)
         _check(load().rt_cell_temperatures_pathlength(self._h, p, mem, _stream(stream)),
                "rt_cell_temperatures_pathlength")
         return out
@@ -294,14 +330,14 @@ class Grid:
     def pathlength(self, out=None, stream=None) -> np.ndarray:
         if out is None:
             out = np.zeros((self.S, self.N), dtype=np.float32)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "f32", self.S * self.N, "out", device=self.device)
         _check(load().rt_pathlength(self._h, p, mem, _stream(stream)), "rt_pathlength")
         return out
 
     def sed(self, out=None, stream=None):
         if out is None:
             out = np.zeros((2, self.n_dir, self.B), dtype=np.uint64)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "u64", 2 * self.n_dir * self.B, "out", device=self.device)
         eps = C.c_double()
         _check(load().rt_sed(self._h, p, mem, C.byref(eps), _stream(stream)), "rt_sed")
         return out, eps.value
@@ -309,20 +345,21 @@ class Grid:
     def counts(self, out=None, stream=None) -> np.ndarray:
         if out is None:
             out = np.zeros((self.S, self.N), dtype=np.uint64)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "u64", self.S * self.N, "out", device=self.device)
         _check(load().rt_counts(self._h, p, mem, _stream(stream)), "rt_counts")
         return out
 
     def set_counts(self, counts, stream=None):
         if not hasattr(counts, "data_ptr"):
             counts = np.ascontiguousarray(counts, dtype=np.uint64).reshape(self.S, self.N)
-        p, mem = _ptr_mem(counts)
+        p, mem = _buf(counts, "u64", self.S * self.N, "counts", exact=True, device=self.device)
         _check(load().rt_set_counts(self._h, p, mem, _stream(stream)), "rt_set_counts")
 
     def pah_absorbed(self, out=None, stream=None) -> np.ndarray:
         if out is None:
             out = np.zeros((self.n_pah, self.N, self.n_coarse), dtype=np.uint32)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "u32", self.n_pah * self.N * self.n_coarse, "out",
+                      device=self.device)
         _check(load().rt_pah_absorbed(self._h, p, mem, _stream(stream)), "rt_pah_absorbed")
         return out
 
@@ -332,7 +369,7 @@ class Grid:
         n = self.N - first if n is None else n
         if out is None:
             out = np.zeros((n, self.B), dtype=np.float32)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "f32", int(n) * self.B, "out", device=self.device)
         nf = C.c_uint64()
         _check(load().rt_pah_emission(self._h, int(first), int(n), int(pah), int(mode),
                                       surrogate._h if surrogate is not None else None,
@@ -350,8 +387,11 @@ class Grid:
         if out is None:
             cells = np.zeros(self.N, dtype=np.int32)
             out = np.zeros((self.N, self.B), dtype=np.float32)
-        pc, mc = _ptr_mem(cells)
-        p, mem = _ptr_mem(out)
+        if len(out.shape) != 2 or int(out.shape[1]) != self.B:
+            raise ValueError(f"out must be [rows][{self.B}]")
+        rows = int(out.shape[0])
+        pc, mc = _buf(cells, "i32", rows, "cells", device=self.device)
+        p, mem = _buf(out, "f32", rows * self.B, "out", exact=True, device=self.device)
         if mc != mem:
             raise ValueError("cells and out must both be host or both be device memory")
         na = C.c_int64()
@@ -373,7 +413,7 @@ class Grid:
             return
         if not hasattr(J, "data_ptr"):
             J = np.ascontiguousarray(J, dtype=np.float32).reshape(-1, self.B)
-        p, mem = _ptr_mem(J)
+        p, mem = _buf(J, "f32", int(J.shape[0]) * self.B, "J", exact=True, device=self.device)
         _check(load().rt_set_pah_spectra(self._h, int(pah), int(first), int(J.shape[0]), p, mem,
                                          _stream(stream)), "rt_set_pah_spectra")
 
@@ -405,7 +445,7 @@ class Grid:
     def images(self, out=None, stream=None) -> np.ndarray:
         if out is None:
             out = np.zeros(self.image_shape, dtype=np.float64)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "f64", int(np.prod(self.image_shape)), "out", device=self.device)
         _check(load().rt_images(self._h, p, mem, _stream(stream)), "rt_images")
         return out
 
@@ -413,7 +453,7 @@ class Grid:
                       stream=None) -> np.ndarray:
         if out is None:
             out = np.zeros(max(self.image_shape[2], 1), dtype=np.float64)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "f64", self.image_shape[2], "out", device=self.device)
         _check(load().rt_image_profile(self._h, int(plane_a), int(plane_b), int(half_rows), p,
                                        mem, _stream(stream)), "rt_image_profile")
         return out
@@ -515,7 +555,7 @@ class Batch:
         g = self.grids[model]
         if out is None:
             out = np.zeros((g.S, g.N), dtype=np.float32)
-        p, mem = _ptr_mem(out)
+        p, mem = _buf(out, "f32", g.S * g.N, "out", device=g.device)
         _check(load().rt_batch_temperatures(self._h, int(model), p, mem, _stream(stream)),
                "rt_batch_temperatures")
         return out
