@@ -45,3 +45,52 @@ def test_torch_host_tensors():
         rt._buf(torch.zeros(16, dtype=torch.float64), "f32", 16, "T")
     with pytest.raises(ValueError):
         rt._buf(torch.zeros((8, 4))[:, :2], "f32", 16, "T")
+
+
+class _NoLibrary:
+    """Stands in for the library: any call reaching it fails the test."""
+
+    def __getattr__(self, name):
+        raise AssertionError(f"{name} was called with a buffer the binding should reject")
+
+
+@pytest.fixture
+def fake_grid(monkeypatch):
+    """A Grid of 2 species, 10 cells, 4 bins, one PAH and one escape direction, with no
+    library behind it: only the checks before each call can run."""
+    g = object.__new__(rt.Grid)
+    g.S, g.N, g.B, g.n_dir, g.n_pah, g.n_coarse, g.device = 2, 10, 4, 1, 1, 4, None
+    g.image_shape = (2, 3, 5)
+    g._h = None
+    monkeypatch.setattr(rt, "load", lambda *a, **k: _NoLibrary())
+    return g
+
+
+@pytest.mark.parametrize("call", [
+    lambda g: g.temperatures(out=np.zeros((2, 10), np.float64)),
+    lambda g: g.temperatures(out=np.zeros((2, 9), np.float32)),
+    lambda g: g.temperatures_pathlength(out=np.zeros(19, np.float32)),
+    lambda g: g.pathlength(out=np.zeros((10, 2), np.float32).T),
+    lambda g: g.sed(out=np.zeros((2, 1, 3), np.uint64)),
+    lambda g: g.counts(out=np.zeros((2, 10), np.uint32)),
+    lambda g: g.pah_absorbed(out=np.zeros((1, 10, 3), np.uint32)),
+    lambda g: g.pah_emission(first=2, n=5, out=np.zeros((4, 4), np.float32)),
+    lambda g: g.pah_emission_active(cells=np.zeros(6, np.int32), out=np.zeros((6, 3), np.float32)),
+    lambda g: g.pah_emission_active(cells=np.zeros(5, np.int32), out=np.zeros((6, 4), np.float32)),
+    lambda g: g.pah_emission_active(cells=np.zeros(6, np.int64), out=np.zeros((6, 4), np.float32)),
+    lambda g: g.images(out=np.zeros((2, 3, 4), np.float64)),
+    lambda g: g.image_profile(0, out=np.zeros(4, np.float64)),
+])
+def test_grid_methods_reject_wrong_outputs(fake_grid, call):
+    with pytest.raises(ValueError):
+        call(fake_grid)
+
+
+def test_grid_inputs_must_have_the_exact_length(fake_grid):
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        fake_grid.set_counts(torch.zeros(21, dtype=torch.int64))
+    with pytest.raises(ValueError):
+        fake_grid.set_frozen_temperatures(torch.zeros(19, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        fake_grid.set_pah_spectra(0, torch.zeros((3, 5), dtype=torch.float32))
