@@ -223,6 +223,15 @@ def _buf(x, kind: str, n: int, what: str, exact: bool = False, device=None):
     return ptr, mem
 
 
+def _dev_buf(x, kind: str, n: int, what: str, exact: bool = False, device=None):
+    """Device pointer of a CUDA tensor checked as in _buf (for calls that take device
+    buffers only)."""
+    ptr, mem = _buf(x, kind, n, what, exact=exact, device=device)
+    if mem != MEM_DEVICE:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    return ptr
+
+
 class Grid:
     """One model on the device (handle to ``rt_grid``)."""
 
@@ -418,10 +427,14 @@ class Grid:
                                          _stream(stream)), "rt_set_pah_spectra")
 
     def pah_training_pairs(self, pah: int, X, Y, p_abs, first: int = 0, stream=None):
+        """Training pairs of PAH `pah` for cells first .. first+n-1 into CUDA tensors X
+        [n][n_coarse+2], Y [n][B] and p_abs [n] (float32)."""
         n = int(X.shape[0])
-        _check(load().rt_pah_training_pairs(self._h, int(pah), int(first), n, X.data_ptr(),
-                                            Y.data_ptr(), p_abs.data_ptr(), _stream(stream)),
-               "rt_pah_training_pairs")
+        px = _dev_buf(X, "f32", n * (self.n_coarse + 2), "X", exact=True, device=self.device)
+        py = _dev_buf(Y, "f32", n * self.B, "Y", exact=True, device=self.device)
+        pa = _dev_buf(p_abs, "f32", n, "p_abs", exact=True, device=self.device)
+        _check(load().rt_pah_training_pairs(self._h, int(pah), int(first), n, px, py, pa,
+                                            _stream(stream)), "rt_pah_training_pairs")
 
     image_shape = (0, 0, 0)
 
@@ -583,6 +596,7 @@ class MLP:
                "rt_mlp_create")
         self._h = h
         self.n_in, self.n_hidden, self.n_layers, self.n_out = n_in, n_hidden, n_layers, n_out
+        self.device = _torch_device()  # the device the network lives on, when torch knows it
         n = C.c_int64()
         _check(L.rt_mlp_n_params(h, C.byref(n)), "rt_mlp_n_params")
         self.n_params = int(n.value)
@@ -605,18 +619,25 @@ class MLP:
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
-        assert p.size == self.n_params
+        if p.size != self.n_params:
+            raise ValueError(f"{p.size} parameters, the network has {self.n_params}")
         _check(load().rt_mlp_set_params(self._h, p.ctypes.data), "rt_mlp_set_params")
 
     def forward(self, x, y, stream=None):
-        _check(load().rt_mlp_forward(self._h, x.data_ptr(), y.data_ptr(), int(x.shape[0]),
-                                     _stream(stream)), "rt_mlp_forward")
+        """y [M][n_out] = network(x [M][n_in]); CUDA float32 tensors."""
+        M = int(x.shape[0])
+        px = _dev_buf(x, "f32", M * self.n_in, "x", exact=True, device=self.device)
+        py = _dev_buf(y, "f32", M * self.n_out, "y", device=self.device)
+        _check(load().rt_mlp_forward(self._h, px, py, M, _stream(stream)), "rt_mlp_forward")
         return y
 
     def loss_grad(self, x, t, want_loss: bool = True, want_grad: bool = False, stream=None):
         loss = C.c_float()
         g = np.zeros(self.n_params, dtype=np.float32) if want_grad else None
-        _check(load().rt_mlp_loss_grad(self._h, x.data_ptr(), t.data_ptr(), int(x.shape[0]),
+        M = int(x.shape[0])
+        px = _dev_buf(x, "f32", M * self.n_in, "x", exact=True, device=self.device)
+        pt = _dev_buf(t, "f32", M * self.n_out, "t", exact=True, device=self.device)
+        _check(load().rt_mlp_loss_grad(self._h, px, pt, M,
                                        C.byref(loss) if want_loss else None,
                                        g.ctypes.data if want_grad else None, _stream(stream)),
                "rt_mlp_loss_grad")

@@ -94,3 +94,19 @@ def test_grid_inputs_must_have_the_exact_length(fake_grid):
         fake_grid.set_frozen_temperatures(torch.zeros(19, dtype=torch.float32))
     with pytest.raises(ValueError):
         fake_grid.set_pah_spectra(0, torch.zeros((3, 5), dtype=torch.float32))
+
+
+def test_device_only_calls_reject_host_and_misshapen_buffers(fake_grid, monkeypatch):
+    torch = pytest.importorskip("torch")
+    net = object.__new__(rt.MLP)
+    net.n_in, net.n_out, net.n_params, net.device, net._h = 6, 4, 10, None, None
+    x, y = torch.zeros((3, 6)), torch.zeros((3, 4))
+    with pytest.raises(ValueError):           # host tensors where device buffers are read
+        net.forward(x, y)
+    with pytest.raises(ValueError):
+        net.loss_grad(np.zeros((3, 6), np.float32), y)
+    with pytest.raises(ValueError):
+        fake_grid.pah_training_pairs(0, torch.zeros((5, 6)), torch.zeros((5, 4)),
+                                     torch.zeros(5))
+    with pytest.raises(ValueError):
+        net.set_params(np.zeros(9, np.float32))
