@@ -19,6 +19,19 @@ from . import rt
 BATCH_CANDIDATES = dict(blocks_per_sm=(0, 5), threads=(128, 256), interaction_batch=(4, 8, 12),
                         refill_period=(16, 32))
 CANDIDATES = dict(BATCH_CANDIDATES, walk=(rt.WALK_LINKED, rt.WALK_PATH))
+
+
+def single_grid_candidates():
+    """The launch options tried for one grid. Five resident blocks of 256 threads
+    select the linked walk's variant compiled for that occupancy; the path walk is
+    compiled for four such blocks only, so there a cap of five is the occupancy itself
+    and that launch is tried (and reported) once, as blocks_per_sm = 0."""
+    for values in itertools.product(*CANDIDATES.values()):
+        opts = dict(zip(CANDIDATES, values))
+        if (opts["walk"] == rt.WALK_PATH and opts["blocks_per_sm"] == 5 and
+                opts["threads"] == 256):
+            continue
+        yield opts
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1201_3588_gb300",
                              "autotune.json")
 
@@ -51,8 +64,7 @@ def tune(grid: "rt.Grid", tau_v: float, n_probe: int = 2_000_000, cache: Optiona
     n_probe = min(n_probe, getattr(grid, "n_total", n_probe))
     grid.transport(min(n_probe, 100_000), seed=1)      # warm
     best = None
-    for values in itertools.product(*CANDIDATES.values()):
-        opts = dict(zip(CANDIDATES, values))
+    for opts in single_grid_candidates():
         grid.reset(s)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)

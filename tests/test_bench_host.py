@@ -71,3 +71,18 @@ def test_source_hash_ignores_comments_and_blank_lines(tmp_path, monkeypatch):
     assert bench.source_code_hash(["a.cu"]) == h
     a.write_text("int f() {\n  return 2;\n}\n")
     assert bench.source_code_hash(["a.cu"]) != h
+
+
+def test_autotuner_tries_each_distinct_launch_once():
+    from paper_1201_3588_gb300 import autotune, rt
+    c = list(autotune.single_grid_candidates())
+    keys = [tuple(sorted(o.items())) for o in c]
+    assert len(keys) == len(set(keys))
+    assert all(set(o) == set(autotune.CANDIDATES) for o in c)
+    # both walks, every interaction batch and refill period
+    for k, vals in autotune.CANDIDATES.items():
+        assert {o[k] for o in c} == set(vals)
+    # the path walk has no five-block build for 256 threads: that cap is its occupancy
+    assert not any(o["walk"] == rt.WALK_PATH and o["blocks_per_sm"] == 5 and o["threads"] == 256
+                   for o in c)
+    assert any(o["walk"] == rt.WALK_LINKED and o["blocks_per_sm"] == 5 for o in c)
